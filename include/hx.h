@@ -1,0 +1,207 @@
+/*
+ * hx — matrix-free high-order Helmholtz / Poisson operator and Jacobi-PCG on
+ * one NVIDIA B300 (sm_103a).  C ABI of libhx.so.
+ *
+ * The operator is A = alpha M + K(nu) on a continuous Q_p space over a mesh of
+ * trilinear hexahedra, with the nodal Gauss-Lobatto-Legendre basis and tensor
+ * Gauss quadrature with q points per direction:
+ *   M_ij = int phi_i phi_j dx                      (Sec. 2, Eq. (vectorMass))
+ *   K_ij = int nu grad phi_i . grad phi_j dx       (Sec. 2, Eq. (vectorDiffusion);
+ *                                                   element form Sec. 3.1, Eqs. (localStiffness)-(localStiffnessQuadrature))
+ * i.e. the system A u = b with A = c M + L, c >= 0, of Sec. 5.2, applied
+ * matrix-free by sum factorization (Sec. 3.1) and solved with conjugate
+ * gradients (Sec. 5, Sec. 5.3) preconditioned by the diagonal of A.
+ *
+ * Conventions (readings where the paper is silent):
+ *   - reference cube [-1,1]^3; local node and quadrature-point order is
+ *     lexicographic with the first reference coordinate fastest;
+ *   - J_ij = dx_i/dxi_j, stiffness coefficient nu w detJ J^-1 J^-T;
+ *   - Dirichlet DoFs are eliminated symmetrically: the constrained operator is
+ *     A_c = P A P + (I - P), P zeroing Dirichlet DoFs; solves use b_c = P b;
+ *   - element corners are ordered c = cx + 2 cy + 4 cz (corner c at reference
+ *     point (2cx-1, 2cy-1, 2cz-1)).
+ *
+ * Memory and streams: arguments documented "device" are pointers into the
+ * current CUDA device's global memory, owned by the caller and left
+ * untouched by the library except where written as outputs.  "host" pointers
+ * are ordinary CPU memory (pinned memory gives faster copies).  The library
+ * allocates and owns its own workspaces (restriction maps, geometric factors,
+ * E-vectors, CG vectors) in *_create (CG vectors at the first solve) and frees
+ * them in *_destroy.  Calls taking a `stream` (a cudaStream_t passed as void*,
+ * NULL = legacy default stream) enqueue their work on it and return without
+ * waiting, except where noted.
+ *
+ * Errors: every call returns an hx_status; 0 is success.  On failure the
+ * thread-local message hx_last_error() says what went wrong.  No call aborts,
+ * throws or exits.  Supported orders: 1 <= p <= 8 with q = p+1 or q = p+2.
+ */
+#ifndef HX_H
+#define HX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HX_API __attribute__((visibility("default")))
+#else
+#define HX_API
+#endif
+
+typedef int hx_status;
+
+#define HX_OK 0
+#define HX_ERR_ARG (-1)            /* invalid argument (null pointer, bad size, out-of-range index) */
+#define HX_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define HX_ERR_OOM (-3)            /* device memory allocation failed */
+#define HX_ERR_INVALID_MESH (-4)   /* detJ <= 0 at some quadrature point */
+#define HX_ERR_NOT_CONVERGED (-5)  /* CG hit max_it before the tolerance */
+#define HX_ERR_BREAKDOWN (-6)      /* CG breakdown: p^T A p <= 0 or a non-finite value */
+#define HX_ERR_UNSUPPORTED (-7)    /* (p, q) or a size outside what is built */
+
+#define HX_GEOM_STORED 0   /* factors m, G stored at every quadrature point (Sec. 3.1: J stored at points) */
+#define HX_GEOM_ONTHEFLY 1 /* factors recomputed from the 8 element vertices at every apply */
+
+typedef struct hx_mesh hx_mesh;
+typedef struct hx_op hx_op;
+
+/* Result of a solve (all fields filled whatever the return status). */
+typedef struct hx_solve_info {
+  int iterations;            /* CG iterations performed */
+  int status;                /* HX_OK, HX_ERR_NOT_CONVERGED or HX_ERR_BREAKDOWN */
+  double rel_residual;       /* ||r_k||_2 / ||P b||_2 of the CG recurrence residual */
+  double true_rel_residual;  /* ||P b - A_c x||_2 / ||P b||_2, recomputed with one extra apply */
+  double b_norm;             /* ||P b||_2 */
+} hx_solve_info;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+HX_API int hx_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+HX_API const char* hx_last_error(void);
+
+/*
+ * Mesh of trilinear hexahedra carrying a Q_p space (Sec. 3: mapped hexahedra,
+ * nodal Gauss-Lobatto tensor-product basis; Sec. 3.1: the element restriction
+ * over which the element-by-element sum of the operator action runs).
+ *   p, q          order and Gauss points per direction (1 <= p <= 8, q in {p+1, p+2})
+ *   n_vert        number of vertices; vert_xyz: host, n_vert x 3 doubles (x, y, z per vertex)
+ *   n_elem        number of elements; elem_vert: host, n_elem x 8 vertex ids (corner order above)
+ *   n_dof         number of global DoFs (L-vector length)
+ *   restriction   host, n_elem x (p+1)^3 global DoF ids in [0, n_dof), local node order
+ *                 lexicographic; the caller guarantees it is conforming (shared nodes share ids)
+ *   dirichlet     host, n_dof bytes, nonzero = Dirichlet (eliminated) DoF; NULL = none
+ *   out           receives the new mesh (NULL on failure)
+ * Copies everything to the device; the host arrays can be freed on return.
+ * Errors: HX_ERR_ARG (null/invalid sizes, ids out of range, a DoF in no element),
+ * HX_ERR_UNSUPPORTED (p, q, or n_elem (p+1)^3 >= 2^31), HX_ERR_OOM, HX_ERR_CUDA.
+ * Synchronous.
+ */
+HX_API hx_status hx_mesh_create(int p, int q, int64_t n_vert, const double* vert_xyz, int64_t n_elem,
+                                const int64_t* elem_vert, int64_t n_dof, const int64_t* restriction,
+                                const uint8_t* dirichlet, hx_mesh** out);
+
+/*
+ * Structured nx x ny x nz mesh (elements and vertices lexicographic, x fastest)
+ * with the vertex positions given: vert_xyz is host, (nx+1)(ny+1)(nz+1) x 3.
+ * The library numbers the global DoFs lexicographically over the
+ * (p nx + 1) x (p ny + 1) x (p nz + 1) node grid (x fastest) and marks every
+ * DoF on the boundary of the index box as Dirichlet.  Errors as hx_mesh_create.
+ */
+HX_API hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const double* vert_xyz,
+                                           hx_mesh** out);
+
+/* Frees the mesh (NULL is ignored).  Operators built on it must be destroyed first. */
+HX_API void hx_mesh_destroy(hx_mesh* mesh);
+
+/* Sizes of a mesh; any output pointer may be NULL. */
+HX_API hx_status hx_mesh_info(const hx_mesh* mesh, int64_t* n_elem, int64_t* n_dof, int* p, int* q);
+
+/*
+ * Physical coordinates of the quadrature points (the points xi of Sec. 3.1
+ * mapped by the trilinear element map).  xyz: device, n_elem x q^3 x 3
+ * doubles, point order lexicographic.  Stream-ordered.
+ */
+HX_API hx_status hx_mesh_qpoint_coords(const hx_mesh* mesh, double* xyz, void* stream);
+
+/* Physical coordinates of every global DoF (GLL node).  xyz: device, n_dof x 3.  Stream-ordered. */
+HX_API hx_status hx_mesh_node_coords(const hx_mesh* mesh, double* xyz, void* stream);
+
+/*
+ * Operator A = alpha M + K(nu) (Sec. 5.2, A = c M + L) on `mesh`.
+ *   alpha      mass coefficient (>= 0 for an SPD/SPSD operator; e.g. 1/dt, 0 for Poisson)
+ *   nu         constant viscosity, used when nu_q is NULL
+ *   nu_q       device, n_elem x q^3 per-quadrature-point viscosity, or NULL; copied
+ *   geom_mode  HX_GEOM_STORED: precompute m = alpha w detJ and G = nu w detJ J^-1 J^-T
+ *              at every point ([E][7][q^3] doubles, Sec. 3.1 stored-J variant);
+ *              HX_GEOM_ONTHEFLY: recompute them from the element vertices at each apply
+ *   stream     stream for the setup kernels (geometric factors, diagonal)
+ * Also assembles the diagonal of A (for Jacobi).  Returns HX_ERR_INVALID_MESH
+ * when detJ <= 0 at some quadrature point.  Synchronizes `stream` before returning.
+ */
+HX_API hx_status hx_op_create(hx_mesh* mesh, double alpha, double nu, const double* nu_q, int geom_mode,
+                              void* stream, hx_op** out);
+
+/* Sizes of the mesh an operator is built on; any output pointer may be NULL. */
+HX_API hx_status hx_op_info(const hx_op* op, int64_t* n_elem, int64_t* n_dof, int* p, int* q);
+
+/* Frees the operator (NULL is ignored). */
+HX_API void hx_op_destroy(hx_op* op);
+
+/*
+ * y = A x (constrained = 0) or y = A_c x = P A P x + (I - P) x (constrained = 1),
+ * matrix-free: gather through the element restriction, sum-factorized
+ * contractions with B and D (Sec. 3.1, Eqs. (B1D), (D1D), (sumFactorized),
+ * (tensorGradient)), pointwise factors, transposed contractions, and an
+ * atomic-free element-to-global sum in a fixed order (bitwise reproducible).
+ * x, y: device, n_dof doubles each; must not overlap.  Stream-ordered.
+ */
+HX_API hx_status hx_op_apply(hx_op* op, const double* x, double* y, int constrained, void* stream);
+
+/*
+ * diag: device, n_dof doubles <- the exact diagonal of A (same quadrature),
+ * assembled sum-factorized; with constrained = 1 the Dirichlet entries are 1
+ * (the diagonal of A_c).  Stream-ordered.
+ */
+HX_API hx_status hx_op_diagonal(hx_op* op, double* diag, int constrained, void* stream);
+
+/*
+ * Load vector b_i = (f, phi_i) = sum_K sum_q w_q detJ_q f_q phi_i(xi_q), the
+ * right-hand side of the weak form (Sec. 3, Eq. (weak-stokes), one scalar
+ * component).  f_q: device, n_elem x q^3 values of f at the quadrature points
+ * (see hx_mesh_qpoint_coords); b: device, n_dof.  Stream-ordered.
+ */
+HX_API hx_status hx_op_load_vector(hx_op* op, const double* f_q, double* b, void* stream);
+
+/*
+ * Jacobi-preconditioned CG (Sec. 5, Sec. 5.3; Jacobi = diagonal of A_c) for
+ * A_c x = P b.  Stops when ||r_k||_2 <= rtol ||P b||_2 (recurrence residual) or
+ * after max_it iterations.
+ *   b         device, n_dof (entries at Dirichlet DoFs are ignored)
+ *   x         device, n_dof; input initial guess if use_x0 != 0 (Dirichlet
+ *             entries taken as 0), else ignored; output solution (0 at Dirichlet DoFs)
+ *   info      host, filled on return (may be NULL)
+ * All scalars stay on the device; iterations run in a CUDA graph and the
+ * host only polls a status word.  Waits for `stream`'s prior work and
+ * returns after the solution is written (synchronous).
+ * Returns HX_OK, HX_ERR_NOT_CONVERGED or HX_ERR_BREAKDOWN (x then holds the
+ * last iterate), or an argument / CUDA error.
+ */
+HX_API hx_status hx_solve_pcg(hx_op* op, const double* b, double* x, double rtol, int max_it, int use_x0,
+                              void* stream, hx_solve_info* info);
+
+/*
+ * As hx_solve_pcg with b and x in host memory: copies b (and x0) to the
+ * device, solves, and copies x back.  b_host, x_host: host, n_dof doubles.
+ * Synchronous.
+ */
+HX_API hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, double rtol, int max_it,
+                                   int use_x0, hx_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HX_H */

@@ -10,8 +10,8 @@ directly (no sum factorization, no blocking):
   * element matrix (Eqs. (vectorMass), (localStiffnessQuadrature), with the
     Helmholtz combination A = c M + L of Sec. 5.2):
         A^K = sum_q w_q detJ_q [ alpha Phi_q Phi_q^T + nu_q (J^-T dPhi_q)^T (J^-T dPhi_q) ];
-  * global action y = sum_K R_K^T A^K R_K x, the "sum of the contributions of
-    each element" (Sec. 3.1).
+  * global action y = sum_K R_K^T A^K R_K x: the element-by-element sum of the
+    operator action described in Sec. 3.1.
 
 Local node order is lexicographic, i (the xi_1 index) fastest; quadrature
 points likewise.  Global DoF order for structured meshes: lexicographic over
@@ -101,6 +101,9 @@ class Mesh:
         self.n_dof = int(n_dof)
         self.dirichlet = np.zeros(self.n_dof, dtype=bool) if dirichlet is None else np.asarray(dirichlet, dtype=bool)
 
+    def element_dofs(self, e):
+        return self.restriction[e]
+
     def qpoint_coords(self):
         """Physical coordinates of every quadrature point, (E, Q, 3)."""
         x, _ = trilinear_map(self.vertices[self.elem_vert], self.ref.xi)
@@ -118,23 +121,19 @@ class Mesh:
         return out
 
 
-def structured_restriction(nx, ny, nz, p):
-    """Global ids (E, (p+1)^3) of the local nodes of each element of an nx x ny x nz grid."""
+def structured_restriction(nx, ny, nz, p, elems=None):
+    """Global ids (len(elems), (p+1)^3) of the local nodes of elements of an nx x ny x nz grid.
+
+    Element e = ex + nx (ey + ny ez) has local node (i, j, k) at global grid
+    node (p ex + i, p ey + j, p ez + k), numbered x fastest.
+    """
     n = p + 1
     gx, gy = p * nx + 1, p * ny + 1
-    R = np.empty((nx * ny * nz, n ** 3), dtype=np.int64)
-    e = 0
-    for ez in range(nz):
-        for ey in range(ny):
-            for ex in range(nx):
-                l = 0
-                for k in range(n):
-                    for j in range(n):
-                        for i in range(n):
-                            R[e, l] = (p * ex + i) + gx * ((p * ey + j) + gy * (p * ez + k))
-                            l += 1
-                e += 1
-    return R
+    e = np.arange(nx * ny * nz, dtype=np.int64) if elems is None else np.asarray(elems, dtype=np.int64)
+    ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+    l = np.arange(n ** 3, dtype=np.int64)
+    i, j, k = l % n, (l // n) % n, l // (n * n)
+    return (p * ex[:, None] + i[None, :]) + gx * ((p * ey[:, None] + j[None, :]) + gy * (p * ez[:, None] + k[None, :]))
 
 
 def structured_boundary(nx, ny, nz, p):
@@ -146,14 +145,27 @@ def structured_boundary(nx, ny, nz, p):
 
 
 class StructuredMesh(Mesh):
-    """Mesh of an nx x ny x nz grid of hexahedra (vertex layout of ``synthetic``)."""
+    """Mesh of an nx x ny x nz grid of hexahedra (vertex layout of ``synthetic``).
 
-    def __init__(self, nx, ny, nz, p, q, vertices, elem_vert, dirichlet_boundary=True):
-        R = structured_restriction(nx, ny, nz, p)
+    lazy=True skips building the full restriction (large meshes): element
+    DoFs are then computed per element by ``element_dofs``.
+    """
+
+    def __init__(self, nx, ny, nz, p, q, vertices, elem_vert, dirichlet_boundary=True, lazy=False):
+        R = None if lazy else structured_restriction(nx, ny, nz, p)
         n_dof = (p * nx + 1) * (p * ny + 1) * (p * nz + 1)
         dmask = structured_boundary(nx, ny, nz, p) if dirichlet_boundary else None
-        super().__init__(p, q, vertices, elem_vert, R, n_dof, dmask)
         self.shape = (nx, ny, nz)
+        if lazy:
+            Mesh.__init__(self, p, q, vertices, elem_vert, np.zeros((0, (p + 1) ** 3), np.int64), n_dof, dmask)
+            self.restriction = None
+        else:
+            super().__init__(p, q, vertices, elem_vert, R, n_dof, dmask)
+
+    def element_dofs(self, e):
+        if self.restriction is not None:
+            return self.restriction[e]
+        return structured_restriction(*self.shape, self.p, [e])[0]
 
     def elements_of_dof(self, g):
         """(element, local index) pairs containing global DoF g."""
@@ -253,7 +265,7 @@ class Operator:
                 continue
             for e, l in mesh.elements_of_dof(int(g)):
                 row = self.element_matrices([e], [l])[0, 0]
-                out[t] += row @ xin[mesh.restriction[e]]
+                out[t] += row @ xin[mesh.element_dofs(e)]
         return out
 
     def diagonal(self, constrained=False):

@@ -1,0 +1,324 @@
+"""Python binding of libhx.so: the B300 matrix-free Q_p Helmholtz operator and Jacobi-PCG.
+
+Argument marshalling only.  Every computation runs in the CUDA library
+behind ``include/hx.h``; the functions here carry the same names as its C
+entry points, take torch CUDA tensors (float64, contiguous) for device
+buffers and numpy arrays / CPU tensors for host buffers, check their sizes,
+and raise ``HxError`` when the library returns a non-zero status.  The
+library must be built first (``python paper_1910_03032_b300/build.py``);
+importing without it raises ImportError: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhx.so")
+
+HX_OK = 0
+HX_ERR_ARG = -1
+HX_ERR_CUDA = -2
+HX_ERR_OOM = -3
+HX_ERR_INVALID_MESH = -4
+HX_ERR_NOT_CONVERGED = -5
+HX_ERR_BREAKDOWN = -6
+HX_ERR_UNSUPPORTED = -7
+HX_GEOM_STORED = 0
+HX_GEOM_ONTHEFLY = 1
+
+_NAMES = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_CUDA", -3: "HX_ERR_OOM", -4: "HX_ERR_INVALID_MESH",
+          -5: "HX_ERR_NOT_CONVERGED", -6: "HX_ERR_BREAKDOWN", -7: "HX_ERR_UNSUPPORTED"}
+
+_P, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_SIZES = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+
+# Every entry point of include/hx.h: name -> (restype, argtypes)
+SIGNATURES = {
+    "hx_version": (ctypes.c_int, []),
+    "hx_last_error": (ctypes.c_char_p, []),
+    "hx_mesh_create": (_I, [_I, _I, _I64, _P, _I64, _P, _I64, _P, _P, ctypes.POINTER(_P)]),
+    "hx_mesh_create_structured": (_I, [_I, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
+    "hx_mesh_destroy": (None, [_P]),
+    "hx_mesh_info": (_I, _SIZES),
+    "hx_mesh_qpoint_coords": (_I, [_P, _P, _P]),
+    "hx_mesh_node_coords": (_I, [_P, _P, _P]),
+    "hx_op_create": (_I, [_P, _D, _D, _P, _I, _P, ctypes.POINTER(_P)]),
+    "hx_op_info": (_I, _SIZES),
+    "hx_op_destroy": (None, [_P]),
+    "hx_op_apply": (_I, [_P, _P, _P, _I, _P]),
+    "hx_op_diagonal": (_I, [_P, _P, _I, _P]),
+    "hx_op_load_vector": (_I, [_P, _P, _P, _P]),
+    "hx_solve_pcg": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
+    "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(SolveInfo)]),
+}
+
+
+class HxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python paper_1910_03032_b300/build.py`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int) -> int:
+    if status != HX_OK:
+        raise HxError(status, _lib.hx_last_error().decode())
+    return status
+
+
+def _dptr(t, n=None, name="tensor"):
+    """Device pointer of a contiguous float64 CUDA tensor with n elements."""
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != "torch.float64" or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float64")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, n, name="array"):
+    """Host pointer of a contiguous float64 numpy array or CPU tensor with n elements."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise TypeError(f"{name} must be a contiguous float64 CPU tensor")
+        if a.numel() != n:
+            raise ValueError(f"{name} has {a.numel()} elements, expected {n}")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous float64 numpy array")
+    if a.size != n:
+        raise ValueError(f"{name} has {a.size} elements, expected {n}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def hx_version() -> int:
+    return _lib.hx_version()
+
+
+def hx_last_error() -> str:
+    return _lib.hx_last_error().decode()
+
+
+def hx_mesh_create(p, q, vert_xyz, elem_vert, n_dof, restriction, dirichlet=None):
+    vert_xyz = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    elem_vert = np.ascontiguousarray(elem_vert, dtype=np.int64)
+    restriction = np.ascontiguousarray(restriction, dtype=np.int64)
+    n_elem = elem_vert.shape[0]
+    if elem_vert.shape != (n_elem, 8) or restriction.shape != (n_elem, (p + 1) ** 3) or vert_xyz.shape[1] != 3:
+        raise ValueError("shape mismatch in hx_mesh_create arguments")
+    dptr = None
+    if dirichlet is not None:
+        dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+        if dirichlet.size != n_dof:
+            raise ValueError("dirichlet must have n_dof entries")
+        dptr = ctypes.c_void_p(dirichlet.ctypes.data)
+    out = ctypes.c_void_p()
+    _check(_lib.hx_mesh_create(p, q, vert_xyz.shape[0], ctypes.c_void_p(vert_xyz.ctypes.data), n_elem,
+                               ctypes.c_void_p(elem_vert.ctypes.data), int(n_dof),
+                               ctypes.c_void_p(restriction.ctypes.data), dptr, ctypes.byref(out)))
+    return out
+
+
+def hx_mesh_create_structured(nx, ny, nz, p, q, vert_xyz):
+    vert_xyz = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    if nx < 1 or ny < 1 or nz < 1:
+        # still handed to the library, which reports HX_ERR_ARG
+        return _check_none(_lib.hx_mesh_create_structured(nx, ny, nz, p, q, ctypes.c_void_p(vert_xyz.ctypes.data),
+                                                          ctypes.byref(ctypes.c_void_p())))
+    if vert_xyz.shape != ((nx + 1) * (ny + 1) * (nz + 1), 3):
+        raise ValueError("vert_xyz must be ((nx+1)(ny+1)(nz+1), 3)")
+    out = ctypes.c_void_p()
+    _check(_lib.hx_mesh_create_structured(nx, ny, nz, p, q, ctypes.c_void_p(vert_xyz.ctypes.data), ctypes.byref(out)))
+    return out
+
+
+def _check_none(status):
+    _check(status)
+    return None
+
+
+def hx_mesh_destroy(mesh):
+    _lib.hx_mesh_destroy(mesh)
+
+
+def _info(fn, h):
+    E, n, p, q = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+    _check(fn(h, ctypes.byref(E), ctypes.byref(n), ctypes.byref(p), ctypes.byref(q)))
+    return E.value, n.value, p.value, q.value
+
+
+def hx_mesh_info(mesh):
+    return _info(_lib.hx_mesh_info, mesh)
+
+
+def hx_op_info(op):
+    return _info(_lib.hx_op_info, op)
+
+
+def hx_mesh_qpoint_coords(mesh, xyz, stream=None):
+    E, _, _, q = hx_mesh_info(mesh)
+    _check(_lib.hx_mesh_qpoint_coords(mesh, _dptr(xyz, E * q ** 3 * 3, "xyz"), _stream(stream)))
+
+
+def hx_mesh_node_coords(mesh, xyz, stream=None):
+    _, n, _, _ = hx_mesh_info(mesh)
+    _check(_lib.hx_mesh_node_coords(mesh, _dptr(xyz, n * 3, "xyz"), _stream(stream)))
+
+
+def hx_op_create(mesh, alpha, nu, nu_q=None, geom_mode=HX_GEOM_STORED, stream=None):
+    E, _, _, q = hx_mesh_info(mesh)
+    nptr = None if nu_q is None else _dptr(nu_q, E * q ** 3, "nu_q")
+    out = ctypes.c_void_p()
+    _check(_lib.hx_op_create(mesh, float(alpha), float(nu), nptr, int(geom_mode), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def hx_op_destroy(op):
+    _lib.hx_op_destroy(op)
+
+
+def hx_op_apply(op, x, y, constrained=False, stream=None):
+    n = hx_op_info(op)[1]
+    _check(_lib.hx_op_apply(op, _dptr(x, n, "x"), _dptr(y, n, "y"), int(bool(constrained)), _stream(stream)))
+
+
+def hx_op_diagonal(op, diag, constrained=False, stream=None):
+    n = hx_op_info(op)[1]
+    _check(_lib.hx_op_diagonal(op, _dptr(diag, n, "diag"), int(bool(constrained)), _stream(stream)))
+
+
+def hx_op_load_vector(op, f_q, b, stream=None):
+    E, n, _, q = hx_op_info(op)
+    _check(_lib.hx_op_load_vector(op, _dptr(f_q, E * q ** 3, "f_q"), _dptr(b, n, "b"), _stream(stream)))
+
+
+def hx_solve_pcg(op, b, x, rtol=1e-10, max_it=10000, use_x0=False, stream=None, raise_on_fail=True):
+    n = hx_op_info(op)[1]
+    info = SolveInfo()
+    st = _lib.hx_solve_pcg(op, _dptr(b, n, "b"), _dptr(x, n, "x"), float(rtol), int(max_it), int(bool(use_x0)),
+                           _stream(stream), ctypes.byref(info))
+    if raise_on_fail or st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_BREAKDOWN):
+        _check(st)
+    return info.as_dict()
+
+
+def hx_solve_pcg_host(op, b_host, x_host, rtol=1e-10, max_it=10000, use_x0=False, raise_on_fail=True):
+    n = hx_op_info(op)[1]
+    info = SolveInfo()
+    st = _lib.hx_solve_pcg_host(op, _hptr(b_host, n, "b_host"), _hptr(x_host, n, "x_host"), float(rtol),
+                                int(max_it), int(bool(use_x0)), ctypes.byref(info))
+    if raise_on_fail or st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_BREAKDOWN):
+        _check(st)
+    return info.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# owning handles (destroyed on garbage collection); still marshalling only
+# ---------------------------------------------------------------------------
+class Mesh:
+    def __init__(self, handle):
+        self.handle = handle
+        self.n_elem, self.n_dof, self.p, self.q = hx_mesh_info(handle)
+
+    @classmethod
+    def structured(cls, nx, ny, nz, p, q, vert_xyz):
+        return cls(hx_mesh_create_structured(nx, ny, nz, p, q, vert_xyz))
+
+    @classmethod
+    def general(cls, p, q, vert_xyz, elem_vert, n_dof, restriction, dirichlet=None):
+        return cls(hx_mesh_create(p, q, vert_xyz, elem_vert, n_dof, restriction, dirichlet))
+
+    def qpoint_coords(self, stream=None):
+        import torch
+        out = torch.empty((self.n_elem, self.q ** 3, 3), dtype=torch.float64, device="cuda")
+        hx_mesh_qpoint_coords(self.handle, out, stream)
+        return out
+
+    def node_coords(self, stream=None):
+        import torch
+        out = torch.empty((self.n_dof, 3), dtype=torch.float64, device="cuda")
+        hx_mesh_node_coords(self.handle, out, stream)
+        return out
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h is not None and _lib is not None:
+            _lib.hx_mesh_destroy(h)
+
+
+class Operator:
+    def __init__(self, mesh: Mesh, alpha, nu, nu_q=None, geom_mode=HX_GEOM_STORED, stream=None):
+        self.mesh = mesh  # keeps the mesh alive
+        self.handle = hx_op_create(mesh.handle, alpha, nu, nu_q, geom_mode, stream)
+        self.n_dof = mesh.n_dof
+
+    def apply(self, x, y=None, constrained=False, stream=None):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        hx_op_apply(self.handle, x, y, constrained, stream)
+        return y
+
+    def diagonal(self, constrained=False, stream=None):
+        import torch
+        d = torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+        hx_op_diagonal(self.handle, d, constrained, stream)
+        return d
+
+    def load_vector(self, f_q, stream=None):
+        import torch
+        b = torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+        hx_op_load_vector(self.handle, f_q, b, stream)
+        return b
+
+    def solve(self, b, x=None, rtol=1e-10, max_it=10000, stream=None, raise_on_fail=True):
+        import torch
+        use_x0 = x is not None
+        x = torch.zeros_like(b) if x is None else x
+        info = hx_solve_pcg(self.handle, b, x, rtol, max_it, use_x0, stream, raise_on_fail)
+        return x, info
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h is not None and _lib is not None:
+            _lib.hx_op_destroy(h)
+
+
+__all__ = list(SIGNATURES) + ["Mesh", "Operator", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
+                              "HX_GEOM_ONTHEFLY"]

@@ -1,0 +1,607 @@
+// C ABI of libhx.so (declared in include/hx.h): mesh and restriction setup,
+// operator setup (geometric factors, diagonal), operator apply, load vector,
+// and the graph-driven Jacobi-PCG solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hx.h"
+#include "hx_internal.h"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string g_err;
+
+hx_status fail(hx_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+hx_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a non-sticky error
+  if (e == cudaErrorMemoryAllocation) return fail(HX_ERR_OOM, "%s: out of device memory", what);
+  return fail(HX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define HX_TRY(call, what)                             \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+template <typename T>
+hx_status dalloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, what);
+  }
+  return HX_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct hx_mesh {
+  int p = 0, q = 0, n = 0, N3 = 0, device = 0;
+  long long E = 0, n_dof = 0;
+  HxTables T;
+  int* R = nullptr;              // [E][n^3], g or -(g+1) for Dirichlet
+  int* off = nullptr;            // [n_dof + 1] transpose offsets
+  int* idx = nullptr;            // [E n^3] E-vector positions, increasing per DoF
+  unsigned char* dir = nullptr;  // [n_dof]
+  double* X8 = nullptr;          // [E][8][3]
+  int n_ops = 0;
+};
+
+struct hx_op {
+  hx_mesh* mesh = nullptr;
+  double alpha = 0, nu = 0;
+  int geom = 0;
+  double* factors = nullptr;  // [E][7][Q3] (stored)
+  double* nu_q = nullptr;     // [E][Q3] (on the fly with a field)
+  double* yE = nullptr;       // [E][n^3]
+  double* diag = nullptr;     // [n_dof] unconstrained diagonal
+  // solver workspace (allocated at the first solve)
+  double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *dinv = nullptr, *partial = nullptr;
+  double *hb = nullptr, *hx = nullptr;  // device staging for hx_solve_pcg_host
+  double* scalars = nullptr;            // [2] device scalars (dot products)
+  unsigned int* counters = nullptr;     // [2]
+  HxCgState* st = nullptr;
+  HxCgState* st_host = nullptr;   // pinned
+  cudaStream_t stream = nullptr;  // private non-blocking stream for solves
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+};
+
+namespace {
+
+hx_apply_launcher apply_launcher(int p) {
+  static const hx_apply_launcher t[] = {nullptr, hx_launch_apply_p1, hx_launch_apply_p2, hx_launch_apply_p3,
+                                        hx_launch_apply_p4, hx_launch_apply_p5, hx_launch_apply_p6,
+                                        hx_launch_apply_p7, hx_launch_apply_p8};
+  return t[p];
+}
+hx_diag_launcher diag_launcher(int p) {
+  static const hx_diag_launcher t[] = {nullptr, hx_launch_diag_p1, hx_launch_diag_p2, hx_launch_diag_p3,
+                                       hx_launch_diag_p4, hx_launch_diag_p5, hx_launch_diag_p6,
+                                       hx_launch_diag_p7, hx_launch_diag_p8};
+  return t[p];
+}
+hx_load_launcher load_launcher(int p) {
+  static const hx_load_launcher t[] = {nullptr, hx_launch_load_p1, hx_launch_load_p2, hx_launch_load_p3,
+                                       hx_launch_load_p4, hx_launch_load_p5, hx_launch_load_p6,
+                                       hx_launch_load_p7, hx_launch_load_p8};
+  return t[p];
+}
+
+hx_status check_order(int p, int q) {
+  if (p < 1 || p > HX_PMAX) return fail(HX_ERR_UNSUPPORTED, "p = %d outside 1..%d", p, HX_PMAX);
+  if (q != p + 1 && q != p + 2) return fail(HX_ERR_UNSUPPORTED, "q = %d not in {p+1, p+2} for p = %d", q, p);
+  return HX_OK;
+}
+
+// Build the device mesh from host arrays.  restriction is [E][n^3] int64.
+hx_status build_mesh(int p, int q, long long n_vert, const double* vert, long long E, const int64_t* ev,
+                     long long n_dof, const int64_t* R, const uint8_t* dir, hx_mesh** out) {
+  const int n = p + 1, N3 = n * n * n;
+  if ((long double)E * N3 >= 2147483647.0L)
+    return fail(HX_ERR_UNSUPPORTED, "n_elem * (p+1)^3 = %lld exceeds int32 indexing", (long long)E * N3);
+  if (n_dof >= 2147483647LL) return fail(HX_ERR_UNSUPPORTED, "n_dof too large");
+  // host-side restriction encoding and transpose (counting sort: deterministic order)
+  std::vector<int> Renc((size_t)E * N3);
+  std::vector<int> off((size_t)n_dof + 1, 0);
+  for (long long k = 0; k < E * N3; ++k) {
+    const long long g = R[k];
+    if (g < 0 || g >= n_dof) return fail(HX_ERR_ARG, "restriction entry %lld = %lld outside [0, %lld)", k, g, n_dof);
+    off[g + 1] += 1;
+  }
+  for (long long g = 0; g < n_dof; ++g) {
+    if (off[g + 1] == 0) return fail(HX_ERR_ARG, "global DoF %lld belongs to no element", g);
+    off[g + 1] += off[g];
+  }
+  std::vector<int> idx((size_t)E * N3), fill(off.begin(), off.end() - 1);
+  for (long long k = 0; k < E * N3; ++k) {
+    const long long g = R[k];
+    idx[fill[g]++] = (int)k;
+    Renc[k] = (dir && dir[g]) ? (int)(-g - 1) : (int)g;
+  }
+  std::vector<double> X8((size_t)E * 24);
+  for (long long e = 0; e < E; ++e)
+    for (int c = 0; c < 8; ++c) {
+      const long long v = ev[e * 8 + c];
+      if (v < 0 || v >= n_vert) return fail(HX_ERR_ARG, "elem_vert[%lld][%d] = %lld out of range", e, c, v);
+      for (int d = 0; d < 3; ++d) X8[e * 24 + c * 3 + d] = vert[v * 3 + d];
+    }
+  std::vector<unsigned char> dmask((size_t)n_dof, 0);
+  if (dir)
+    for (long long g = 0; g < n_dof; ++g) dmask[g] = dir[g] ? 1 : 0;
+
+  hx_mesh* m = new (std::nothrow) hx_mesh();
+  if (!m) return fail(HX_ERR_OOM, "host allocation failed");
+  m->p = p;
+  m->q = q;
+  m->n = n;
+  m->N3 = N3;
+  m->E = E;
+  m->n_dof = n_dof;
+  cudaGetDevice(&m->device);
+  if (hx_build_tables(p, q, &m->T) != 0) {
+    delete m;
+    return fail(HX_ERR_UNSUPPORTED, "cannot build tables for p=%d q=%d", p, q);
+  }
+  hx_status s;
+  if ((s = dalloc(&m->R, Renc.size(), "mesh restriction")) || (s = dalloc(&m->off, off.size(), "mesh offsets")) ||
+      (s = dalloc(&m->idx, idx.size(), "mesh transpose")) || (s = dalloc(&m->dir, dmask.size(), "mesh mask")) ||
+      (s = dalloc(&m->X8, X8.size(), "mesh vertices"))) {
+    hx_mesh_destroy(m);
+    return s;
+  }
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpy(m->R, Renc.data(), Renc.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->dir, dmask.data(), dmask.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->X8, X8.data(), X8.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    hx_mesh_destroy(m);
+    return cuda_fail(e, "mesh upload");
+  }
+  *out = m;
+  return HX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hx_version(void) { return 100; }
+
+const char* hx_last_error(void) { return g_err.c_str(); }
+
+hx_status hx_mesh_create(int p, int q, int64_t n_vert, const double* vert_xyz, int64_t n_elem,
+                         const int64_t* elem_vert, int64_t n_dof, const int64_t* restriction, const uint8_t* dirichlet,
+                         hx_mesh** out) {
+  if (!out) return fail(HX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  hx_status s = check_order(p, q);
+  if (s) return s;
+  if (n_vert < 8 || n_elem < 1 || n_dof < 1 || !vert_xyz || !elem_vert || !restriction)
+    return fail(HX_ERR_ARG, "bad sizes or NULL arrays");
+  return build_mesh(p, q, n_vert, vert_xyz, n_elem, elem_vert, n_dof, restriction, dirichlet, out);
+}
+
+hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const double* vert_xyz, hx_mesh** out) {
+  if (!out) return fail(HX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  hx_status s = check_order(p, q);
+  if (s) return s;
+  if (nx < 1 || ny < 1 || nz < 1 || !vert_xyz) return fail(HX_ERR_ARG, "bad grid size or NULL vertices");
+  const int n = p + 1, N3 = n * n * n;
+  const long long E = (long long)nx * ny * nz;
+  const long long gx = (long long)p * nx + 1, gy = (long long)p * ny + 1, gz = (long long)p * nz + 1;
+  const long long n_dof = gx * gy * gz;
+  if ((long double)E * N3 >= 2147483647.0L) return fail(HX_ERR_UNSUPPORTED, "mesh too large for int32 indexing");
+  const long long n_vert = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  std::vector<int64_t> ev((size_t)E * 8), R((size_t)E * N3);
+  std::vector<uint8_t> dir((size_t)n_dof);
+  const long long sx = nx + 1, sy = (long long)(nx + 1) * (ny + 1);
+  long long e = 0;
+  for (int ez = 0; ez < nz; ++ez)
+    for (int ey = 0; ey < ny; ++ey)
+      for (int ex = 0; ex < nx; ++ex, ++e) {
+        for (int c = 0; c < 8; ++c)
+          ev[e * 8 + c] = (ex + (c & 1)) + (ey + ((c >> 1) & 1)) * sx + (ez + ((c >> 2) & 1)) * sy;
+        int l = 0;
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i, ++l)
+              R[e * N3 + l] = ((long long)p * ex + i) + gx * (((long long)p * ey + j) + gy * ((long long)p * ez + k));
+      }
+  long long g = 0;
+  for (long long K = 0; K < gz; ++K)
+    for (long long J = 0; J < gy; ++J)
+      for (long long I = 0; I < gx; ++I, ++g)
+        dir[g] = (I == 0 || I == gx - 1 || J == 0 || J == gy - 1 || K == 0 || K == gz - 1) ? 1 : 0;
+  return build_mesh(p, q, n_vert, vert_xyz, E, ev.data(), n_dof, R.data(), dir.data(), out);
+}
+
+void hx_mesh_destroy(hx_mesh* m) {
+  if (!m) return;
+  dfree(m->R);
+  dfree(m->off);
+  dfree(m->idx);
+  dfree(m->dir);
+  dfree(m->X8);
+  delete m;
+}
+
+hx_status hx_mesh_info(const hx_mesh* m, int64_t* n_elem, int64_t* n_dof, int* p, int* q) {
+  if (!m) return fail(HX_ERR_ARG, "mesh is NULL");
+  if (n_elem) *n_elem = m->E;
+  if (n_dof) *n_dof = m->n_dof;
+  if (p) *p = m->p;
+  if (q) *q = m->q;
+  return HX_OK;
+}
+
+hx_status hx_mesh_qpoint_coords(const hx_mesh* m, double* xyz, void* stream) {
+  if (!m || !xyz) return fail(HX_ERR_ARG, "NULL argument");
+  HX_TRY(hx_launch_qpoint_coords(m->T, m->E, m->X8, xyz, (cudaStream_t)stream), "qpoint coords");
+  return HX_OK;
+}
+
+hx_status hx_mesh_node_coords(const hx_mesh* m, double* xyz, void* stream) {
+  if (!m || !xyz) return fail(HX_ERR_ARG, "NULL argument");
+  HX_TRY(hx_launch_node_coords(m->T, m->n_dof, m->off, m->idx, m->X8, xyz, (cudaStream_t)stream), "node coords");
+  return HX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// operator
+// ---------------------------------------------------------------------------
+namespace {
+
+HxApplyArgs apply_args(const hx_op* op, const double* x, int constrained, const int* done) {
+  const hx_mesh* m = op->mesh;
+  HxApplyArgs a;
+  a.E = m->E;
+  a.R = m->R;
+  a.x = x;
+  a.yE = op->yE;
+  a.factors = op->factors;
+  a.X8 = m->X8;
+  a.nu_q = op->nu_q;
+  a.alpha = op->alpha;
+  a.nu = op->nu;
+  a.constrained = constrained;
+  a.done = done;
+  return a;
+}
+
+cudaError_t element_apply(const hx_op* op, const double* x, int constrained, const int* done, cudaStream_t s) {
+  const HxApplyArgs a = apply_args(op, x, constrained, done);
+  return apply_launcher(op->mesh->p)(op->mesh->T, a, op->geom, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void hx_op_destroy(hx_op* op) {
+  if (!op) return;
+  if (op->graph) cudaGraphExecDestroy(op->graph);
+  if (op->ev) cudaEventDestroy(op->ev);
+  if (op->stream) cudaStreamDestroy(op->stream);
+  if (op->st_host) cudaFreeHost(op->st_host);
+  dfree(op->factors);
+  dfree(op->nu_q);
+  dfree(op->yE);
+  dfree(op->diag);
+  dfree(op->x);
+  dfree(op->r);
+  dfree(op->p);
+  dfree(op->Ap);
+  dfree(op->dinv);
+  dfree(op->partial);
+  dfree(op->hb);
+  dfree(op->hx);
+  dfree(op->scalars);
+  dfree(op->counters);
+  dfree(op->st);
+  if (op->mesh) op->mesh->n_ops -= 1;
+  delete op;
+}
+
+hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, int geom_mode, void* stream,
+                       hx_op** out) {
+  if (!out) return fail(HX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!m) return fail(HX_ERR_ARG, "mesh is NULL");
+  if (geom_mode != HX_GEOM_STORED && geom_mode != HX_GEOM_ONTHEFLY) return fail(HX_ERR_ARG, "bad geom_mode");
+  cudaStream_t s = (cudaStream_t)stream;
+  hx_op* op = new (std::nothrow) hx_op();
+  if (!op) return fail(HX_ERR_OOM, "host allocation failed");
+  op->mesh = m;
+  m->n_ops += 1;
+  op->alpha = alpha;
+  op->nu = nu;
+  op->geom = geom_mode;
+  const long long Q3 = (long long)m->q * m->q * m->q;
+  int* bad = nullptr;
+  double* tmp = nullptr;
+  hx_status st = HX_OK;
+  int nbad = 0;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((st = dalloc(&op->yE, (size_t)m->E * m->N3, "E-vector"))) break;
+    if ((st = dalloc(&op->diag, (size_t)m->n_dof, "diagonal"))) break;
+    if ((st = dalloc(&bad, 1, "flag"))) break;
+    if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+    if (geom_mode == HX_GEOM_STORED) {
+      if ((st = dalloc(&op->factors, (size_t)m->E * 7 * Q3, "geometric factors"))) break;
+      e = hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s);
+      if (e != cudaSuccess) { st = cuda_fail(e, "geometry kernel"); break; }
+    } else {
+      if (nu_q) {
+        if ((st = dalloc(&op->nu_q, (size_t)m->E * Q3, "nu field"))) break;
+        e = cudaMemcpyAsync(op->nu_q, nu_q, sizeof(double) * m->E * Q3, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "nu copy"); break; }
+      }
+      // detJ check through the factor kernel, a bounded slab of elements at a time
+      const long long chunk = 65536;
+      if ((st = dalloc(&tmp, (size_t)std::min(chunk, m->E) * 7 * Q3, "detJ check"))) break;
+      for (long long e0 = 0; e0 < m->E && e == cudaSuccess; e0 += chunk) {
+        const long long ne = std::min(chunk, m->E - e0);
+        e = hx_launch_geometry(m->T, ne, m->X8 + e0 * 24, nullptr, 1.0, 1.0, tmp, bad, s);
+      }
+      if (e != cudaSuccess) { st = cuda_fail(e, "detJ check"); break; }
+    }
+    // diagonal: element diagonals -> assembled L-vector
+    HxDiagArgs d;
+    d.E = m->E;
+    d.factors = op->factors;
+    d.X8 = m->X8;
+    d.nu_q = op->nu_q;
+    d.alpha = alpha;
+    d.nu = nu;
+    d.dE = op->yE;
+    e = diag_launcher(m->p)(m->T, d, geom_mode, s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "diagonal kernel"); break; }
+    e = hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "diagonal assembly"); break; }
+    e = cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "operator setup"); break; }
+    if (nbad > 0) st = fail(HX_ERR_INVALID_MESH, "detJ <= 0 at %d quadrature points", nbad);
+  } while (0);
+  dfree(bad);
+  dfree(tmp);
+  if (st != HX_OK) {
+    hx_op_destroy(op);
+    return st;
+  }
+  *out = op;
+  return HX_OK;
+}
+
+hx_status hx_op_info(const hx_op* op, int64_t* n_elem, int64_t* n_dof, int* p, int* q) {
+  if (!op) return fail(HX_ERR_ARG, "op is NULL");
+  return hx_mesh_info(op->mesh, n_elem, n_dof, p, q);
+}
+
+hx_status hx_op_apply(hx_op* op, const double* x, double* y, int constrained, void* stream) {
+  if (!op || !x || !y) return fail(HX_ERR_ARG, "NULL argument");
+  if (x == y) return fail(HX_ERR_ARG, "x and y must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  const hx_mesh* m = op->mesh;
+  HX_TRY(element_apply(op, x, constrained, nullptr, s), "element kernel");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, constrained, x, 0.0, y, s), "assembly");
+  return HX_OK;
+}
+
+hx_status hx_op_diagonal(hx_op* op, double* diag, int constrained, void* stream) {
+  if (!op || !diag) return fail(HX_ERR_ARG, "NULL argument");
+  HX_TRY(hx_launch_masked_copy(op->mesh->n_dof, op->diag, op->mesh->dir, constrained, 1.0, diag,
+                               (cudaStream_t)stream),
+         "diagonal copy");
+  return HX_OK;
+}
+
+hx_status hx_op_load_vector(hx_op* op, const double* f_q, double* b, void* stream) {
+  if (!op || !f_q || !b) return fail(HX_ERR_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const hx_mesh* m = op->mesh;
+  HxLoadArgs a;
+  a.E = m->E;
+  a.X8 = m->X8;
+  a.fq = f_q;
+  a.yE = op->yE;
+  HX_TRY(load_launcher(m->p)(m->T, a, s), "load kernel");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, b, s), "assembly");
+  return HX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Jacobi-PCG
+// ---------------------------------------------------------------------------
+namespace {
+
+HxCgBuffers cg_buffers(const hx_op* op) {
+  const hx_mesh* m = op->mesh;
+  HxCgBuffers b;
+  b.n = m->n_dof;
+  b.off = m->off;
+  b.idx = m->idx;
+  b.dir = m->dir;
+  b.x = op->x;
+  b.r = op->r;
+  b.p = op->p;
+  b.Ap = op->Ap;
+  b.dinv = op->dinv;
+  b.yE = op->yE;
+  b.partial = op->partial;
+  b.st = op->st;
+  return b;
+}
+
+hx_status ensure_solver(hx_op* op) {
+  if (op->st) return HX_OK;
+  const long long n = op->mesh->n_dof;
+  hx_status s;
+  if ((s = dalloc(&op->x, n, "cg x")) || (s = dalloc(&op->r, n, "cg r")) || (s = dalloc(&op->p, n, "cg p")) ||
+      (s = dalloc(&op->Ap, n, "cg Ap")) || (s = dalloc(&op->dinv, n, "cg dinv")) ||
+      (s = dalloc(&op->partial, 2 * HX_RED_BLOCKS, "cg partials")) || (s = dalloc(&op->scalars, 2, "scalars")) ||
+      (s = dalloc(&op->counters, 2, "counters")) || (s = dalloc(&op->st, 1, "cg state")))
+    return s;
+  HX_TRY(cudaMallocHost((void**)&op->st_host, sizeof(HxCgState)), "pinned state");
+  HX_TRY(cudaStreamCreateWithFlags(&op->stream, cudaStreamNonBlocking), "solver stream");
+  HX_TRY(cudaEventCreateWithFlags(&op->ev, cudaEventDisableTiming), "solver event");
+  HX_TRY(cudaMemsetAsync(op->st, 0, sizeof(HxCgState), op->stream), "state init");
+  HX_TRY(cudaMemsetAsync(op->counters, 0, 2 * sizeof(unsigned int), op->stream), "counter init");
+  HX_TRY(hx_launch_dinv(n, op->diag, op->mesh->dir, op->dinv, op->stream), "dinv");
+  return HX_OK;
+}
+
+// One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
+cudaError_t cg_iteration(const hx_op* op, cudaStream_t s) {
+  const HxCgBuffers b = cg_buffers(op);
+  cudaError_t e = element_apply(op, op->p, 1, &op->st->done, s);
+  if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
+  if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
+  if (e == cudaSuccess) e = hx_launch_cg_direction(b, s);
+  return e;
+}
+
+constexpr int kChunk = 16;  // CG iterations per graph launch (finished iterations exit at once)
+
+void ensure_graph(hx_op* op) {
+  if (op->graph || op->graph_failed) return;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(op->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) e = cg_iteration(op, op->stream);
+    cudaError_t e2 = cudaStreamEndCapture(op->stream, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&op->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    op->graph = nullptr;
+    op->graph_failed = true;  // fall back to direct launches of the same kernels
+  }
+}
+
+hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int max_it, int use_x0,
+                       cudaStream_t user, hx_solve_info* info) {
+  const hx_mesh* m = op->mesh;
+  hx_status s = ensure_solver(op);
+  if (s) return s;
+  ensure_graph(op);
+  cudaStream_t st = op->stream;
+  // order after the caller's prior work on `user`
+  HX_TRY(cudaEventRecord(op->ev, user), "event record");
+  HX_TRY(cudaStreamWaitEvent(st, op->ev, 0), "stream wait");
+  const HxCgBuffers buf = cg_buffers(op);
+  HX_TRY(hx_launch_cg_init(buf, b, use_x0 ? x : nullptr, rtol, max_it, st), "cg init");
+  if (use_x0) {
+    HX_TRY(element_apply(op, op->x, 1, nullptr, st), "cg x0 apply");
+    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "cg x0 assembly");
+    HX_TRY(hx_launch_cg_residual(buf, st), "cg residual");
+  }
+  HX_TRY(hx_launch_cg_start(buf, st), "cg start");
+  for (;;) {
+    HX_TRY(cudaMemcpyAsync(op->st_host, op->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
+    HX_TRY(cudaStreamSynchronize(st), "solver sync");
+    if (op->st_host->done) break;
+    if (op->graph) {
+      HX_TRY(cudaGraphLaunch(op->graph, st), "graph launch");
+    } else {
+      for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration(op, st), "cg iteration");
+    }
+  }
+  const HxCgState cs = *op->st_host;
+  // true residual ||P b - A_c x|| with one extra apply
+  HX_TRY(element_apply(op, op->x, 1, nullptr, st), "residual apply");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "residual assembly");
+  HX_TRY(hx_launch_resnorm(m->n_dof, b, op->Ap, m->dir, op->partial, op->counters, op->scalars, st), "residual norm");
+  double rn2 = 0.0;
+  HX_TRY(cudaMemcpyAsync(&rn2, op->scalars, sizeof(double), cudaMemcpyDeviceToHost, st), "residual read");
+  HX_TRY(cudaMemcpyAsync(x, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, st), "solution copy");
+  HX_TRY(cudaStreamSynchronize(st), "solver sync");
+  const double bn = std::sqrt(cs.bb);
+  hx_solve_info inf;
+  inf.iterations = cs.iter;
+  inf.status = cs.status;
+  inf.b_norm = bn;
+  inf.rel_residual = bn > 0 ? std::sqrt(cs.rr) / bn : 0.0;
+  inf.true_rel_residual = bn > 0 ? std::sqrt(rn2) / bn : std::sqrt(rn2);
+  if (info) *info = inf;
+  if (cs.status == HX_ERR_NOT_CONVERGED)
+    return fail(HX_ERR_NOT_CONVERGED, "not converged in %d iterations (rel. residual %.3e)", cs.iter, inf.rel_residual);
+  if (cs.status == HX_ERR_BREAKDOWN) return fail(HX_ERR_BREAKDOWN, "CG breakdown at iteration %d", cs.iter);
+  return HX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hx_status hx_solve_pcg(hx_op* op, const double* b, double* x, double rtol, int max_it, int use_x0, void* stream,
+                       hx_solve_info* info) {
+  if (!op || !b || !x) return fail(HX_ERR_ARG, "NULL argument");
+  if (!(rtol >= 0.0) || max_it < 0) return fail(HX_ERR_ARG, "rtol must be >= 0 and max_it >= 0");
+  return solve_device(op, b, x, rtol, max_it, use_x0, (cudaStream_t)stream, info);
+}
+
+hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, double rtol, int max_it, int use_x0,
+                            hx_solve_info* info) {
+  if (!op || !b_host || !x_host) return fail(HX_ERR_ARG, "NULL argument");
+  if (!(rtol >= 0.0) || max_it < 0) return fail(HX_ERR_ARG, "rtol must be >= 0 and max_it >= 0");
+  const long long n = op->mesh->n_dof;
+  hx_status s = ensure_solver(op);
+  if (s) return s;
+  if (!op->hb) {
+    if ((s = dalloc(&op->hb, n, "staging b")) || (s = dalloc(&op->hx, n, "staging x"))) return s;
+  }
+  HX_TRY(cudaMemcpyAsync(op->hb, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, op->stream), "b upload");
+  if (use_x0)
+    HX_TRY(cudaMemcpyAsync(op->hx, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, op->stream), "x0 upload");
+  hx_status r = solve_device(op, op->hb, op->hx, rtol, max_it, use_x0, op->stream, info);
+  if (r != HX_OK && r != HX_ERR_NOT_CONVERGED && r != HX_ERR_BREAKDOWN) return r;
+  const std::string msg = g_err;
+  HX_TRY(cudaMemcpyAsync(x_host, op->hx, sizeof(double) * n, cudaMemcpyDeviceToHost, op->stream), "x download");
+  HX_TRY(cudaStreamSynchronize(op->stream), "solver sync");
+  g_err = msg;
+  return r;
+}
+
+}  // extern "C"

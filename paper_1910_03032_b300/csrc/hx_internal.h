@@ -1,0 +1,122 @@
+// Internal declarations shared by the C ABI (hx_capi.cu) and the kernel
+// translation units.  Not part of the public interface (see include/hx.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hx_tables.h"
+
+// Arguments of the element-operator kernel (gather -> contractions ->
+// pointwise -> transposed contractions -> E-vector).
+struct HxApplyArgs {
+  long long E;            // number of elements
+  const int* R;           // [E][n^3] restriction; g >= 0 free DoF, -(g+1) Dirichlet DoF
+  const double* x;        // L-vector input
+  double* yE;             // [E][n^3] E-vector output
+  const double* factors;  // stored geometry: [E][7][q^3] (m, G00, G01, G02, G11, G12, G22)
+  const double* X8;       // [E][8][3] element corner coordinates (on-the-fly geometry)
+  const double* nu_q;     // [E][q^3] per-point viscosity or null (on-the-fly geometry)
+  double alpha, nu;       // Helmholtz coefficients (on-the-fly geometry)
+  int constrained;        // 1: Dirichlet DoFs of x read as zero
+  const int* done;        // optional device flag: kernel returns at once when *done != 0
+};
+
+// Arguments of the diagonal kernel (sum-factorized diag of the element matrices).
+struct HxDiagArgs {
+  long long E;
+  const double* factors;  // stored geometry or null
+  const double* X8;
+  const double* nu_q;
+  double alpha, nu;
+  double* dE;             // [E][n^3] element diagonals
+};
+
+// Arguments of the load-vector kernel: bE = B^T (w detJ f) per element.
+struct HxLoadArgs {
+  long long E;
+  const double* X8;
+  const double* fq;       // [E][q^3] source values at the quadrature points
+  double* yE;
+};
+
+enum { HX_KGEOM_STORED = 0, HX_KGEOM_ONTHEFLY = 1 };
+
+// Per-order launchers (one translation unit per p; q in {p+1, p+2}).
+typedef cudaError_t (*hx_apply_launcher)(const HxTables&, const HxApplyArgs&, int geom, cudaStream_t);
+typedef cudaError_t (*hx_diag_launcher)(const HxTables&, const HxDiagArgs&, int geom, cudaStream_t);
+typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cudaStream_t);
+
+#define HX_DECLARE_ORDER(P)                                                                        \
+  cudaError_t hx_launch_apply_p##P(const HxTables&, const HxApplyArgs&, int, cudaStream_t);       \
+  cudaError_t hx_launch_diag_p##P(const HxTables&, const HxDiagArgs&, int, cudaStream_t);         \
+  cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);
+HX_DECLARE_ORDER(1)
+HX_DECLARE_ORDER(2)
+HX_DECLARE_ORDER(3)
+HX_DECLARE_ORDER(4)
+HX_DECLARE_ORDER(5)
+HX_DECLARE_ORDER(6)
+HX_DECLARE_ORDER(7)
+HX_DECLARE_ORDER(8)
+
+// ---- order-independent kernels (hx_kernels.cu) ----
+cudaError_t hx_launch_geometry(const HxTables& T, long long E, const double* X8, const double* nu_q,
+                               double alpha, double nu, double* factors, int* bad_count, cudaStream_t s);
+cudaError_t hx_launch_qpoint_coords(const HxTables& T, long long E, const double* X8, double* xyz,
+                                    cudaStream_t s);
+cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int* off, const int* idx,
+                                  const double* X8, double* xyz, cudaStream_t s);
+// y[g] = sum_{k in off[g]..off[g+1]} yE[idx[k]]; with `constrained`, Dirichlet rows
+// (dir[g] != 0) take x[g] (x non-null) or dir_const.
+cudaError_t hx_launch_assemble(long long n_dof, const int* off, const int* idx, const double* yE,
+                               const unsigned char* dir, int constrained, const double* x,
+                               double dir_const, double* y, cudaStream_t s);
+
+// Jacobi-PCG state (device); scalars kept on the device between kernels.
+struct HxCgState {
+  double rz;        // (r, z)
+  double alpha;     // step
+  double beta;      // direction update
+  double bb;        // ||P b||^2
+  double rr;        // ||r||^2 of the last update
+  double tol2;      // rtol^2 * bb
+  int iter;         // completed iterations
+  int max_it;
+  int done;         // 0 running, 1 finished
+  int status;       // HX_OK / HX_ERR_NOT_CONVERGED / HX_ERR_BREAKDOWN
+  unsigned int count[4];  // last-block counters, one per reduction kernel
+};
+
+#define HX_RED_BLOCKS 1184  // 8 x 148 SMs: fixed grid of every reduction kernel
+#define HX_RED_THREADS 256
+
+struct HxCgBuffers {
+  long long n;
+  const int* off;
+  const int* idx;
+  const unsigned char* dir;
+  double* x;
+  double* r;
+  double* p;
+  double* Ap;
+  double* dinv;
+  double* yE;
+  double* partial;  // [2 * HX_RED_BLOCKS]
+  HxCgState* st;
+};
+
+cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s);
+cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
+                                  double value, double* dst, cudaStream_t s);
+cudaError_t hx_launch_cg_init(const HxCgBuffers& b, const double* bvec, const double* x0, double rtol, int max_it,
+                              cudaStream_t s);
+cudaError_t hx_launch_cg_residual(const HxCgBuffers& b, cudaStream_t s);
+cudaError_t hx_launch_cg_start(const HxCgBuffers& b, cudaStream_t s);
+cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffers& b, cudaStream_t s);
+cudaError_t hx_launch_cg_update(const HxCgBuffers& b, cudaStream_t s);
+cudaError_t hx_launch_cg_direction(const HxCgBuffers& b, cudaStream_t s);
+cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,
+                          double* out, cudaStream_t s);
+cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,
+                              unsigned int* counter, double* out, cudaStream_t s);

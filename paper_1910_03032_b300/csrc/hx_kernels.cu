@@ -1,0 +1,400 @@
+// Order-independent kernels: geometric factors (setup), point and node
+// coordinates, the atomic-free E-to-L assembly, and the fused Jacobi-PCG
+// vector kernels with deterministic reductions.
+#include <cuda_runtime.h>
+
+#include "hx_element.cuh"
+#include "hx_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum in a fixed order (deterministic); result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = (lane < NT / 32) ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// Last-block completion: every block writes NV partial sums to partial[v * G + block];
+// the block that finishes last reduces them in a fixed order into out[v].
+// Returns true in the last block (all threads), with out[] written by thread 0.
+template <int NV>
+__device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsigned int* counter, double (&out)[NV]) {
+  __shared__ double red[32];
+  __shared__ bool is_last;
+  const int G = gridDim.x;
+  for (int k = 0; k < NV; ++k) {
+    const double s = block_sum<HX_RED_THREADS>(v[k], red);
+    if (threadIdx.x == 0) partial[k * G + blockIdx.x] = s;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    is_last = (ticket == (unsigned int)G - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < G; b += HX_RED_THREADS) s += __ldcg(partial + k * G + b);
+    s = block_sum<HX_RED_THREADS>(s, red);
+    if (threadIdx.x == 0) out[k] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// geometry setup: factors[e][c][pt], c = (m, G00, G01, G02, G11, G12, G22)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) geometry_kernel(const __grid_constant__ HxTables T, long long E, int EB,
+                                                             const double* __restrict__ X8,
+                                                             const double* __restrict__ nu_q, double alpha, double nu,
+                                                             double* __restrict__ factors, int* bad) {
+  extern __shared__ double cf[];  // EB x 24
+  const int q = T.q, Q3 = q * q * q;
+  const long long e0 = (long long)blockIdx.x * EB;
+  for (int el = threadIdx.x; el < EB; el += blockDim.x) {
+    const long long e = e0 + el;
+    double x8[24];
+    for (int c = 0; c < 24; ++c) x8[c] = (e < E) ? X8[e * 24 + c] : 0.0;
+    hx::trilinear_coeffs(x8, cf + el * 24);
+  }
+  __syncthreads();
+  int nbad = 0;
+  for (int t = threadIdx.x; t < EB * Q3; t += blockDim.x) {
+    const int el = t / Q3, pt = t - el * Q3;
+    const long long e = e0 + el;
+    if (e >= E) continue;
+    const int iq = pt % q, jq = (pt / q) % q, kq = pt / (q * q);
+    double j0[3], j1[3], j2[3], f[7];
+    hx::trilinear_jacobian(cf + el * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
+    const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
+    const double nuv = nu_q ? nu_q[e * Q3 + pt] : nu;
+    const double det = hx::point_factors(j0, j1, j2, alpha * w, nuv * w, f);
+    if (!(det > 0.0)) ++nbad;
+    for (int c = 0; c < 7; ++c) factors[(e * 7 + c) * Q3 + pt] = f[c];
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+__global__ void __launch_bounds__(kThreads) qpoint_kernel(const __grid_constant__ HxTables T, long long E, int EB,
+                                                           const double* __restrict__ X8, double* __restrict__ xyz) {
+  extern __shared__ double cf[];
+  const int q = T.q, Q3 = q * q * q;
+  const long long e0 = (long long)blockIdx.x * EB;
+  for (int el = threadIdx.x; el < EB; el += blockDim.x) {
+    const long long e = e0 + el;
+    double x8[24];
+    for (int c = 0; c < 24; ++c) x8[c] = (e < E) ? X8[e * 24 + c] : 0.0;
+    hx::trilinear_coeffs(x8, cf + el * 24);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < EB * Q3 * 3; t += blockDim.x) {
+    const int el = t / (Q3 * 3), r = t - el * Q3 * 3;
+    const int pt = r / 3, d = r - pt * 3;
+    const long long e = e0 + el;
+    if (e >= E) continue;
+    const int iq = pt % q, jq = (pt / q) % q, kq = pt / (q * q);
+    xyz[(e * Q3) * 3 + r] = hx::trilinear_point(cf + el * 24, d, T.xq[iq], T.xq[jq], T.xq[kq]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) node_kernel(const __grid_constant__ HxTables T, long long n_dof,
+                                                         const int* __restrict__ off, const int* __restrict__ idx,
+                                                         const double* __restrict__ X8, double* __restrict__ xyz) {
+  const int n = T.p + 1, N3 = n * n * n;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n_dof; g += (long long)gridDim.x * blockDim.x) {
+    const int v = idx[off[g]];  // first (element, node) holding g: deterministic owner
+    const long long e = v / N3;
+    const int l = v - (int)(e * N3);
+    const int i = l % n, j = (l / n) % n, k = l / (n * n);
+    double x8[24], cf[24];
+    for (int c = 0; c < 24; ++c) x8[c] = X8[e * 24 + c];
+    hx::trilinear_coeffs(x8, cf);
+    for (int d = 0; d < 3; ++d) xyz[g * 3 + d] = hx::trilinear_point(cf, d, T.xn[i], T.xn[j], T.xn[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// E -> L assembly through the transpose map (atomic-free, fixed summation order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double gather_sum(long long g, const int* __restrict__ off, const int* __restrict__ idx,
+                                             const double* __restrict__ yE) {
+  const int k0 = __ldg(off + g), k1 = __ldg(off + g + 1);
+  double s = 0.0;
+  for (int k = k0; k < k1; ++k) s += __ldg(yE + __ldg(idx + k));
+  return s;
+}
+
+#define HX_GRID_STRIDE(g, n) \
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (n); g += (long long)gridDim.x * blockDim.x)
+
+__global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const int* __restrict__ off,
+                                                             const int* __restrict__ idx, const double* __restrict__ yE,
+                                                             const unsigned char* __restrict__ dir, int constrained,
+                                                             const double* __restrict__ x, double dir_const,
+                                                             double* __restrict__ y) {
+  HX_GRID_STRIDE(g, n) {
+    double s;
+    if (constrained && dir[g]) s = x ? x[g] : dir_const;
+    else s = gather_sum(g, off, idx, yE);
+    y[g] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) dinv_kernel(long long n, const double* __restrict__ diag,
+                                                         const unsigned char* __restrict__ dir, double* __restrict__ dinv) {
+  HX_GRID_STRIDE(g, n) { dinv[g] = dir[g] ? 1.0 : 1.0 / diag[g]; }
+}
+
+__global__ void __launch_bounds__(kThreads) masked_copy_kernel(long long n, const double* __restrict__ src,
+                                                                const unsigned char* __restrict__ dir, int constrained,
+                                                                double value, double* __restrict__ dst) {
+  HX_GRID_STRIDE(g, n) { dst[g] = (constrained && dir[g]) ? value : src[g]; }
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi-PCG (Sec. 5.3: CG on the SPD Helmholtz / Poisson systems), fused passes
+// ---------------------------------------------------------------------------
+// x = P x0 (or 0), r = P b; sums ||P b||^2.
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffers B, const double* __restrict__ b,
+                                                                  const double* __restrict__ x0, double rtol, int max_it) {
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, B.n) {
+    const bool d = B.dir[g];
+    const double bg = d ? 0.0 : b[g];
+    B.r[g] = bg;
+    B.x[g] = (x0 && !d) ? x0[g] : 0.0;
+    acc[0] += bg * bg;
+  }
+  double out[1];
+  if (last_block_reduce<1>(acc, B.partial, &B.st->count[0], out) && threadIdx.x == 0) {
+    HxCgState* s = B.st;
+    s->bb = out[0];
+    s->tol2 = rtol * rtol * out[0];
+    s->iter = 0;
+    s->max_it = max_it;
+    s->done = 0;
+    s->status = 0;
+    s->rz = s->alpha = s->beta = 0.0;
+    s->rr = out[0];
+  }
+}
+
+// r -= A_c x (after an apply of the initial guess into Ap).
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffers B) {
+  HX_GRID_STRIDE(g, B.n) { B.r[g] -= B.Ap[g]; }
+}
+
+// z = D^-1 r, p = z; rz = (r, z), rr = (r, r); finishes at once if rr <= tol^2 ||b||^2.
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffers B) {
+  double acc[2] = {0.0, 0.0};
+  HX_GRID_STRIDE(g, B.n) {
+    const double r = B.r[g], z = B.dinv[g] * r;
+    B.p[g] = z;
+    acc[0] += r * z;
+    acc[1] += r * r;
+  }
+  double out[2];
+  if (last_block_reduce<2>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
+    HxCgState* s = B.st;
+    s->rz = out[0];
+    s->rr = out[1];
+    if (!isfinite(out[0]) || !isfinite(out[1])) {
+      s->status = -6;  // HX_ERR_BREAKDOWN
+      s->done = 1;
+    } else if (out[1] <= s->tol2) {
+      s->done = 1;
+    }
+  }
+}
+
+// Ap = assemble(yE) with Dirichlet rows Ap = p; pAp = (p, Ap); alpha = rz / pAp.
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuffers B) {
+  if (*(volatile int*)&B.st->done) return;
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, B.n) {
+    const double pg = B.p[g];
+    const double ap = B.dir[g] ? pg : gather_sum(g, B.off, B.idx, B.yE);
+    B.Ap[g] = ap;
+    acc[0] += pg * ap;
+  }
+  double out[1];
+  if (last_block_reduce<1>(acc, B.partial, &B.st->count[2], out) && threadIdx.x == 0) {
+    HxCgState* s = B.st;
+    if (!(out[0] > 0.0) || !isfinite(out[0])) {
+      s->status = -6;  // HX_ERR_BREAKDOWN
+      s->done = 1;
+    } else {
+      s->alpha = s->rz / out[0];
+    }
+  }
+}
+
+// x += alpha p, r -= alpha Ap, z = D^-1 r; rr = (r, r), rz' = (r, z); convergence test.
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffers B) {
+  if (*(volatile int*)&B.st->done) return;
+  const double a = B.st->alpha;
+  double acc[2] = {0.0, 0.0};
+  HX_GRID_STRIDE(g, B.n) {
+    const double pg = B.p[g];
+    B.x[g] += a * pg;
+    const double r = B.r[g] - a * B.Ap[g];
+    B.r[g] = r;
+    acc[0] += r * r;
+    acc[1] += r * (B.dinv[g] * r);
+  }
+  double out[2];
+  if (last_block_reduce<2>(acc, B.partial, &B.st->count[3], out) && threadIdx.x == 0) {
+    HxCgState* s = B.st;
+    s->iter += 1;
+    s->rr = out[0];
+    if (!isfinite(out[0]) || !isfinite(out[1])) {
+      s->status = -6;
+      s->done = 1;
+    } else if (out[0] <= s->tol2) {
+      s->done = 1;
+    } else if (s->iter >= s->max_it) {
+      s->status = -5;  // HX_ERR_NOT_CONVERGED
+      s->done = 1;
+    } else {
+      s->beta = out[1] / s->rz;
+      s->rz = out[1];
+    }
+  }
+}
+
+// p = D^-1 r + beta p.
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffers B) {
+  if (*(volatile int*)&B.st->done) return;
+  const double beta = B.st->beta;
+  HX_GRID_STRIDE(g, B.n) { B.p[g] = B.dinv[g] * B.r[g] + beta * B.p[g]; }
+}
+
+__global__ void __launch_bounds__(HX_RED_THREADS) dot_kernel(long long n, const double* __restrict__ a,
+                                                              const double* __restrict__ c, double* partial,
+                                                              unsigned int* counter, double* out) {
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, n) { acc[0] += a[g] * c[g]; }
+  double res[1];
+  if (last_block_reduce<1>(acc, partial, counter, res) && threadIdx.x == 0) *out = res[0];
+}
+
+// out = sum_g (dir[g] ? 0 : b[g] - Ax[g])^2
+__global__ void __launch_bounds__(HX_RED_THREADS) resnorm_kernel(long long n, const double* __restrict__ b,
+                                                                  const double* __restrict__ Ax,
+                                                                  const unsigned char* __restrict__ dir,
+                                                                  double* partial, unsigned int* counter, double* out) {
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, n) {
+    const double r = dir[g] ? 0.0 : b[g] - Ax[g];
+    acc[0] += r * r;
+  }
+  double res[1];
+  if (last_block_reduce<1>(acc, partial, counter, res) && threadIdx.x == 0) *out = res[0];
+}
+
+unsigned grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 148LL * 16) b = 148LL * 16;
+  return (unsigned)(b > 0 ? b : 1);
+}
+
+}  // namespace
+
+cudaError_t hx_launch_geometry(const HxTables& T, long long E, const double* X8, const double* nu_q, double alpha,
+                               double nu, double* factors, int* bad, cudaStream_t s) {
+  const int Q3 = T.q * T.q * T.q;
+  const int EB = Q3 >= 1024 ? 1 : 1024 / Q3;
+  const long long blocks = (E + EB - 1) / EB;
+  if (blocks == 0) return cudaSuccess;
+  geometry_kernel<<<(unsigned)blocks, kThreads, EB * 24 * sizeof(double), s>>>(T, E, EB, X8, nu_q, alpha, nu, factors, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_qpoint_coords(const HxTables& T, long long E, const double* X8, double* xyz, cudaStream_t s) {
+  const int Q3 = T.q * T.q * T.q;
+  const int EB = Q3 >= 1024 ? 1 : 1024 / Q3;
+  const long long blocks = (E + EB - 1) / EB;
+  if (blocks == 0) return cudaSuccess;
+  qpoint_kernel<<<(unsigned)blocks, kThreads, EB * 24 * sizeof(double), s>>>(T, E, EB, X8, xyz);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int* off, const int* idx, const double* X8,
+                                  double* xyz, cudaStream_t s) {
+  node_kernel<<<grid_for(n_dof), kThreads, 0, s>>>(T, n_dof, off, idx, X8, xyz);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_assemble(long long n, const int* off, const int* idx, const double* yE, const unsigned char* dir,
+                               int constrained, const double* x, double dir_const, double* y, cudaStream_t s) {
+  assemble_kernel<<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, dir_const, y);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s) {
+  dinv_kernel<<<grid_for(n), kThreads, 0, s>>>(n, diag, dir, dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
+                                  double value, double* dst, cudaStream_t s) {
+  masked_copy_kernel<<<grid_for(n), kThreads, 0, s>>>(n, src, dir, constrained, value, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_cg_init(const HxCgBuffers& b, const double* bvec, const double* x0, double rtol, int max_it,
+                              cudaStream_t s) {
+  cg_init_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b, bvec, x0, rtol, max_it);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_cg_residual(const HxCgBuffers& b, cudaStream_t s) {
+  cg_residual_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_cg_start(const HxCgBuffers& b, cudaStream_t s) {
+  cg_start_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffers& b, cudaStream_t s) {
+  cg_assemble_pap_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_cg_update(const HxCgBuffers& b, cudaStream_t s) {
+  cg_update_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_cg_direction(const HxCgBuffers& b, cudaStream_t s) {
+  cg_direction_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,
+                          double* out, cudaStream_t s) {
+  dot_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, a, c, partial, counter, out);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,
+                              unsigned int* counter, double* out, cudaStream_t s) {
+  resnorm_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, b, Ax, dir, partial, counter, out);
+  return cudaGetLastError();
+}

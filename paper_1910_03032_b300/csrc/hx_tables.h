@@ -1,0 +1,49 @@
+// 1D tables of the Q_p reference element, passed to every kernel by value
+// (kernel parameters live in the constant bank, so a fully unrolled
+// contraction reads its coefficients as constant-bank operands).
+//
+// Notation (Sec. 3.1): n = p + 1 Gauss-Lobatto nodes, q Gauss points.
+//   B  (q x n)  B[a][j]  = phi_j(xi_a)                       Eq. (B1D)
+//   D  (q x n)  D[a][j]  = phi_j'(xi_a)                      Eq. (D1D)
+//   Dh (q x q)  Dh[a][b] = psi_b'(xi_a), psi_b the Lagrange polynomials of
+//               the Gauss points; D = Dh B holds exactly for q >= n, so the
+//               gradient tensor of Eq. (tensorGradient) can be applied as
+//               "interpolate with B, then differentiate at the points".
+// Even-odd folded forms (the symmetry noted in Sec. 6): for a 1D operator S
+// (M x L) with S[M-1-a][L-1-b] = sigma S[a][b]:
+//   Se[a][b] = (S[a][b] + S[a][L-1-b]) / 2   (b < L/2),  Se[a][L/2] = S[a][L/2] for odd L
+//   So[a][b] = (S[a][b] - S[a][L-1-b]) / 2   (b < L/2)
+// for a < ceil(M/2); row stride ceil(L/2) for Se and floor(L/2) for So.
+#pragma once
+
+#define HX_PMAX 8
+#define HX_QMAX 10
+#define HX_NMAX (HX_PMAX + 1)
+#define HX_H(x) (((x) + 1) / 2)
+
+struct HxTables {
+  int p, q;
+  // folded B (sigma = +1): M = q, L = n
+  double Be[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
+  double Bo[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
+  // folded B^T (sigma = +1): M = n, L = q
+  double Bte[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
+  double Bto[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
+  // folded Dh (sigma = -1): M = L = q
+  double De[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  double Do[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  // folded Dh^T (sigma = -1)
+  double Dte[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  double Dto[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  // unfolded tables, row-major
+  double B[HX_QMAX * HX_NMAX];
+  double D[HX_QMAX * HX_NMAX];
+  double xq[HX_QMAX];    // Gauss points on [-1, 1]
+  double wq[HX_QMAX];    // Gauss weights
+  double xn[HX_NMAX];    // Gauss-Lobatto nodes
+};
+
+#ifdef __cplusplus
+// Host construction (basis.cpp). Returns 0 on success.
+int hx_build_tables(int p, int q, HxTables* t);
+#endif

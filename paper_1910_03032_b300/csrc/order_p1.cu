@@ -1,0 +1,3 @@
+// Kernels of the order-1 operator (q = 2 and 3).
+#include "hx_element.cuh"
+HX_DEFINE_ORDER(1)
