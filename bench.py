@@ -1,0 +1,427 @@
+"""Benchmark: FP64 matrix-free Q_p Helmholtz operator and Jacobi-PCG on one B300 (per rank).
+
+One step = one pass of the whole hot path on the resident problem:
+  coefficient setup (geometric factors m = alpha w detJ, G = nu w detJ J^-1 J^-T,
+  and the sum-factorized diagonal), then Jacobi-PCG to a 1e-10 relative
+  residual, each iteration one matrix-free apply (gather, sum-factorized
+  contractions, pointwise factors, transposed contractions, atomic-free
+  assembly) plus the fused vector updates; one more apply checks the true
+  residual.
+
+Workload (default): perturbed 96^3 hexahedral mesh of the unit cube, Q_4
+(57,066,625 DoFs), 6^3 Gauss points per element, alpha = 1/dt = 1000,
+nu = 1e-2, homogeneous Dirichlet boundary, manufactured right-hand side
+f = (alpha + 3 pi^2 nu) sin(pi x) sin(pi y) sin(pi z), stored factors.
+
+value = DoF-applies per second: n_dof x (applies per solve) / step time, in
+GDoF/s, summed over ranks (each rank solves its own replica; there is no
+data-path collective).  The JSON line also carries the PCG time, the
+isolated apply throughput, the roofline of the element kernel, the
+end-to-end number through host buffers, the CPU oracle baseline, and the
+SM clocks sampled during the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hx|reference]
+                       [--p P] [--n N] [--geom stored|onthefly] [--sweep]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "Helmholtz apply GDoF/s & PCG time, p=2-8; mixed/batched vs FP64 at 1e-10"
+ALPHA, NU, RTOL = 1000.0, 1e-2, 1e-10
+SWEEP_N = {2: 160, 3: 96, 4: 96, 5: 64, 6: 64, 7: 48, 8: 48}
+HBM_GBS = 6518.0  # measured copy bandwidth of the B300s
+# FP64 peak of the B300: 2 DFMA per clock per SM (a throughput probe measured
+# 565 G DFMA/s at ~1.94 GHz: 1.97 per clock per SM) x 148 SMs x 2032 MHz x 2 flops.
+FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch from
+# an ncu capture, keyed by (p, N, geom); None until a capture of the current kernel exists.
+NCU_TRAFFIC = {}
+
+
+def alg_flops_per_element(p: int, q: int) -> int:
+    """Algorithmic flops of one element apply: the cheaper of the two sum-factorized
+    formulations (B/D-direct, or interpolate then q x q collocated derivative), forward
+    plus transpose, and ~20 flops per point for the stored pointwise factors."""
+    n = p + 1
+    direct = 2 * (4 * q * n ** 3 + 6 * q * q * n * n + 8 * q ** 3 * n)
+    coll = 2 * (2 * (q * n ** 3 + q * q * n * n + q ** 3 * n) + 6 * q ** 4)
+    return min(direct, coll) + 20 * q ** 3
+
+
+def alg_bytes_per_apply(p: int, q: int, E: int, n_dof: int, geom: str) -> int:
+    """Algorithmic minimum HBM bytes of one apply: x in, y out, restriction indices,
+    and the stored factors (7 doubles per point) or 8 vertices per element."""
+    n = p + 1
+    geo = 7 * 8 * q ** 3 * E if geom == "stored" else 24 * 8 * E
+    return 16 * n_dof + 4 * n ** 3 * E + geo
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: one independent problem per rank)
+# ---------------------------------------------------------------------------
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# problem set-up through the library
+# ---------------------------------------------------------------------------
+def make_problem(hx, torch, p: int, N: int, geom: str):
+    q = p + 2
+    V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED)
+    mesh = hx.Mesh.structured(N, N, N, p, q, V)
+    gm = hx.HX_GEOM_STORED if geom == "stored" else hx.HX_GEOM_ONTHEFLY
+    op = hx.Operator(mesh, ALPHA, NU, geom_mode=gm)
+    xq = mesh.qpoint_coords()
+    f = (ALPHA + 3 * math.pi ** 2 * NU) * torch.sin(math.pi * xq[..., 0]) * torch.sin(math.pi * xq[..., 1]) * \
+        torch.sin(math.pi * xq[..., 2])
+    del xq
+    b = op.load_vector(f.contiguous())
+    del f
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return mesh, op, b
+
+
+def time_applies(op, torch, x, reps=20, warm=3):
+    """Average device time of hx_op_apply (element kernel + assembly) with CUDA events on its stream."""
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream()
+    for _ in range(warm):
+        op.apply(x, y, constrained=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        e0.record(s)
+        op.apply(x, y, constrained=True)
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(times)), float(np.mean(times))
+
+
+def run_step(op, b, x):
+    """Coefficient set-up, then a cold-started (x0 = 0) Jacobi-PCG solve into x."""
+    import paper_1910_03032_b300 as hx
+    op.set_coefficients(ALPHA, NU)
+    return hx.hx_solve_pcg(op.handle, b, x, RTOL, 20000, use_x0=False)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample_throughput(p: int, n_apply: int, ns: int):
+    """Oracle DoF-applies per second on an ns^3-element piece of the workload: the
+    oracle builds its explicit element matrices once, then applies them n_apply times."""
+    from oracle import fem
+    q = p + 2
+    V = S.structured_vertices(ns, ns, ns, 0.1, S.DEFAULT_MESH_SEED)
+    om = fem.StructuredMesh(ns, ns, ns, p, q, V, S.structured_elem_vert(ns, ns, ns))
+    t0 = time.perf_counter()
+    op = fem.Operator(om, ALPHA, NU)
+    t1 = time.perf_counter()
+    x = S.random_vector(om.n_dof, S.DEFAULT_VECTOR_SEED)
+    reps = 3
+    for _ in range(reps):
+        op.apply(x, constrained=True)
+    t2 = time.perf_counter()
+    t_setup, t_apply = t1 - t0, (t2 - t1) / reps
+    dofs = om.n_dof
+    t_solve = t_setup + n_apply * t_apply
+    return {"gdofs": dofs * n_apply / t_solve / 1e9, "t_setup": t_setup, "t_apply": t_apply, "n_dof": dofs,
+            "n_elem": om.n_elem}
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if th:
+            return int(max(th))
+    except Exception:
+        pass
+    return len(os.sched_getaffinity(0))
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step = oracle set-up + PCG-length applies on a sample."""
+    if rank != 0:
+        return
+    p = args.p
+    its = args.ref_iterations
+    ns = args.ref_elems
+    for _ in range(args.warmup):
+        oracle_sample_throughput(p, its + 1, ns)
+    vals, times = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_sample_throughput(p, its + 1, ns)
+        times.append(time.perf_counter() - t0)
+        vals.append(r["gdofs"])
+    v = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"{ns}^3 elements of the same p/q/perturbation; explicit element matrices "
+                                   f"built once, then {its + 1} applies (the GPU arm's PCG applies per solve)"},
+        "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    p, N = args.p, args.n
+    return {"workload": f"FP64 Helmholtz alpha*M+nu*K (alpha=1/dt=1000, nu=1e-2) on a perturbed {N}^3 hex mesh, "
+                        f"Q_{p} GLL, q={p + 2} Gauss; coefficient setup + Jacobi-PCG to 1e-10 on the "
+                        f"manufactured RHS", "p": p, "q": p + 2, "mesh": f"{N}^3", "n_dof": (p * N + 1) ** 3,
+            "geometry": args.geom, "l2": "inputs larger than L2 (geometric factors stream from HBM every apply)"}
+
+
+def run_hx(args, world, rank, local):
+    import torch
+    import paper_1910_03032_b300 as hx
+    torch.cuda.set_device(local)
+    p, N = args.p, args.n
+    mesh, op, b = make_problem(hx, torch, p, N, args.geom)
+    n_dof, E, q = mesh.n_dof, mesh.n_elem, mesh.q
+    x = torch.zeros_like(b)
+    # warm-up
+    for _ in range(args.warmup):
+        info = run_step(op, b, x)
+    torch.cuda.synchronize()
+    barrier(world)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    l0 = op.launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.steps):
+            infos.append(run_step(op, b, x))
+        e1.record(s)
+        torch.cuda.synchronize()
+    launches = op.launch_count() - l0
+    barrier(world)
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = reduce_max(t_local, world)
+    applies = sum(i["iterations"] + 1 for i in infos)
+    value = world * n_dof * applies / t / 1e9
+    its = infos[-1]["iterations"]
+
+    # isolated apply and roofline of the element kernel (dominant kernel)
+    t_apply_med, t_apply_mean = time_applies(op, torch, b)
+    flops = alg_flops_per_element(p, q) * E
+    achieved = flops / t_apply_mean / 1e12
+    bytes_alg = alg_bytes_per_apply(p, q, E, n_dof, args.geom)
+    traffic = NCU_TRAFFIC.get((p, N, args.geom))
+
+    # end to end through host buffers (pinned), public API, copies inside the timed region
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros(n_dof, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op.set_coefficients(ALPHA, NU)
+        info_h = hx.hx_solve_pcg_host(op.handle, bh, xh, RTOL, 20000, False)
+    torch.cuda.synchronize()
+    t_e2e = reduce_max(time.perf_counter() - t0, world)
+    e2e = world * n_dof * args.steps * (info_h["iterations"] + 1) / t_e2e / 1e9
+    clocks = clk.summary()
+    del bh, xh
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            # free the device problem first; the oracle runs on the host cores
+            r = oracle_sample_throughput(p, its + 1, args.cpu_elems)
+            cpu = {"value": r["gdofs"], "unit": "GDoF/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"{args.cpu_elems}^3 elements ({r['n_dof']} DoFs) of the same p, q and perturbation: "
+                             f"explicit element matrices built once ({r['t_setup']:.2f} s), then {its + 1} applies "
+                             f"at {r['t_apply']:.3f} s each (the GPU's applies per solve)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "pcg_time_s": t / args.steps, "pcg_iterations": its,
+            "true_rel_residual": infos[-1]["true_rel_residual"],
+            "apply_gdofs": n_dof / t_apply_mean / 1e9, "apply_ms": 1e3 * t_apply_mean,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "kernel": f"apply_kernel<P={p},Q={q}> (+ assembly, timed together)",
+                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 148 SMs x 2032 MHz (derived)",
+                         "alg_flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
+                         "hbm_gbs": bytes_alg / t_apply_mean / 1e9,
+                         "hbm_frac": bytes_alg / t_apply_mean / 1e9 / HBM_GBS},
+            "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n_dof, "d2h_bytes_per_step": 8 * n_dof},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+    del op, mesh, b, x
+    torch.cuda.empty_cache()
+    if rank == 0 and args.sweep:
+        line["sweep"] = run_sweep(hx, torch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_sweep(hx, torch):
+    """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
+    out = []
+    for p in range(2, 9):
+        N = SWEEP_N[p]
+        for geom in ("stored", "onthefly"):
+            mesh, op, b = make_problem(hx, torch, p, N, geom)
+            t_med, t_mean = time_applies(op, torch, b)
+            x = torch.zeros_like(b)
+            run_step(op, b, x)  # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = run_step(op, b, x)
+            torch.cuda.synchronize()
+            t_pcg = time.perf_counter() - t0
+            flops = alg_flops_per_element(p, p + 2) * mesh.n_elem
+            out.append({"p": p, "N": N, "geom": geom, "n_dof": mesh.n_dof, "apply_ms": 1e3 * t_mean,
+                        "apply_gdofs": mesh.n_dof / t_mean / 1e9,
+                        "alg_tflops": flops / t_mean / 1e12, "fp64_frac": flops / t_mean / 1e12 / FP64_PEAK_TFLOPS,
+                        "pcg_s": t_pcg, "pcg_iterations": info["iterations"],
+                        "pcg_gdofs": mesh.n_dof * (info["iterations"] + 1) / t_pcg / 1e9,
+                        "true_rel_residual": info["true_rel_residual"]})
+            del op, mesh, b, x
+            torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hx", choices=["hx", "reference"])
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--n", type=int, default=96)
+    ap.add_argument("--geom", default="stored", choices=["stored", "onthefly"])
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-elems", type=int, default=14)
+    ap.add_argument("--ref-elems", type=int, default=6)
+    ap.add_argument("--ref-iterations", type=int, default=100)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_hx(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -74,6 +74,7 @@ typedef struct hx_solve_info {
   double rel_residual;       /* ||r_k||_2 / ||P b||_2 of the CG recurrence residual */
   double true_rel_residual;  /* ||P b - A_c x||_2 / ||P b||_2, recomputed with one extra apply */
   double b_norm;             /* ||P b||_2 */
+  int kernel_launches;       /* kernels this solve enqueued (CUDA-graph replays included) */
 } hx_solve_info;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -143,6 +144,19 @@ HX_API hx_status hx_mesh_node_coords(const hx_mesh* mesh, double* xyz, void* str
  */
 HX_API hx_status hx_op_create(hx_mesh* mesh, double alpha, double nu, const double* nu_q, int geom_mode,
                               void* stream, hx_op** out);
+
+/*
+ * Replace the coefficients of an existing operator: recomputes the stored
+ * factors m = alpha w detJ, G = nu w detJ J^-1 J^-T (Sec. 3.1) and the
+ * diagonal, e.g. when the time step 1/alpha or the viscosity changes between
+ * the Helmholtz solves of successive time steps (Sec. 4.2, Sec. 5.3).  Same
+ * meaning of alpha, nu, nu_q as hx_op_create; an HX_GEOM_ONTHEFLY operator takes
+ * a nu_q field only if it was created with one.  Allocates nothing; stream-ordered.
+ */
+HX_API hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const double* nu_q, void* stream);
+
+/* Number of kernels the operator has enqueued since creation (graph replays counted per kernel). */
+HX_API int64_t hx_op_launch_count(const hx_op* op);
 
 /* Sizes of the mesh an operator is built on; any output pointer may be NULL. */
 HX_API hx_status hx_op_info(const hx_op* op, int64_t* n_elem, int64_t* n_dof, int* p, int* q);

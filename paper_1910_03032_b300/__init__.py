@@ -37,7 +37,8 @@ _P, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_doubl
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("true_rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double)]
+                ("true_rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -57,6 +58,8 @@ SIGNATURES = {
     "hx_mesh_node_coords": (_I, [_P, _P, _P]),
     "hx_op_create": (_I, [_P, _D, _D, _P, _I, _P, ctypes.POINTER(_P)]),
     "hx_op_info": (_I, _SIZES),
+    "hx_op_set_coefficients": (_I, [_P, _D, _D, _P, _P]),
+    "hx_op_launch_count": (ctypes.c_int64, [_P]),
     "hx_op_destroy": (None, [_P]),
     "hx_op_apply": (_I, [_P, _P, _P, _I, _P]),
     "hx_op_diagonal": (_I, [_P, _P, _I, _P]),
@@ -210,6 +213,16 @@ def hx_op_create(mesh, alpha, nu, nu_q=None, geom_mode=HX_GEOM_STORED, stream=No
     return out
 
 
+def hx_op_set_coefficients(op, alpha, nu, nu_q=None, stream=None):
+    E, _, _, q = hx_op_info(op)
+    nptr = None if nu_q is None else _dptr(nu_q, E * q ** 3, "nu_q")
+    _check(_lib.hx_op_set_coefficients(op, float(alpha), float(nu), nptr, _stream(stream)))
+
+
+def hx_op_launch_count(op) -> int:
+    return int(_lib.hx_op_launch_count(op))
+
+
 def hx_op_destroy(op):
     _lib.hx_op_destroy(op)
 
@@ -306,6 +319,12 @@ class Operator:
         b = torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
         hx_op_load_vector(self.handle, f_q, b, stream)
         return b
+
+    def set_coefficients(self, alpha, nu, nu_q=None, stream=None):
+        hx_op_set_coefficients(self.handle, alpha, nu, nu_q, stream)
+
+    def launch_count(self):
+        return hx_op_launch_count(self.handle)
 
     def solve(self, b, x=None, rtol=1e-10, max_it=10000, stream=None, raise_on_fail=True):
         import torch

@@ -82,6 +82,7 @@ struct hx_op {
   int geom = 0;
   double* factors = nullptr;  // [E][7][Q3] (stored)
   double* nu_q = nullptr;     // [E][Q3] (on the fly with a field)
+  bool use_field = false;     // on the fly: nu_q holds the current field
   double* yE = nullptr;       // [E][n^3]
   double* diag = nullptr;     // [n_dof] unconstrained diagonal
   // solver workspace (allocated at the first solve)
@@ -95,6 +96,7 @@ struct hx_op {
   cudaEvent_t ev = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_failed = false;
+  long long launches = 0;  // kernels enqueued by this operator so far (graph replays included)
 };
 
 namespace {
@@ -296,7 +298,7 @@ HxApplyArgs apply_args(const hx_op* op, const double* x, int constrained, const 
   a.yE = op->yE;
   a.factors = op->factors;
   a.X8 = m->X8;
-  a.nu_q = op->nu_q;
+  a.nu_q = op->use_field ? op->nu_q : nullptr;
   a.alpha = op->alpha;
   a.nu = op->nu;
   a.constrained = constrained;
@@ -338,6 +340,55 @@ void hx_op_destroy(hx_op* op) {
   delete op;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Coefficient-dependent setup, stream-ordered and allocation-free: stored
+// factors (alpha, nu) and the assembled diagonal (and its inverse once the
+// solver workspace exists).  `bad` (nullable) counts detJ <= 0 points.
+hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* nu_q, int* bad, cudaStream_t s,
+                             int* launches) {
+  hx_mesh* m = op->mesh;
+  const long long Q3 = (long long)m->q * m->q * m->q;
+  int nl = 0;
+  cudaError_t e;
+  op->alpha = alpha;
+  op->nu = nu;
+  if (op->geom == HX_GEOM_STORED) {
+    HX_TRY(hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s), "geometry kernel");
+    ++nl;
+  } else {
+    op->use_field = nu_q != nullptr;
+    if (nu_q && nu_q != op->nu_q) {
+      e = cudaMemcpyAsync(op->nu_q, nu_q, sizeof(double) * m->E * Q3, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(e, "nu copy");
+    }
+  }
+  HxDiagArgs d;
+  d.E = m->E;
+  d.factors = op->factors;
+  d.X8 = m->X8;
+  d.nu_q = op->use_field ? op->nu_q : nullptr;
+  d.alpha = alpha;
+  d.nu = nu;
+  d.dE = op->yE;
+  HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
+         "diagonal assembly");
+  nl += 2;
+  if (op->dinv) {
+    HX_TRY(hx_launch_dinv(m->n_dof, op->diag, m->dir, op->dinv, s), "dinv");
+    ++nl;
+  }
+  if (launches) *launches = nl;
+  return HX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, int geom_mode, void* stream,
                        hx_op** out) {
   if (!out) return fail(HX_ERR_ARG, "out is NULL");
@@ -349,8 +400,6 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
   if (!op) return fail(HX_ERR_OOM, "host allocation failed");
   op->mesh = m;
   m->n_ops += 1;
-  op->alpha = alpha;
-  op->nu = nu;
   op->geom = geom_mode;
   const long long Q3 = (long long)m->q * m->q * m->q;
   int* bad = nullptr;
@@ -365,14 +414,8 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
     if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
     if (geom_mode == HX_GEOM_STORED) {
       if ((st = dalloc(&op->factors, (size_t)m->E * 7 * Q3, "geometric factors"))) break;
-      e = hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s);
-      if (e != cudaSuccess) { st = cuda_fail(e, "geometry kernel"); break; }
     } else {
-      if (nu_q) {
-        if ((st = dalloc(&op->nu_q, (size_t)m->E * Q3, "nu field"))) break;
-        e = cudaMemcpyAsync(op->nu_q, nu_q, sizeof(double) * m->E * Q3, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "nu copy"); break; }
-      }
+      if (nu_q && (st = dalloc(&op->nu_q, (size_t)m->E * Q3, "nu field"))) break;
       // detJ check through the factor kernel, a bounded slab of elements at a time
       const long long chunk = 65536;
       if ((st = dalloc(&tmp, (size_t)std::min(chunk, m->E) * 7 * Q3, "detJ check"))) break;
@@ -382,19 +425,9 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
       }
       if (e != cudaSuccess) { st = cuda_fail(e, "detJ check"); break; }
     }
-    // diagonal: element diagonals -> assembled L-vector
-    HxDiagArgs d;
-    d.E = m->E;
-    d.factors = op->factors;
-    d.X8 = m->X8;
-    d.nu_q = op->nu_q;
-    d.alpha = alpha;
-    d.nu = nu;
-    d.dE = op->yE;
-    e = diag_launcher(m->p)(m->T, d, geom_mode, s);
-    if (e != cudaSuccess) { st = cuda_fail(e, "diagonal kernel"); break; }
-    e = hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s);
-    if (e != cudaSuccess) { st = cuda_fail(e, "diagonal assembly"); break; }
+    int nl = 0;
+    if ((st = setup_coefficients(op, alpha, nu, nu_q, bad, s, &nl))) break;
+    op->launches += nl;
     e = cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = cuda_fail(e, "operator setup"); break; }
@@ -410,6 +443,18 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
   return HX_OK;
 }
 
+hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const double* nu_q, void* stream) {
+  if (!op) return fail(HX_ERR_ARG, "op is NULL");
+  if (op->geom == HX_GEOM_ONTHEFLY && nu_q && !op->nu_q)
+    return fail(HX_ERR_ARG, "on-the-fly operator created without a nu field cannot take one");
+  int nl = 0;
+  hx_status st = setup_coefficients(op, alpha, nu, nu_q, nullptr, (cudaStream_t)stream, &nl);
+  if (st == HX_OK) op->launches += nl;
+  return st;
+}
+
+int64_t hx_op_launch_count(const hx_op* op) { return op ? op->launches : -1; }
+
 hx_status hx_op_info(const hx_op* op, int64_t* n_elem, int64_t* n_dof, int* p, int* q) {
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
   return hx_mesh_info(op->mesh, n_elem, n_dof, p, q);
@@ -422,6 +467,7 @@ hx_status hx_op_apply(hx_op* op, const double* x, double* y, int constrained, vo
   const hx_mesh* m = op->mesh;
   HX_TRY(element_apply(op, x, constrained, nullptr, s), "element kernel");
   HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, constrained, x, 0.0, y, s), "assembly");
+  op->launches += 2;
   return HX_OK;
 }
 
@@ -430,6 +476,7 @@ hx_status hx_op_diagonal(hx_op* op, double* diag, int constrained, void* stream)
   HX_TRY(hx_launch_masked_copy(op->mesh->n_dof, op->diag, op->mesh->dir, constrained, 1.0, diag,
                                (cudaStream_t)stream),
          "diagonal copy");
+  op->launches += 1;
   return HX_OK;
 }
 
@@ -444,6 +491,7 @@ hx_status hx_op_load_vector(hx_op* op, const double* f_q, double* b, void* strea
   a.yE = op->yE;
   HX_TRY(load_launcher(m->p)(m->T, a, s), "load kernel");
   HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, b, s), "assembly");
+  op->launches += 2;
   return HX_OK;
 }
 
@@ -487,6 +535,7 @@ hx_status ensure_solver(hx_op* op) {
   HX_TRY(cudaMemsetAsync(op->st, 0, sizeof(HxCgState), op->stream), "state init");
   HX_TRY(cudaMemsetAsync(op->counters, 0, 2 * sizeof(unsigned int), op->stream), "counter init");
   HX_TRY(hx_launch_dinv(n, op->diag, op->mesh->dir, op->dinv, op->stream), "dinv");
+  op->launches += 1;
   return HX_OK;
 }
 
@@ -531,13 +580,16 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   HX_TRY(cudaEventRecord(op->ev, user), "event record");
   HX_TRY(cudaStreamWaitEvent(st, op->ev, 0), "stream wait");
   const HxCgBuffers buf = cg_buffers(op);
+  const long long launches0 = op->launches;
   HX_TRY(hx_launch_cg_init(buf, b, use_x0 ? x : nullptr, rtol, max_it, st), "cg init");
   if (use_x0) {
     HX_TRY(element_apply(op, op->x, 1, nullptr, st), "cg x0 apply");
     HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "cg x0 assembly");
     HX_TRY(hx_launch_cg_residual(buf, st), "cg residual");
+    op->launches += 3;
   }
   HX_TRY(hx_launch_cg_start(buf, st), "cg start");
+  op->launches += 2;
   for (;;) {
     HX_TRY(cudaMemcpyAsync(op->st_host, op->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
     HX_TRY(cudaStreamSynchronize(st), "solver sync");
@@ -547,12 +599,14 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
     } else {
       for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration(op, st), "cg iteration");
     }
+    op->launches += 4 * kChunk;
   }
   const HxCgState cs = *op->st_host;
   // true residual ||P b - A_c x|| with one extra apply
   HX_TRY(element_apply(op, op->x, 1, nullptr, st), "residual apply");
   HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "residual assembly");
   HX_TRY(hx_launch_resnorm(m->n_dof, b, op->Ap, m->dir, op->partial, op->counters, op->scalars, st), "residual norm");
+  op->launches += 3;
   double rn2 = 0.0;
   HX_TRY(cudaMemcpyAsync(&rn2, op->scalars, sizeof(double), cudaMemcpyDeviceToHost, st), "residual read");
   HX_TRY(cudaMemcpyAsync(x, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, st), "solution copy");
@@ -564,6 +618,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   inf.b_norm = bn;
   inf.rel_residual = bn > 0 ? std::sqrt(cs.rr) / bn : 0.0;
   inf.true_rel_residual = bn > 0 ? std::sqrt(rn2) / bn : std::sqrt(rn2);
+  inf.kernel_launches = (int)(op->launches - launches0);
   if (info) *info = inf;
   if (cs.status == HX_ERR_NOT_CONVERGED)
     return fail(HX_ERR_NOT_CONVERGED, "not converged in %d iterations (rel. residual %.3e)", cs.iter, inf.rel_residual);
