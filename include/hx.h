@@ -214,6 +214,51 @@ HX_API hx_status hx_solve_pcg(hx_op* op, const double* b, double* x, double rtol
 HX_API hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, double rtol, int max_it,
                                    int use_x0, hx_solve_info* info);
 
+/*
+ * Operator apply that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc.  Examples are code running while a stream is captured into a
+ * CUDA graph (allocation is not a stream operation), code inside a framework
+ * whose pool allocator owns all device memory, and latency-bound loops that
+ * cannot pay for the device synchronization cudaMalloc / cudaFree bring.
+ * hx_op_create allocates an element-vector workspace; this call instead uses
+ * a fixed array in the library's static device memory (HX_NOALLOC_MAX_EVEC
+ * doubles, 32 MiB, held by every GPU that loads the library until the process
+ * exits) and takes everything else from the caller.
+ *
+ * Computes y = A x for A = alpha M + K(nu) with constant alpha, nu, geometric
+ * factors recomputed from the element vertices (as HX_GEOM_ONTHEFLY), and no
+ * Dirichlet elimination (the unconstrained operator of hx_op_apply).
+ *   p, q        1 <= p <= 8, q in {p+1, p+2}
+ *   n_elem      elements; n_elem (p+1)^3 must not exceed HX_NOALLOC_MAX_EVEC
+ *               (else HX_ERR_UNSUPPORTED with a message saying so)
+ *   n_dof       length of x and y
+ *   X8          device, n_elem x 8 x 3 doubles: element corner coordinates,
+ *               corner order c = cx + 2 cy + 4 cz
+ *   restriction device, n_elem x (p+1)^3 int32 global DoF ids in [0, n_dof),
+ *               local node order lexicographic (as hx_mesh_create)
+ *   t_offsets   device, n_dof + 1 int32: the transpose of the restriction in
+ *   t_indices   device, n_elem (p+1)^3 int32  compressed form: DoF g owns the
+ *               positions t_indices[t_offsets[g] .. t_offsets[g+1]), each
+ *               position e (p+1)^3 + l naming local node l of element e; the
+ *               sum over them runs in the order given (increasing positions
+ *               reproduce hx_op_apply bit for bit)
+ *   x, y        device, n_dof doubles, not overlapping
+ *   stream      stream the two kernels are enqueued on
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before capturing any stream.  Every call on a device shares the
+ * one scratch array and leaves its contents behind; the element kernel
+ * overwrites every entry it later reads, so nothing needs clearing, but calls
+ * whose work overlaps on the GPU (different streams, or several threads) race
+ * on the array and must be serialized by the caller.  No device memory is
+ * allocated or freed.  Stream-ordered.
+ */
+#define HX_NOALLOC_MAX_EVEC (1LL << 22)
+HX_API hx_status hx_apply_noalloc(int p, int q, int64_t n_elem, int64_t n_dof, const double* X8,
+                                  const int32_t* restriction, const int32_t* t_offsets, const int32_t* t_indices,
+                                  double alpha, double nu, const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

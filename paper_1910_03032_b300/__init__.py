@@ -66,7 +66,10 @@ SIGNATURES = {
     "hx_op_load_vector": (_I, [_P, _P, _P, _P]),
     "hx_solve_pcg": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(SolveInfo)]),
+    "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
 }
+
+HX_NOALLOC_MAX_EVEC = 1 << 22
 
 
 class HxError(RuntimeError):
@@ -260,6 +263,26 @@ def hx_solve_pcg_host(op, b_host, x_host, rtol=1e-10, max_it=10000, use_x0=False
     if raise_on_fail or st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_BREAKDOWN):
         _check(st)
     return info.as_dict()
+
+
+def _iptr(t, n, name):
+    """Device pointer of a contiguous int32 CUDA tensor with n elements."""
+    if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.int32" or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hx_apply_noalloc(p, q, X8, restriction, t_offsets, t_indices, alpha, nu, x, y, stream=None):
+    """y = A x without any device allocation (see include/hx.h): every array comes from the caller."""
+    n_elem = int(restriction.shape[0])
+    n_dof = int(x.numel())
+    n3 = (p + 1) ** 3
+    _check(_lib.hx_apply_noalloc(int(p), int(q), n_elem, n_dof, _dptr(X8, n_elem * 24, "X8"),
+                                 _iptr(restriction, n_elem * n3, "restriction"), _iptr(t_offsets, n_dof + 1, "t_offsets"),
+                                 _iptr(t_indices, n_elem * n3, "t_indices"), float(alpha), float(nu),
+                                 _dptr(x, n_dof, "x"), _dptr(y, n_dof, "y"), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

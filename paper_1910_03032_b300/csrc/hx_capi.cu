@@ -64,6 +64,8 @@ void dfree(T*& p) {
 
 }  // namespace
 
+void hx_internal_set_error(const char* msg) { g_err = msg; }
+
 struct hx_mesh {
   int p = 0, q = 0, n = 0, N3 = 0, device = 0;
   long long E = 0, n_dof = 0;

@@ -120,3 +120,7 @@ cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double*
                           double* out, cudaStream_t s);
 cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,
                               unsigned int* counter, double* out, cudaStream_t s);
+
+// Sets the message hx_last_error() returns on this thread (for entry points
+// defined outside hx_capi.cu).
+void hx_internal_set_error(const char* msg);
