@@ -207,12 +207,13 @@ HX_API hx_status hx_solve_pcg(hx_op* op, const double* b, double* x, double rtol
                               void* stream, hx_solve_info* info);
 
 /*
- * As hx_solve_pcg with b and x in host memory: copies b (and x0) to the
+ * As hx_solve_pcg with b and x in host memory: after the caller's prior work
+ * on `stream` (e.g. an hx_op_set_coefficients), copies b (and x0) to the
  * device, solves, and copies x back.  b_host, x_host: host, n_dof doubles.
  * Synchronous.
  */
 HX_API hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, double rtol, int max_it,
-                                   int use_x0, hx_solve_info* info);
+                                   int use_x0, void* stream, hx_solve_info* info);
 
 /*
  * Operator apply that allocates no device memory.  The paper has no

@@ -65,7 +65,7 @@ SIGNATURES = {
     "hx_op_diagonal": (_I, [_P, _P, _I, _P]),
     "hx_op_load_vector": (_I, [_P, _P, _P, _P]),
     "hx_solve_pcg": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
-    "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(SolveInfo)]),
+    "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
 }
 
@@ -255,11 +255,11 @@ def hx_solve_pcg(op, b, x, rtol=1e-10, max_it=10000, use_x0=False, stream=None, 
     return info.as_dict()
 
 
-def hx_solve_pcg_host(op, b_host, x_host, rtol=1e-10, max_it=10000, use_x0=False, raise_on_fail=True):
+def hx_solve_pcg_host(op, b_host, x_host, rtol=1e-10, max_it=10000, use_x0=False, stream=None, raise_on_fail=True):
     n = hx_op_info(op)[1]
     info = SolveInfo()
     st = _lib.hx_solve_pcg_host(op, _hptr(b_host, n, "b_host"), _hptr(x_host, n, "x_host"), float(rtol),
-                                int(max_it), int(bool(use_x0)), ctypes.byref(info))
+                                int(max_it), int(bool(use_x0)), _stream(stream), ctypes.byref(info))
     if raise_on_fail or st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_BREAKDOWN):
         _check(st)
     return info.as_dict()

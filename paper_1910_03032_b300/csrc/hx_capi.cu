@@ -640,7 +640,7 @@ hx_status hx_solve_pcg(hx_op* op, const double* b, double* x, double rtol, int m
 }
 
 hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, double rtol, int max_it, int use_x0,
-                            hx_solve_info* info) {
+                            void* stream, hx_solve_info* info) {
   if (!op || !b_host || !x_host) return fail(HX_ERR_ARG, "NULL argument");
   if (!(rtol >= 0.0) || max_it < 0) return fail(HX_ERR_ARG, "rtol must be >= 0 and max_it >= 0");
   const long long n = op->mesh->n_dof;
@@ -649,6 +649,9 @@ hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, dou
   if (!op->hb) {
     if ((s = dalloc(&op->hb, n, "staging b")) || (s = dalloc(&op->hx, n, "staging x"))) return s;
   }
+  // the uploads run on the solver stream after the caller's prior work on `stream`
+  HX_TRY(cudaEventRecord(op->ev, (cudaStream_t)stream), "event record");
+  HX_TRY(cudaStreamWaitEvent(op->stream, op->ev, 0), "stream wait");
   HX_TRY(cudaMemcpyAsync(op->hb, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, op->stream), "b upload");
   if (use_x0)
     HX_TRY(cudaMemcpyAsync(op->hx, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, op->stream), "x0 upload");

@@ -167,6 +167,12 @@ def test_solve_matches_dense_and_host_api(hx, geom):
     # warm start from the solution converges at once
     x2, info2 = op.solve(to_dev(b), x=x.clone(), rtol=1e-8)
     assert info2["iterations"] <= 1
+    # new coefficients enqueued on the caller's stream, then a host-buffer solve:
+    # the solve must see the updated factors and diagonal
+    op.set_coefficients(10.0, 0.5)
+    hx.hx_solve_pcg_host(op.handle, np.ascontiguousarray(b), xh, 1e-12, 10000, False)
+    A2 = fem.Operator(om, 10.0, 0.5).assembled(constrained=True)
+    assert rel_err(xh, np.linalg.solve(A2, np.where(om.dirichlet, 0.0, b))) <= 1e-10
 
 
 def test_solver_status_codes(hx):
