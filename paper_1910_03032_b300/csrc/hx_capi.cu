@@ -452,6 +452,12 @@ hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const doubl
   int nl = 0;
   hx_status st = setup_coefficients(op, alpha, nu, nu_q, nullptr, (cudaStream_t)stream, &nl);
   if (st == HX_OK) op->launches += nl;
+  if (op->geom == HX_GEOM_ONTHEFLY && op->graph) {
+    // the captured CG iterations carry alpha, nu (and the field pointer) as kernel
+    // parameters: drop the graph so the next solve captures the new values
+    cudaGraphExecDestroy(op->graph);
+    op->graph = nullptr;
+  }
   return st;
 }
 
