@@ -51,10 +51,7 @@ HBM_GBS = 6518.0  # measured copy bandwidth of the B300s
 FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch from
 # an ncu capture, keyed by (p, N, geom); None until a capture of the current kernel exists.
-NCU_TRAFFIC = {
-    # profiles/apply_kernel_fp64_p4_q6_n32.md: 457.38 MB per launch at 32^3, x 27 elements
-    (4, 96, "stored"): 457379840 * 27,
-}
+NCU_TRAFFIC = {}
 
 
 def alg_flops_per_element(p: int, q: int) -> int:

@@ -165,6 +165,16 @@ int hx_build_tables(int p, int q, HxTables* t) {
   fold(Bt.data(), n, q, t->Bte, t->Bto);
   fold(Dh.data(), q, q, t->De, t->Do);
   fold(Dht.data(), q, q, t->Dte, t->Dto);
+  {
+    const int HQ = q / 2, CQ = (q + 1) / 2;
+    for (int a = 0; a < CQ; ++a) {
+      for (int b = 0; b < CQ; ++b) t->De2[a * CQ + b] = (b < HQ ? 2.0 : 1.0) * t->De[a * CQ + b];
+      for (int b = 0; b < HQ; ++b) t->Do2[a * HQ + b] = 2.0 * t->Do[a * HQ + b];
+      const double r = (a < HQ) ? 2.0 : 1.0;
+      for (int b = 0; b < CQ; ++b) t->Dte2[a * CQ + b] = r * t->Dte[a * CQ + b];
+      for (int b = 0; b < HQ; ++b) t->Dto2[a * HQ + b] = r * t->Dto[a * HQ + b];
+    }
+  }
   std::memcpy(t->B, B.data(), sizeof(double) * q * n);
   std::memcpy(t->D, D.data(), sizeof(double) * q * n);
   for (int i = 0; i < q; ++i) { t->xq[i] = xq[i]; t->wq[i] = wq[i]; }

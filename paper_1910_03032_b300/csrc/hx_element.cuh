@@ -1,22 +1,25 @@
 // Element kernels of the matrix-free Q_p Helmholtz operator alpha M + nu K.
 //
-// One thread block processes NE elements.  Every stage is a loop over "line
-// tasks" (one 1D contraction of one line of one element) spread over all NT
-// threads, so warps stay full whatever p is; stages are separated by
-// __syncthreads().  Per element, shared memory holds four q^3 regions
-//   A: u at the quadrature points, then v = m u
-//   B: du/dxi_1, then w_1, then (Dh^T w_1)
-//   C: du/dxi_2, then w_2, then (Dh^T w_2)
-//   D: the in-place pipeline x_E -> (B x) -> (B B x) -> ... and du/dxi_3
-// all with strides (1, q, q^2), so each line of a stage is owned by one thread
-// and can be overwritten in place.
+// One thread block processes NE elements with NT >= NE q^2 threads, so that
+// thread t owns z-column t (element t / q^2, column t % q^2) in the three
+// "column" stages and keeps that column's data in registers between them.
+// The other stages are loops over line tasks (one 1D contraction of one line
+// of one element) spread over all threads, so warps stay full at every p.
+// Stages are separated by __syncthreads().  Per element, shared memory holds
+// three q^3 regions with strides (1, q, q^2):
+//   D: the in-place pipeline x_E -> (B x) -> (B B x) -> u at the points,
+//      later (B^T V) -> (B^T B^T V) -> y_E along the transposed directions
+//   X: du/dxi_1, then w_1 = (G grad u)_1, then Dh^T w_1
+//   Y: du/dxi_2, then w_2, then Dh^T w_2
+// du/dxi_3, v = m u, w_3 and Dh^T w_3 never leave the column owner's registers.
 //
 // Sum factorization (Sec. 3.1, Eqs. (sumFactorized), (tensorGradient)):
 //   u_q = (B x B x B) x_E, grad u_q = (Dh applied along each direction) u_q,
 //   [v; w] = [m u_q; G grad u_q]  (pointwise, G = nu w detJ J^-1 J^-T, m = alpha w detJ),
 //   y_E = (B x B x B)^T (v + sum_d Dh_d^T w_d).
-// Each 1D contraction uses the even-odd folding of the symmetric 1D matrices
-// (the symmetry the paper points out in Sec. 6).
+// Each 1D contraction uses the even-odd folding of the centro-symmetric 1D
+// matrices (the symmetry the paper points out in Sec. 6); along z the folded
+// parts of one contraction feed the next one directly, without recombining.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,44 +29,72 @@
 
 namespace hx {
 
-// y = S x for a centro-symmetric (SIGMA = +1) or centro-antisymmetric
-// (SIGMA = -1) M x L matrix S given by its folded parts Se, So.
-template <int L, int M, int SIGMA>
-__device__ __forceinline__ void eo_apply(const double* __restrict__ Se, const double* __restrict__ So,
-                                         const double (&x)[L], double (&y)[M]) {
-  constexpr int HL = L / 2, CL = (L + 1) / 2, HM = M / 2;
-  double ev[CL], od[HL];
+// sum_k S[k] v[k] (K >= 1 terms), first term a multiply
+template <int K>
+__device__ __forceinline__ double dotk(const double* __restrict__ S, const double* v) {
+  double s = S[0] * v[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) s = fma(S[k], v[k], s);
+  return s;
+}
+
+// Even / odd parts of x: ev[b] = x[b] + x[L-1-b], od[b] = x[b] - x[L-1-b] (b < L/2),
+// ev[L/2] = x[L/2] for odd L.
+template <int L>
+__device__ __forceinline__ void fold(const double (&x)[L], double* ev, double* od) {
+  constexpr int HL = L / 2;
 #pragma unroll
   for (int b = 0; b < HL; ++b) {
     ev[b] = x[b] + x[L - 1 - b];
     od[b] = x[b] - x[L - 1 - b];
   }
   if (L & 1) ev[HL] = x[HL];
+}
+
+// Folded products of a centro-(anti)symmetric M x L matrix with folded input:
+// E[a] = sum_b Se[a][b] ev[b], O[a] = sum_b So[a][b] od[b] for a < M/2; for odd M the
+// middle row has only its E part (SIGMA = +1) or only its O part (SIGMA = -1).
+template <int L, int M, int SIGMA>
+__device__ __forceinline__ void products(const double* __restrict__ Se, const double* __restrict__ So,
+                                         const double* ev, const double* od, double* E, double* O) {
+  constexpr int HL = L / 2, CL = (L + 1) / 2, HM = M / 2;
 #pragma unroll
   for (int a = 0; a < HM; ++a) {
-    double E = Se[a * CL] * ev[0];
-#pragma unroll
-    for (int b = 1; b < CL; ++b) E = fma(Se[a * CL + b], ev[b], E);
-    double O = So[a * HL] * od[0];
-#pragma unroll
-    for (int b = 1; b < HL; ++b) O = fma(So[a * HL + b], od[b], O);
-    y[a] = E + O;
-    y[M - 1 - a] = (SIGMA > 0) ? (E - O) : (O - E);
+    E[a] = dotk<CL>(Se + a * CL, ev);
+    O[a] = dotk<HL>(So + a * HL, od);
   }
   if (M & 1) {
-    constexpr int a = HM;
     if (SIGMA > 0) {
-      double E = Se[a * CL] * ev[0];
-#pragma unroll
-      for (int b = 1; b < CL; ++b) E = fma(Se[a * CL + b], ev[b], E);
-      y[a] = E;
+      E[HM] = dotk<CL>(Se + HM * CL, ev);
+      O[HM] = 0.0;
     } else {
-      double O = So[a * HL] * od[0];
-#pragma unroll
-      for (int b = 1; b < HL; ++b) O = fma(So[a * HL + b], od[b], O);
-      y[a] = O;
+      O[HM] = dotk<HL>(So + HM * HL, od);
+      E[HM] = 0.0;
     }
   }
+}
+
+// y from folded parts: y[a] = E + O, y[M-1-a] = SIGMA (E - O); middle as in products.
+template <int M, int SIGMA>
+__device__ __forceinline__ void combine(const double* E, const double* O, double (&y)[M]) {
+  constexpr int HM = M / 2;
+#pragma unroll
+  for (int a = 0; a < HM; ++a) {
+    y[a] = E[a] + O[a];
+    y[M - 1 - a] = (SIGMA > 0) ? (E[a] - O[a]) : (O[a] - E[a]);
+  }
+  if (M & 1) y[HM] = (SIGMA > 0) ? E[HM] : O[HM];
+}
+
+// y = S x for a centro-symmetric (SIGMA = +1) or centro-antisymmetric
+// (SIGMA = -1) M x L matrix S given by its folded parts Se, So.
+template <int L, int M, int SIGMA>
+__device__ __forceinline__ void eo_apply(const double* __restrict__ Se, const double* __restrict__ So,
+                                         const double (&x)[L], double (&y)[M]) {
+  double ev[(L + 1) / 2], od[(L + 1) / 2], E[(M + 1) / 2], O[(M + 1) / 2];
+  fold<L>(x, ev, od);
+  products<L, M, SIGMA>(Se, So, ev, od, E, O);
+  combine<M, SIGMA>(E, O, y);
 }
 
 template <int L>
@@ -163,18 +194,18 @@ __device__ __forceinline__ double point_factors(const double (&j0)[3], const dou
 }
 
 // ---------------------------------------------------------------------------
-// stages shared by the apply and load-vector kernels
+// stages shared by the apply and load-vector kernels (region D at stride R3)
 // ---------------------------------------------------------------------------
 // After the z-direction transpose has left [kz][jq][iq] in region D: B^T along
-// y, B^T along x, then a coalesced copy of the block's E-vector slab.
+// y, then B^T along x written straight to the E-vector.
 template <int N, int Q, int NE, int NT>
-__device__ __forceinline__ void stage_transpose_y_x_store(const HxTables& T, double* smem, long long e0,
-                                                          long long E, double* __restrict__ yE) {
-  constexpr int Q3 = Q * Q * Q, N3 = N * N * N, SY = Q, SZ = Q * Q, R4 = 4 * Q3;
+__device__ __forceinline__ void transpose_y_x_store(const HxTables& T, double* smem, long long e0, long long E,
+                                                    double* __restrict__ yE) {
+  constexpr int Q3 = Q * Q * Q, N3 = N * N * N, SY = Q, SZ = Q * Q, R3 = 3 * Q3;
   for (int t = threadIdx.x; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
     const int kz = r / Q, iq = r - kz * Q;
-    double* line = smem + el * R4 + 3 * Q3 + kz * SZ + iq;
+    double* line = smem + el * R3 + kz * SZ + iq;
     double vin[Q], vout[N];
     load_line<Q>(line, SY, vin);
     eo_apply<Q, N, 1>(T.Bte, T.Bto, vin, vout);
@@ -184,36 +215,36 @@ __device__ __forceinline__ void stage_transpose_y_x_store(const HxTables& T, dou
   for (int t = threadIdx.x; t < NE * N * N; t += NT) {
     const int el = t / (N * N), r = t - el * (N * N);
     const int kz = r / N, j = r - kz * N;
-    double* line = smem + el * R4 + 3 * Q3 + kz * SZ + j * SY;
-    double vin[Q], vout[N];
-    load_line<Q>(line, 1, vin);
-    eo_apply<Q, N, 1>(T.Bte, T.Bto, vin, vout);
-    store_line<N>(line, 1, vout);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < NE * N3; t += NT) {
-    const int el = t / N3, l = t - el * N3;
     const long long e = e0 + el;
-    if (e < E) {
-      const int i = l % N, j = (l / N) % N, k = l / (N * N);
-      yE[e * N3 + l] = smem[el * R4 + 3 * Q3 + k * SZ + j * SY + i];
-    }
+    double vin[Q], vout[N];
+    load_line<Q>(smem + el * R3 + kz * SZ + j * SY, 1, vin);
+    eo_apply<Q, N, 1>(T.Bte, T.Bto, vin, vout);
+    if (e < E) store_line<N>(yE + e * N3 + r * N, 1, vout);
   }
 }
 
 // ---------------------------------------------------------------------------
 // the operator kernel
 // ---------------------------------------------------------------------------
-template <int P, int Q, int NE, int NT, int GEOM, bool NUF>
-__global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ HxTables T, const HxApplyArgs A) {
-  constexpr int N = P + 1, N3 = N * N * N, Q3 = Q * Q * Q, SY = Q, SZ = Q * Q, R4 = 4 * Q3;
+template <int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
+__global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__ HxTables T, const HxApplyArgs A) {
+  constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q, SY = Q, SZ = Q2, R3 = 3 * Q3;
+  constexpr int CQ = (Q + 1) / 2, CN = (N + 1) / 2;
+  static_assert(NT >= NE * Q2, "one thread per z-column");
   if (A.done != nullptr && *(volatile const int*)A.done) return;
   extern __shared__ double smem[];
-  double* geo = smem + NE * R4;  // on-the-fly: NE x 24 map coefficients
+  double* geo = smem + NE * R3;  // on-the-fly: NE x 24 map coefficients
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
 
-  if (GEOM == HX_KGEOM_ONTHEFLY) {
+  if (GEOM == HX_KGEOM_STORED) {
+    // pull this block's factors toward L2 while the forward contractions run
+    const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
+    const char* base = reinterpret_cast<const char*>(A.factors + e0 * 7 * Q3);
+    const long long bytes = nel * 7 * Q3 * (long long)sizeof(double);
+    for (long long off = (long long)tid * 128; off < bytes; off += (long long)NT * 128)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+  } else {
     for (int el = tid; el < NE; el += NT) {
       const long long e = e0 + el;
       double X8[24];
@@ -221,140 +252,157 @@ __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ HxTab
       trilinear_coeffs(X8, geo + el * 24);
     }
   }
-  // gather x_E = R x (Dirichlet DoFs read as zero for the constrained operator)
-  for (int t = tid; t < NE * N3; t += NT) {
-    const int el = t / N3, l = t - el * N3;
-    const long long e = e0 + el;
-    double v = 0.0;
-    if (e < A.E) {
-      const int g = __ldg(A.R + e * N3 + l);
-      if (g >= 0) v = __ldg(A.x + g);
-      else if (!A.constrained) v = __ldg(A.x + (-g - 1));
-    }
-    const int i = l % N, j = (l / N) % N, k = l / (N * N);
-    smem[el * R4 + 3 * Q3 + k * SZ + j * SY + i] = v;
-  }
-  __syncthreads();
-  // x-lines: [k][j][i] -> [k][j][iq]
+  // 1. gather x_E = R x (Dirichlet DoFs read as zero for A_c) and B along x: [k][j][i] -> [k][j][iq]
   for (int t = tid; t < NE * N * N; t += NT) {
     const int el = t / (N * N), r = t - el * (N * N);
+    const long long e = e0 + el;
+    double vin[N];
+    if (e < A.E) {
+      const int* Rp = A.R + e * N3 + r * N;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int g = __ldg(Rp + i);
+        vin[i] = (g >= 0) ? __ldg(A.x + g) : (A.constrained ? 0.0 : __ldg(A.x + (-g - 1)));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) vin[i] = 0.0;
+    }
     const int k = r / N, j = r - k * N;
-    double* line = smem + el * R4 + 3 * Q3 + k * SZ + j * SY;
-    double vin[N], vout[Q];
-    load_line<N>(line, 1, vin);
+    double vout[Q];
     eo_apply<N, Q, 1>(T.Be, T.Bo, vin, vout);
-    store_line<Q>(line, 1, vout);
+    store_line<Q>(smem + el * R3 + k * SZ + j * SY, 1, vout);
   }
   __syncthreads();
-  // y-lines: [k][j][iq] -> [k][jq][iq]
+  // 2. B along y: [k][j][iq] -> [k][jq][iq]
   for (int t = tid; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
     const int k = r / Q, iq = r - k * Q;
-    double* line = smem + el * R4 + 3 * Q3 + k * SZ + iq;
+    double* line = smem + el * R3 + k * SZ + iq;
     double vin[N], vout[Q];
     load_line<N>(line, SY, vin);
     eo_apply<N, Q, 1>(T.Be, T.Bo, vin, vout);
     store_line<Q>(line, SY, vout);
   }
   __syncthreads();
-  // z-lines: [k][jq][iq] -> u at the points (region A) and du/dxi_3 (region D)
-  for (int t = tid; t < NE * Q * Q; t += NT) {
-    const int el = t / (Q * Q), r = t - el * (Q * Q);
-    double* col = smem + el * R4 + 3 * Q3 + r;  // r = jq * q + iq
-    double vin[N], u[Q], du[Q];
+  // 3. columns: B along z -> u (stored for the x/y derivatives);
+  //    du/dxi_3 from the folded parts of that same contraction (kept in registers)
+  const bool owner = tid < NE * Q2;
+  const int cel = tid / Q2, c = tid - cel * Q2;
+  double du[Q];
+  if (owner) {
+    double* col = smem + cel * R3 + c;
+    double vin[N], u[Q], ev[CN], od[CN], Eu[CQ], Ou[CQ], Ed[CQ], Od[CQ];
     load_line<N>(col, SZ, vin);
-    eo_apply<N, Q, 1>(T.Be, T.Bo, vin, u);
-    eo_apply<Q, Q, -1>(T.De, T.Do, u, du);
-    store_line<Q>(smem + el * R4 + r, SZ, u);
-    store_line<Q>(col, SZ, du);
+    fold<N>(vin, ev, od);
+    products<N, Q, 1>(T.Be, T.Bo, ev, od, Eu, Ou);
+    combine<Q, 1>(Eu, Ou, u);
+    store_line<Q>(col, SZ, u);
+    products<Q, Q, -1>(T.De2, T.Do2, Eu, Ou, Ed, Od);
+    combine<Q, -1>(Ed, Od, du);
   }
   __syncthreads();
-  // du/dxi_1 (x-lines of A -> B) and du/dxi_2 (y-lines of A -> C)
-  for (int t = tid; t < NE * 2 * Q * Q; t += NT) {
-    const int el = t / (2 * Q * Q), r = t - el * (2 * Q * Q);
-    const int dir = r >= Q * Q;
-    const int rr = r - dir * Q * Q;
+  // 4. du/dxi_1 (x-lines of D -> X) and du/dxi_2 (y-lines of D -> Y)
+  for (int t = tid; t < NE * 2 * Q2; t += NT) {
+    const int el = t / (2 * Q2), r = t - el * (2 * Q2);
+    const int dir = r >= Q2;
+    const int rr = r - dir * Q2;
     const int a = rr / Q, b = rr - a * Q;
     const int off = dir ? (a * SZ + b) : (a * SZ + b * SY);
     const int stride = dir ? SY : 1;
-    double u[Q], du[Q];
-    load_line<Q>(smem + el * R4 + off, stride, u);
-    eo_apply<Q, Q, -1>(T.De, T.Do, u, du);
-    store_line<Q>(smem + el * R4 + (1 + dir) * Q3 + off, stride, du);
+    double uu[Q], d[Q];
+    load_line<Q>(smem + el * R3 + off, stride, uu);
+    eo_apply<Q, Q, -1>(T.De, T.Do, uu, d);
+    store_line<Q>(smem + el * R3 + (1 + dir) * Q3 + off, stride, d);
   }
   __syncthreads();
-  // pointwise: v = m u, w = G grad u
-  for (int t = tid; t < NE * Q3; t += NT) {
-    const int el = t / Q3, pt = t - el * Q3;
-    const long long e = e0 + el;
-    double f[7];
-    if (GEOM == HX_KGEOM_STORED) {
-      if (e < A.E) {
-        const double* fe = A.factors + e * 7 * Q3 + pt;
+  // 5. columns: pointwise v = m u (into D, over u), w = G grad u; then Dh^T along z of
+  //    w_3 (folded parts kept in registers)
+  double Et[CQ], Ot[CQ];
+  if (owner) {
+    const long long e = e0 + cel;
+    double* Dc = smem + cel * R3 + c;
+    double* Xc = Dc + Q3;
+    double* Yc = Xc + Q3;
+    double w3[Q];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) f[c] = __ldg(fe + c * Q3);
+    for (int kq = 0; kq < Q; ++kq) {
+      const int pt = kq * Q2 + c;
+      double f[7];
+      if (GEOM == HX_KGEOM_STORED) {
+        if (e < A.E) {
+          const double* fe = A.factors + e * 7 * Q3 + pt;
+#pragma unroll
+          for (int m = 0; m < 7; ++m) f[m] = __ldg(fe + m * Q3);
+        } else {
+#pragma unroll
+          for (int m = 0; m < 7; ++m) f[m] = 0.0;
+        }
       } else {
+        const int iq = c % Q, jq = c / Q;
+        double j0[3], j1[3], j2[3];
+        trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
+        const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
+        double nu = A.nu;
+        if (NUF) nu = (e < A.E) ? __ldg(A.nu_q + e * Q3 + pt) : 0.0;
+        point_factors(j0, j1, j2, A.alpha * w, nu * w, f);
+        if (e >= A.E) {
 #pragma unroll
-        for (int c = 0; c < 7; ++c) f[c] = 0.0;
+          for (int m = 0; m < 7; ++m) f[m] = 0.0;
+        }
       }
-    } else {
-      const int iq = pt % Q, jq = (pt / Q) % Q, kq = pt / (Q * Q);
-      double j0[3], j1[3], j2[3];
-      trilinear_jacobian(geo + el * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
-      const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
-      double nu = A.nu;
-      if (NUF) nu = (e < A.E) ? __ldg(A.nu_q + e * Q3 + pt) : 0.0;
-      point_factors(j0, j1, j2, A.alpha * w, nu * w, f);
-      if (e >= A.E) {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) f[c] = 0.0;
-      }
+      const double u1 = Xc[kq * SZ], u2 = Yc[kq * SZ], u3 = du[kq];
+      Dc[kq * SZ] = f[0] * Dc[kq * SZ];
+      Xc[kq * SZ] = f[1] * u1 + f[2] * u2 + f[3] * u3;
+      Yc[kq * SZ] = f[2] * u1 + f[4] * u2 + f[5] * u3;
+      w3[kq] = f[3] * u1 + f[5] * u2 + f[6] * u3;
     }
-    double* s = smem + el * R4 + pt;
-    const double u = s[0], u1 = s[Q3], u2 = s[2 * Q3], u3 = s[3 * Q3];
-    s[0] = f[0] * u;
-    s[Q3] = f[1] * u1 + f[2] * u2 + f[3] * u3;
-    s[2 * Q3] = f[2] * u1 + f[4] * u2 + f[5] * u3;
-    s[3 * Q3] = f[3] * u1 + f[5] * u2 + f[6] * u3;
+    double ev[CQ], od[CQ];
+    fold<Q>(w3, ev, od);
+    products<Q, Q, -1>(T.Dte2, T.Dto2, ev, od, Et, Ot);  // rows doubled: (2E, 2O)
   }
   __syncthreads();
-  // Dh^T along x (B, in place) and along y (C, in place)
-  for (int t = tid; t < NE * 2 * Q * Q; t += NT) {
-    const int el = t / (2 * Q * Q), r = t - el * (2 * Q * Q);
-    const int dir = r >= Q * Q;
-    const int rr = r - dir * Q * Q;
+  // 6. Dh^T along x (X, in place) and along y (Y, in place)
+  for (int t = tid; t < NE * 2 * Q2; t += NT) {
+    const int el = t / (2 * Q2), r = t - el * (2 * Q2);
+    const int dir = r >= Q2;
+    const int rr = r - dir * Q2;
     const int a = rr / Q, b = rr - a * Q;
     const int off = dir ? (a * SZ + b) : (a * SZ + b * SY);
     const int stride = dir ? SY : 1;
-    double* line = smem + el * R4 + (1 + dir) * Q3 + off;
+    double* line = smem + el * R3 + (1 + dir) * Q3 + off;
     double w[Q], tw[Q];
     load_line<Q>(line, stride, w);
     eo_apply<Q, Q, -1>(T.Dte, T.Dto, w, tw);
     store_line<Q>(line, stride, tw);
   }
   __syncthreads();
-  // z-lines: V = v + t1 + t2 + Dh^T w3, then B^T along z -> D region [kz][jq][iq]
-  for (int t = tid; t < NE * Q * Q; t += NT) {
-    const int el = t / (Q * Q), r = t - el * (Q * Q);
-    double* base = smem + el * R4 + r;
-    double w3[Q], t3[Q], V[Q], out[N];
-    load_line<Q>(base + 3 * Q3, SZ, w3);
-    eo_apply<Q, Q, -1>(T.Dte, T.Dto, w3, t3);
+  // 7. columns: V = v + t1 + t2 + Dh^T w_3 formed directly in folded form, then B^T along z
+  if (owner) {
+    double* Dc = smem + cel * R3 + c;
+    double sv[Q], es[CQ], os[CQ], E[(N + 1) / 2], O[(N + 1) / 2], out[N];
 #pragma unroll
-    for (int kq = 0; kq < Q; ++kq) V[kq] = (base[kq * SZ] + base[Q3 + kq * SZ]) + (base[2 * Q3 + kq * SZ] + t3[kq]);
-    eo_apply<Q, N, 1>(T.Bte, T.Bto, V, out);
-    store_line<N>(base + 3 * Q3, SZ, out);
+    for (int kq = 0; kq < Q; ++kq) sv[kq] = Dc[kq * SZ] + Dc[Q3 + kq * SZ] + Dc[2 * Q3 + kq * SZ];
+    fold<Q>(sv, es, os);
+#pragma unroll
+    for (int b = 0; b < CQ; ++b) es[b] += Ot[b];
+#pragma unroll
+    for (int b = 0; b < Q / 2; ++b) os[b] += Et[b];
+    products<Q, N, 1>(T.Bte, T.Bto, es, os, E, O);
+    combine<N, 1>(E, O, out);
+    store_line<N>(Dc, SZ, out);
   }
   __syncthreads();
-  stage_transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
+  transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
 }
 
 // Load vector: bE = (B x B x B)^T (w detJ f) per element.
 template <int P, int Q, int NE, int NT>
 __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTables T, const HxLoadArgs A) {
-  constexpr int N = P + 1, Q3 = Q * Q * Q, SZ = Q * Q, R4 = 4 * Q3;
+  constexpr int N = P + 1, Q2 = Q * Q, Q3 = Q2 * Q, SZ = Q2, R3 = 3 * Q3;
+  static_assert(NT >= NE * Q2, "one thread per z-column");
   extern __shared__ double smem[];
-  double* geo = smem + NE * R4;
+  double* geo = smem + NE * R3;
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
   for (int el = tid; el < NE; el += NT) {
@@ -364,31 +412,28 @@ __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTabl
     trilinear_coeffs(X8, geo + el * 24);
   }
   __syncthreads();
-  for (int t = tid; t < NE * Q3; t += NT) {
-    const int el = t / Q3, pt = t - el * Q3;
-    const long long e = e0 + el;
-    double v = 0.0;
-    if (e < A.E) {
-      const int iq = pt % Q, jq = (pt / Q) % Q, kq = pt / (Q * Q);
-      double j0[3], j1[3], j2[3];
-      trilinear_jacobian(geo + el * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
-      const double det = j0[0] * (j1[1] * j2[2] - j1[2] * j2[1]) + j0[1] * (j1[2] * j2[0] - j1[0] * j2[2]) +
-                         j0[2] * (j1[0] * j2[1] - j1[1] * j2[0]);
-      v = T.wq[iq] * T.wq[jq] * T.wq[kq] * det * __ldg(A.fq + e * Q3 + pt);
-    }
-    smem[el * R4 + pt] = v;
-  }
-  __syncthreads();
-  // z-lines: B^T along z from A into D
-  for (int t = tid; t < NE * Q * Q; t += NT) {
-    const int el = t / (Q * Q), r = t - el * (Q * Q);
+  if (tid < NE * Q2) {
+    const int cel = tid / Q2, c = tid - cel * Q2;
+    const int iq = c % Q, jq = c / Q;
+    const long long e = e0 + cel;
     double V[Q], out[N];
-    load_line<Q>(smem + el * R4 + r, SZ, V);
+#pragma unroll
+    for (int kq = 0; kq < Q; ++kq) {
+      double vv = 0.0;
+      if (e < A.E) {
+        double j0[3], j1[3], j2[3];
+        trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
+        const double det = j0[0] * (j1[1] * j2[2] - j1[2] * j2[1]) + j0[1] * (j1[2] * j2[0] - j1[0] * j2[2]) +
+                           j0[2] * (j1[0] * j2[1] - j1[1] * j2[0]);
+        vv = T.wq[iq] * T.wq[jq] * T.wq[kq] * det * __ldg(A.fq + e * Q3 + kq * Q2 + c);
+      }
+      V[kq] = vv;
+    }
     eo_apply<Q, N, 1>(T.Bte, T.Bto, V, out);
-    store_line<N>(smem + el * R4 + 3 * Q3 + r, SZ, out);
+    store_line<N>(smem + cel * R3 + c, SZ, out);
   }
   __syncthreads();
-  stage_transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
+  transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
 }
 
 // Diagonal of the element matrices, sum-factorized:
@@ -510,19 +555,23 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
 // ---------------------------------------------------------------------------
 // launch configuration per order
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, int Q>
 struct Config {
-  // elements per block of the operator kernel (about 55-70 KB of shared memory)
+  // elements per block of the operator kernel (3 q^3 doubles each: ~40-75 KB per block)
   static constexpr int NE = P == 1 ? 64 : P == 2 ? 32 : P == 3 ? 16 : P == 4 ? 8 : P == 5 ? 6 : P == 6 ? 4 : P == 7 ? 3 : 2;
-  static constexpr int NT = 256;
+  // one thread per z-column, rounded up to whole warps
+  static constexpr int NT = ((NE * Q * Q + 31) / 32) * 32;
+  static_assert(NT <= 1024, "block too large");
+  // resident blocks per SM the register budget is sized for (shared memory allows at least this)
+  static constexpr int MINB = P >= 7 ? 3 : NT >= 512 ? 2 : NT >= 384 ? 3 : 4;
   static constexpr int NE_DIAG = P <= 2 ? 8 : P <= 4 ? 2 : 1;
 };
 
 template <int P, int Q, int GEOM, bool NUF>
 cudaError_t launch_apply_impl(const HxTables& T, const HxApplyArgs& A, cudaStream_t s) {
-  constexpr int NE = Config<P>::NE, NT = Config<P>::NT;
-  const size_t shmem = sizeof(double) * (size_t)(NE * 4 * Q * Q * Q + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
-  auto k = apply_kernel<P, Q, NE, NT, GEOM, NUF>;
+  constexpr int NE = Config<P, Q>::NE, NT = Config<P, Q>::NT, MINB = Config<P, Q>::MINB;
+  const size_t shmem = sizeof(double) * (size_t)(NE * 3 * Q * Q * Q + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+  auto k = apply_kernel<P, Q, NE, NT, MINB, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
   const long long blocks = (A.E + NE - 1) / NE;
@@ -540,7 +589,7 @@ cudaError_t launch_apply_q(const HxTables& T, const HxApplyArgs& A, int geom, cu
 
 template <int P, int Q, int GEOM, bool NUF>
 cudaError_t launch_diag_impl(const HxTables& T, const HxDiagArgs& A, cudaStream_t s) {
-  constexpr int N = P + 1, NE = Config<P>::NE_DIAG, NT = 128;
+  constexpr int N = P + 1, NE = Config<P, Q>::NE_DIAG, NT = 128;
   constexpr int F1 = 7 * Q * Q * N, F2 = 7 * Q * N * N;
   constexpr int FA = (7 * Q * Q * Q > F2) ? 7 * Q * Q * Q : F2;
   const size_t shmem = sizeof(double) * (size_t)(NE * (FA + F1) + 3 * Q * N + NE * 24);
@@ -562,8 +611,8 @@ cudaError_t launch_diag_q(const HxTables& T, const HxDiagArgs& A, int geom, cuda
 
 template <int P, int Q>
 cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s) {
-  constexpr int NE = Config<P>::NE, NT = Config<P>::NT;
-  const size_t shmem = sizeof(double) * (size_t)(NE * 4 * Q * Q * Q + NE * 24);
+  constexpr int NE = Config<P, Q>::NE, NT = Config<P, Q>::NT;
+  const size_t shmem = sizeof(double) * (size_t)(NE * 3 * Q * Q * Q + NE * 24);
   auto k = load_kernel<P, Q, NE, NT>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;

@@ -35,6 +35,15 @@ struct HxTables {
   // folded Dh^T (sigma = -1)
   double Dte[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
   double Dto[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  // Dh applied to an input given by the folded parts (E, O) of a centro-symmetric
+  // interpolation along the same direction: the input's even/odd parts are 2E and 2O
+  // (E alone for the middle entry of odd q), so the columns b < q/2 are doubled.
+  double De2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  double Do2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  // Dh^T with the rows a < q/2 doubled: its folded outputs (2E, 2O) are then exactly the
+  // even/odd parts of the result, ready to feed the next contraction along the same direction.
+  double Dte2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  double Dto2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
   // unfolded tables, row-major
   double B[HX_QMAX * HX_NMAX];
   double D[HX_QMAX * HX_NMAX];
