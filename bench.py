@@ -331,6 +331,8 @@ def run_hx(args, world, rank, local):
     clocks = clk.summary()
     del bh, xh
 
+    mixed = measure_mixed(hx, torch, op, b, x, args, t / args.steps, world) if not args.no_mixed else None
+
     line = None
     if rank == 0:
         cpu = None
@@ -360,6 +362,7 @@ def run_hx(args, world, rank, local):
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "mixed": mixed,
         }
     del op, mesh, b, x
     torch.cuda.empty_cache()
@@ -367,6 +370,58 @@ def run_hx(args, world, rank, local):
         line["sweep"] = run_sweep(hx, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_applies_f32(op, torch, x32, reps=20, warm=3):
+    """Average device time of the FP32 apply (element kernel + assembly) with CUDA events."""
+    y = torch.empty_like(x32)
+    s = torch.cuda.current_stream()
+    for _ in range(warm):
+        op.apply_f32(x32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        e0.record(s)
+        hx_apply = op.apply_f32(x32)
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.mean(times))
+
+
+def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
+    """Mixed precision on the same problem: FP64 refinement around FP32 Jacobi-PCG to the same 1e-10."""
+    p, q = args.p, args.p + 2
+    E, n_dof = hx.hx_op_info(op.handle)[:2]
+    xm = torch.empty_like(b)
+
+    def step():
+        op.set_coefficients(ALPHA, NU)
+        return hx.hx_solve_pcg_mixed(op.handle, b, xm, RTOL, 100000, args.inner_rtol)
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        info = step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_mix = reduce_max(e0.elapsed_time(e1) / 1e3, world) / args.steps
+    err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+    t32 = time_applies_f32(op, torch, b.float())
+    n = p + 1
+    geo = 7 * 4 * q ** 3 * E if args.geom == "stored" else 24 * 8 * E
+    bytes32 = 8 * n_dof + 4 * n ** 3 * E + geo
+    return {"solve_time_s": t_mix, "speedup_vs_fp64": t_fp64 / t_mix, "refinements": info["refinements"],
+            "inner_iterations": info["iterations"], "inner_rtol": args.inner_rtol,
+            "rel_residual_fp64": info["rel_residual"], "rel_diff_vs_fp64_solution": err,
+            "apply_f32_gdofs": n_dof / t32 / 1e9, "apply_f32_ms": 1e3 * t32,
+            "roofline_f32": {"bound": "hbm", "achieved": bytes32 / t32 / 1e9, "peak": HBM_GBS, "unit": "GB/s",
+                             "frac": bytes32 / t32 / 1e9 / HBM_GBS, "alg_bytes_per_launch": bytes32,
+                             "kernel": f"apply_kernel<float,P={p},Q={q}> (+ assembly, timed together)"}}
 
 
 def run_sweep(hx, torch):
@@ -407,6 +462,8 @@ def main():
     ap.add_argument("--geom", default="stored", choices=["stored", "onthefly"])
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--inner-rtol", type=float, default=1e-5)
     ap.add_argument("--cpu-elems", type=int, default=14)
     ap.add_argument("--ref-elems", type=int, default=6)
     ap.add_argument("--ref-iterations", type=int, default=100)

@@ -75,6 +75,7 @@ typedef struct hx_solve_info {
   double true_rel_residual;  /* ||P b - A_c x||_2 / ||P b||_2, recomputed with one extra apply */
   double b_norm;             /* ||P b||_2 */
   int kernel_launches;       /* kernels this solve enqueued (CUDA-graph replays included) */
+  int refinements;           /* hx_solve_pcg_mixed: FP64 refinement steps (0 for the FP64 solves) */
 } hx_solve_info;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -161,7 +162,8 @@ HX_API int64_t hx_op_launch_count(const hx_op* op);
 /* Sizes of the mesh an operator is built on; any output pointer may be NULL. */
 HX_API hx_status hx_op_info(const hx_op* op, int64_t* n_elem, int64_t* n_dof, int* p, int* q);
 
-/* Frees the operator (NULL is ignored). */
+/* Frees the operator (NULL is ignored).  Touches only the operator's own memory, so it is
+ * safe after its mesh has been destroyed (the operator can no longer be used then). */
 HX_API void hx_op_destroy(hx_op* op);
 
 /*
@@ -214,6 +216,30 @@ HX_API hx_status hx_solve_pcg(hx_op* op, const double* b, double* x, double rtol
  */
 HX_API hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, double rtol, int max_it,
                                    int use_x0, void* stream, hx_solve_info* info);
+
+/*
+ * Mixed-precision solve of A_c x = P b to the FP64 relative residual rtol:
+ * iterative refinement whose residual r = P b - A_c x, update x += |r| d and
+ * solution accumulate in FP64, while each correction d solves A_c d = r / |r|
+ * with an FP32 Jacobi-PCG (FP32 operator apply: the same sum-factorized
+ * kernels in FP32 with the FP32 rounding of the stored factors, or FP32
+ * on-the-fly geometry) to the relative residual inner_rtol (e.g. 1e-5).
+ * Not in the paper; it trades the B300's 1:64 FP64:FP32 rate for a few FP64
+ * residual applies.  max_it caps the total inner iterations; the solve also
+ * stops with HX_ERR_NOT_CONVERGED when two refinement steps in a row fail to
+ * halve the residual.  info->iterations = inner iterations in total,
+ * info->refinements = FP64 refinement steps, rel_residual = true_rel_residual =
+ * the final FP64 residual.  Arguments and synchronization as hx_solve_pcg.
+ * The first call allocates the FP32 workspace (FP32 factors, vectors).
+ */
+HX_API hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it,
+                                    double inner_rtol, void* stream, hx_solve_info* info);
+
+/*
+ * The FP32 operator of the mixed-precision solve, constrained form:
+ * y = P A P x + (I - P) x in FP32.  x, y: device, n_dof floats.  Stream-ordered.
+ */
+HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream);
 
 /*
  * Operator apply that allocates no device memory.  The paper has no

@@ -38,7 +38,7 @@ _P, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_doubl
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("true_rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("refinements", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -66,6 +66,8 @@ SIGNATURES = {
     "hx_op_load_vector": (_I, [_P, _P, _P, _P]),
     "hx_solve_pcg": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
+    "hx_solve_pcg_mixed": (_I, [_P, _P, _P, _D, _I, _D, _P, ctypes.POINTER(SolveInfo)]),
+    "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
     "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
 }
 
@@ -265,6 +267,30 @@ def hx_solve_pcg_host(op, b_host, x_host, rtol=1e-10, max_it=10000, use_x0=False
     return info.as_dict()
 
 
+def _fptr(t, n, name):
+    """Device pointer of a contiguous float32 CUDA tensor with n elements."""
+    if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.float32" or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hx_solve_pcg_mixed(op, b, x, rtol=1e-10, max_it=100000, inner_rtol=1e-5, stream=None, raise_on_fail=True):
+    n = hx_op_info(op)[1]
+    info = SolveInfo()
+    st = _lib.hx_solve_pcg_mixed(op, _dptr(b, n, "b"), _dptr(x, n, "x"), float(rtol), int(max_it), float(inner_rtol),
+                                 _stream(stream), ctypes.byref(info))
+    if raise_on_fail or st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_BREAKDOWN):
+        _check(st)
+    return info.as_dict()
+
+
+def hx_op_apply_f32(op, x, y, stream=None):
+    n = hx_op_info(op)[1]
+    _check(_lib.hx_op_apply_f32(op, _fptr(x, n, "x"), _fptr(y, n, "y"), _stream(stream)))
+
+
 def _iptr(t, n, name):
     """Device pointer of a contiguous int32 CUDA tensor with n elements."""
     if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.int32" or not t.is_contiguous():
@@ -355,6 +381,18 @@ class Operator:
         x = torch.zeros_like(b) if x is None else x
         info = hx_solve_pcg(self.handle, b, x, rtol, max_it, use_x0, stream, raise_on_fail)
         return x, info
+
+    def solve_mixed(self, b, rtol=1e-10, inner_rtol=1e-5, max_it=100000, stream=None, raise_on_fail=True):
+        import torch
+        x = torch.empty_like(b)
+        info = hx_solve_pcg_mixed(self.handle, b, x, rtol, max_it, inner_rtol, stream, raise_on_fail)
+        return x, info
+
+    def apply_f32(self, x, stream=None):
+        import torch
+        y = torch.empty_like(x)
+        hx_op_apply_f32(self.handle, x, y, stream)
+        return y
 
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None

@@ -181,3 +181,30 @@ int hx_build_tables(int p, int q, HxTables* t) {
   for (int i = 0; i < n; ++i) t->xn[i] = xn[i];
   return 0;
 }
+
+void hx_tables_to_float(const HxTables& d, HxTablesF* f) {
+  std::memset(f, 0, sizeof(*f));
+  f->p = d.p;
+  f->q = d.q;
+  auto cp = [](const double* a, float* b, int n) {
+    for (int i = 0; i < n; ++i) b[i] = (float)a[i];
+  };
+  const int H = HX_H(HX_QMAX) * HX_H(HX_QMAX);
+  cp(d.Be, f->Be, H);
+  cp(d.Bo, f->Bo, H);
+  cp(d.Bte, f->Bte, H);
+  cp(d.Bto, f->Bto, H);
+  cp(d.De, f->De, H);
+  cp(d.Do, f->Do, H);
+  cp(d.Dte, f->Dte, H);
+  cp(d.Dto, f->Dto, H);
+  cp(d.De2, f->De2, H);
+  cp(d.Do2, f->Do2, H);
+  cp(d.Dte2, f->Dte2, H);
+  cp(d.Dto2, f->Dto2, H);
+  cp(d.B, f->B, HX_QMAX * HX_NMAX);
+  cp(d.D, f->D, HX_QMAX * HX_NMAX);
+  cp(d.xq, f->xq, HX_QMAX);
+  cp(d.wq, f->wq, HX_QMAX);
+  cp(d.xn, f->xn, HX_NMAX);
+}

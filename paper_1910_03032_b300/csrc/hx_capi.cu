@@ -70,12 +70,12 @@ struct hx_mesh {
   int p = 0, q = 0, n = 0, N3 = 0, device = 0;
   long long E = 0, n_dof = 0;
   HxTables T;
+  HxTablesF T32;  // FP32 rounding of T (inner solver of the mixed-precision refinement)
   int* R = nullptr;              // [E][n^3], g or -(g+1) for Dirichlet
   int* off = nullptr;            // [n_dof + 1] transpose offsets
   int* idx = nullptr;            // [E n^3] E-vector positions, increasing per DoF
   unsigned char* dir = nullptr;  // [n_dof]
   double* X8 = nullptr;          // [E][8][3]
-  int n_ops = 0;
 };
 
 struct hx_op {
@@ -99,6 +99,14 @@ struct hx_op {
   cudaGraphExec_t graph = nullptr;
   bool graph_failed = false;
   long long launches = 0;  // kernels enqueued by this operator so far (graph replays included)
+  // FP32 inner solver of the mixed-precision refinement (allocated at the first mixed solve)
+  float* factors32 = nullptr;  // [E][7][Q3] FP32 rounding of the stored factors
+  float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
+  double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual
+  HxCgState* st32 = nullptr;
+  cudaGraphExec_t graph32 = nullptr;
+  bool graph32_failed = false;
+  bool mixed_stale = true;      // FP32 factors / diagonal need refreshing from the FP64 ones
 };
 
 namespace {
@@ -173,7 +181,8 @@ hx_status build_mesh(int p, int q, long long n_vert, const double* vert, long lo
   m->E = E;
   m->n_dof = n_dof;
   cudaGetDevice(&m->device);
-  if (hx_build_tables(p, q, &m->T) != 0) {
+  if (hx_build_tables(p, q, &m->T) == 0) hx_tables_to_float(m->T, &m->T32);
+  else {
     delete m;
     return fail(HX_ERR_UNSUPPORTED, "cannot build tables for p=%d q=%d", p, q);
   }
@@ -338,7 +347,16 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->scalars);
   dfree(op->counters);
   dfree(op->st);
-  if (op->mesh) op->mesh->n_ops -= 1;
+  if (op->graph32) cudaGraphExecDestroy(op->graph32);
+  dfree(op->factors32);
+  dfree(op->yE32);
+  dfree(op->d32);
+  dfree(op->r32);
+  dfree(op->p32);
+  dfree(op->Ap32);
+  dfree(op->dinv32);
+  dfree(op->rn2);
+  dfree(op->st32);
   delete op;
 }
 
@@ -401,7 +419,6 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
   hx_op* op = new (std::nothrow) hx_op();
   if (!op) return fail(HX_ERR_OOM, "host allocation failed");
   op->mesh = m;
-  m->n_ops += 1;
   op->geom = geom_mode;
   const long long Q3 = (long long)m->q * m->q * m->q;
   int* bad = nullptr;
@@ -452,6 +469,11 @@ hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const doubl
   int nl = 0;
   hx_status st = setup_coefficients(op, alpha, nu, nu_q, nullptr, (cudaStream_t)stream, &nl);
   if (st == HX_OK) op->launches += nl;
+  op->mixed_stale = true;
+  if (op->graph32) {
+    cudaGraphExecDestroy(op->graph32);
+    op->graph32 = nullptr;
+  }
   if (op->geom == HX_GEOM_ONTHEFLY && op->graph) {
     // the captured CG iterations carry alpha, nu (and the field pointer) as kernel
     // parameters: drop the graph so the next solve captures the new values
@@ -627,6 +649,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   inf.rel_residual = bn > 0 ? std::sqrt(cs.rr) / bn : 0.0;
   inf.true_rel_residual = bn > 0 ? std::sqrt(rn2) / bn : std::sqrt(rn2);
   inf.kernel_launches = (int)(op->launches - launches0);
+  inf.refinements = 0;
   if (info) *info = inf;
   if (cs.status == HX_ERR_NOT_CONVERGED)
     return fail(HX_ERR_NOT_CONVERGED, "not converged in %d iterations (rel. residual %.3e)", cs.iter, inf.rel_residual);
@@ -668,6 +691,243 @@ hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, dou
   HX_TRY(cudaStreamSynchronize(op->stream), "solver sync");
   g_err = msg;
   return r;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mixed precision: FP64 iterative refinement around an FP32 Jacobi-PCG
+// ---------------------------------------------------------------------------
+namespace {
+
+HxApplyArgsF apply_args32(const hx_op* op, const float* x, const int* done) {
+  const hx_mesh* m = op->mesh;
+  HxApplyArgsF a;
+  a.E = m->E;
+  a.R = m->R;
+  a.x = x;
+  a.yE = op->yE32;
+  a.factors = op->factors32;
+  a.X8 = m->X8;
+  a.nu_q = op->use_field ? op->nu_q : nullptr;
+  a.alpha = op->alpha;
+  a.nu = op->nu;
+  a.constrained = 1;
+  a.done = done;
+  return a;
+}
+
+cudaError_t element_apply32(const hx_op* op, const float* x, const int* done, cudaStream_t s) {
+  static const hx_apply32_launcher t[] = {nullptr, hx_launch_apply32_p1, hx_launch_apply32_p2, hx_launch_apply32_p3,
+                                          hx_launch_apply32_p4, hx_launch_apply32_p5, hx_launch_apply32_p6,
+                                          hx_launch_apply32_p7, hx_launch_apply32_p8};
+  const HxApplyArgsF a = apply_args32(op, x, done);
+  return t[op->mesh->p](op->mesh->T32, a, op->geom, s);
+}
+
+HxCgBuffersF cg_buffers32(const hx_op* op) {
+  const hx_mesh* m = op->mesh;
+  HxCgBuffersF b;
+  b.n = m->n_dof;
+  b.off = m->off;
+  b.idx = m->idx;
+  b.dir = m->dir;
+  b.x = op->d32;
+  b.r = op->r32;
+  b.p = op->p32;
+  b.Ap = op->Ap32;
+  b.dinv = op->dinv32;
+  b.yE = op->yE32;
+  b.partial = op->partial;
+  b.st = op->st32;
+  return b;
+}
+
+// FP32 workspace and the FP32 rounding of the stored factors and inverse diagonal.
+hx_status ensure_mixed(hx_op* op) {
+  const hx_mesh* m = op->mesh;
+  const long long n = m->n_dof;
+  hx_status s;
+  if (!op->st32) {
+    if ((s = dalloc(&op->yE32, (size_t)m->E * m->N3, "FP32 E-vector")) || (s = dalloc(&op->d32, n, "FP32 d")) ||
+        (s = dalloc(&op->r32, n, "FP32 r")) || (s = dalloc(&op->p32, n, "FP32 p")) ||
+        (s = dalloc(&op->Ap32, n, "FP32 Ap")) || (s = dalloc(&op->dinv32, n, "FP32 dinv")) ||
+        (s = dalloc(&op->rn2, 1, "residual norm")) || (s = dalloc(&op->st32, 1, "FP32 state")))
+      return s;
+    if (op->geom == HX_GEOM_STORED &&
+        (s = dalloc(&op->factors32, (size_t)m->E * 7 * m->q * m->q * m->q, "FP32 factors")))
+      return s;
+    HX_TRY(cudaMemsetAsync(op->st32, 0, sizeof(HxCgState), op->stream), "FP32 state init");
+  }
+  if (op->mixed_stale) {
+    if (op->geom == HX_GEOM_STORED)
+      HX_TRY(hx_launch_to_float((long long)m->E * 7 * m->q * m->q * m->q, op->factors, op->factors32, op->stream),
+             "FP32 factors");
+    HX_TRY(hx_launch_to_float(n, op->dinv, op->dinv32, op->stream), "FP32 dinv");
+    op->launches += (op->geom == HX_GEOM_STORED) ? 2 : 1;
+    op->mixed_stale = false;
+  }
+  return HX_OK;
+}
+
+cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s) {
+  const HxCgBuffersF b = cg_buffers32(op);
+  cudaError_t e = element_apply32(op, op->p32, &op->st32->done, s);
+  if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
+  if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
+  if (e == cudaSuccess) e = hx_launch_cg_direction(b, s);
+  return e;
+}
+
+void ensure_graph32(hx_op* op) {
+  if (op->graph32 || op->graph32_failed) return;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(op->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) e = cg_iteration32(op, op->stream);
+    cudaError_t e2 = cudaStreamEndCapture(op->stream, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&op->graph32, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    op->graph32 = nullptr;
+    op->graph32_failed = true;
+  }
+}
+
+// FP64 residual r = P b - A_c x into op->r, ||r||^2 into op->rn2 (x in op->x).
+hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_t st) {
+  const hx_mesh* m = op->mesh;
+  if (x_is_zero) {
+    HX_TRY(cudaMemsetAsync(op->Ap, 0, sizeof(double) * m->n_dof, st), "zero");
+  } else {
+    HX_TRY(element_apply(op, op->x, 1, nullptr, st), "refinement apply");
+    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st),
+           "refinement assembly");
+    op->launches += 2;
+  }
+  HX_TRY(hx_launch_ir_residual(m->n_dof, b, op->Ap, m->dir, op->r, op->partial, op->counters, op->rn2, st),
+         "refinement residual");
+  op->launches += 1;
+  return HX_OK;
+}
+
+hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
+                      cudaStream_t user, hx_solve_info* info) {
+  const hx_mesh* m = op->mesh;
+  hx_status s = ensure_solver(op);
+  if (s) return s;
+  cudaStream_t st = op->stream;
+  HX_TRY(cudaEventRecord(op->ev, user), "event record");
+  HX_TRY(cudaStreamWaitEvent(st, op->ev, 0), "stream wait");
+  if ((s = ensure_mixed(op))) return s;
+  ensure_graph32(op);
+  const long long launches0 = op->launches;
+  HX_TRY(cudaMemsetAsync(op->x, 0, sizeof(double) * m->n_dof, st), "x init");
+  if ((s = outer_residual(op, b, true, st))) return s;
+  double rn2 = 0.0;
+  HX_TRY(cudaMemcpyAsync(&rn2, op->rn2, sizeof(double), cudaMemcpyDeviceToHost, st), "norm read");
+  HX_TRY(cudaStreamSynchronize(st), "solver sync");
+  const double bn = std::sqrt(rn2);
+  double rel = bn > 0 ? 1.0 : 0.0, prev = rel;
+  int inner_total = 0, outer = 0, status = HX_OK, stalls = 0;
+  const HxCgBuffersF buf = cg_buffers32(op);
+  while (rel > rtol) {
+    if (inner_total >= max_it) {
+      status = HX_ERR_NOT_CONVERGED;
+      break;
+    }
+    // inner FP32 Jacobi-PCG on A_c d = r / ||r|| from d = 0
+    HX_TRY(hx_launch_ir_scale_down(m->n_dof, op->r, op->rn2, op->r32, st), "scale down");
+    HX_TRY(hx_launch_cg_init(buf, (const float*)op->r32, (const float*)nullptr, inner_rtol, max_it - inner_total, st),
+           "inner init");
+    HX_TRY(hx_launch_cg_start(buf, st), "inner start");
+    op->launches += 3;
+    for (;;) {
+      HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
+      HX_TRY(cudaStreamSynchronize(st), "solver sync");
+      if (op->st_host->done) break;
+      if (op->graph32) {
+        HX_TRY(cudaGraphLaunch(op->graph32, st), "graph launch");
+      } else {
+        for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration32(op, st), "inner iteration");
+      }
+      op->launches += 4 * kChunk;
+    }
+    const HxCgState cs = *op->st_host;
+    inner_total += cs.iter;
+    ++outer;
+    if (cs.status == HX_ERR_BREAKDOWN) {
+      status = HX_ERR_BREAKDOWN;
+      break;
+    }
+    // x += ||r|| d in FP64, then the FP64 residual of the new x
+    HX_TRY(hx_launch_ir_update(m->n_dof, op->x, op->d32, op->rn2, st), "refinement update");
+    op->launches += 1;
+    if ((s = outer_residual(op, b, false, st))) return s;
+    HX_TRY(cudaMemcpyAsync(&rn2, op->rn2, sizeof(double), cudaMemcpyDeviceToHost, st), "norm read");
+    HX_TRY(cudaStreamSynchronize(st), "solver sync");
+    rel = bn > 0 ? std::sqrt(rn2) / bn : 0.0;
+    if (!std::isfinite(rel)) {
+      status = HX_ERR_BREAKDOWN;
+      break;
+    }
+    // refinement that stops contracting (FP32 operator error above the target) ends the solve
+    stalls = (rel > 0.5 * prev) ? stalls + 1 : 0;
+    if (stalls >= 2 && rel > rtol) {
+      status = HX_ERR_NOT_CONVERGED;
+      break;
+    }
+    prev = rel;
+  }
+  HX_TRY(cudaMemcpyAsync(x, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, st), "solution copy");
+  HX_TRY(cudaStreamSynchronize(st), "solver sync");
+  hx_solve_info inf;
+  inf.iterations = inner_total;
+  inf.status = status;
+  inf.b_norm = bn;
+  inf.rel_residual = rel;
+  inf.true_rel_residual = rel;
+  inf.kernel_launches = (int)(op->launches - launches0);
+  inf.refinements = outer;
+  if (info) *info = inf;
+  if (status == HX_ERR_NOT_CONVERGED)
+    return fail(HX_ERR_NOT_CONVERGED, "mixed solve stopped at rel. residual %.3e after %d refinements", rel, outer);
+  if (status == HX_ERR_BREAKDOWN) return fail(HX_ERR_BREAKDOWN, "mixed solve breakdown");
+  return HX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
+                             void* stream, hx_solve_info* info) {
+  if (!op || !b || !x) return fail(HX_ERR_ARG, "NULL argument");
+  if (!(rtol >= 0.0) || max_it < 0 || !(inner_rtol > 0.0 && inner_rtol < 1.0))
+    return fail(HX_ERR_ARG, "need rtol >= 0, max_it >= 0 and 0 < inner_rtol < 1");
+  return solve_mixed(op, b, x, rtol, max_it, inner_rtol, (cudaStream_t)stream, info);
+}
+
+hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream) {
+  if (!op || !x || !y) return fail(HX_ERR_ARG, "NULL argument");
+  if ((const void*)x == (void*)y) return fail(HX_ERR_ARG, "x and y must not alias");
+  hx_status s = ensure_solver(op);
+  if (s) return s;
+  cudaStream_t us = (cudaStream_t)stream;
+  // the FP32 set-up runs on the solver stream; order it with the caller's stream both ways
+  HX_TRY(cudaEventRecord(op->ev, us), "event record");
+  HX_TRY(cudaStreamWaitEvent(op->stream, op->ev, 0), "stream wait");
+  if ((s = ensure_mixed(op))) return s;
+  HX_TRY(cudaEventRecord(op->ev, op->stream), "event record");
+  HX_TRY(cudaStreamWaitEvent(us, op->ev, 0), "stream wait");
+  const hx_mesh* m = op->mesh;
+  HX_TRY(element_apply32(op, x, nullptr, us), "FP32 element kernel");
+  HX_TRY(hx_launch_assemble32(m->n_dof, m->off, m->idx, op->yE32, m->dir, 1, x, y, us), "FP32 assembly");
+  op->launches += 2;
+  return HX_OK;
 }
 
 }  // extern "C"

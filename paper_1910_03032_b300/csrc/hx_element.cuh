@@ -30,9 +30,9 @@
 namespace hx {
 
 // sum_k S[k] v[k] (K >= 1 terms), first term a multiply
-template <int K>
-__device__ __forceinline__ double dotk(const double* __restrict__ S, const double* v) {
-  double s = S[0] * v[0];
+template <int K, typename Real>
+__device__ __forceinline__ Real dotk(const Real* __restrict__ S, const Real* v) {
+  Real s = S[0] * v[0];
 #pragma unroll
   for (int k = 1; k < K; ++k) s = fma(S[k], v[k], s);
   return s;
@@ -40,8 +40,8 @@ __device__ __forceinline__ double dotk(const double* __restrict__ S, const doubl
 
 // Even / odd parts of x: ev[b] = x[b] + x[L-1-b], od[b] = x[b] - x[L-1-b] (b < L/2),
 // ev[L/2] = x[L/2] for odd L.
-template <int L>
-__device__ __forceinline__ void fold(const double (&x)[L], double* ev, double* od) {
+template <int L, typename Real>
+__device__ __forceinline__ void fold(const Real (&x)[L], Real* ev, Real* od) {
   constexpr int HL = L / 2;
 #pragma unroll
   for (int b = 0; b < HL; ++b) {
@@ -54,9 +54,9 @@ __device__ __forceinline__ void fold(const double (&x)[L], double* ev, double* o
 // Folded products of a centro-(anti)symmetric M x L matrix with folded input:
 // E[a] = sum_b Se[a][b] ev[b], O[a] = sum_b So[a][b] od[b] for a < M/2; for odd M the
 // middle row has only its E part (SIGMA = +1) or only its O part (SIGMA = -1).
-template <int L, int M, int SIGMA>
-__device__ __forceinline__ void products(const double* __restrict__ Se, const double* __restrict__ So,
-                                         const double* ev, const double* od, double* E, double* O) {
+template <int L, int M, int SIGMA, typename Real>
+__device__ __forceinline__ void products(const Real* __restrict__ Se, const Real* __restrict__ So,
+                                         const Real* ev, const Real* od, Real* E, Real* O) {
   constexpr int HL = L / 2, CL = (L + 1) / 2, HM = M / 2;
 #pragma unroll
   for (int a = 0; a < HM; ++a) {
@@ -66,17 +66,17 @@ __device__ __forceinline__ void products(const double* __restrict__ Se, const do
   if (M & 1) {
     if (SIGMA > 0) {
       E[HM] = dotk<CL>(Se + HM * CL, ev);
-      O[HM] = 0.0;
+      O[HM] = Real(0);
     } else {
       O[HM] = dotk<HL>(So + HM * HL, od);
-      E[HM] = 0.0;
+      E[HM] = Real(0);
     }
   }
 }
 
 // y from folded parts: y[a] = E + O, y[M-1-a] = SIGMA (E - O); middle as in products.
-template <int M, int SIGMA>
-__device__ __forceinline__ void combine(const double* E, const double* O, double (&y)[M]) {
+template <int M, int SIGMA, typename Real>
+__device__ __forceinline__ void combine(const Real* E, const Real* O, Real (&y)[M]) {
   constexpr int HM = M / 2;
 #pragma unroll
   for (int a = 0; a < HM; ++a) {
@@ -88,22 +88,22 @@ __device__ __forceinline__ void combine(const double* E, const double* O, double
 
 // y = S x for a centro-symmetric (SIGMA = +1) or centro-antisymmetric
 // (SIGMA = -1) M x L matrix S given by its folded parts Se, So.
-template <int L, int M, int SIGMA>
-__device__ __forceinline__ void eo_apply(const double* __restrict__ Se, const double* __restrict__ So,
-                                         const double (&x)[L], double (&y)[M]) {
-  double ev[(L + 1) / 2], od[(L + 1) / 2], E[(M + 1) / 2], O[(M + 1) / 2];
+template <int L, int M, int SIGMA, typename Real>
+__device__ __forceinline__ void eo_apply(const Real* __restrict__ Se, const Real* __restrict__ So,
+                                         const Real (&x)[L], Real (&y)[M]) {
+  Real ev[(L + 1) / 2], od[(L + 1) / 2], E[(M + 1) / 2], O[(M + 1) / 2];
   fold<L>(x, ev, od);
   products<L, M, SIGMA>(Se, So, ev, od, E, O);
   combine<M, SIGMA>(E, O, y);
 }
 
-template <int L>
-__device__ __forceinline__ void load_line(const double* p, int stride, double (&v)[L]) {
+template <int L, typename Real>
+__device__ __forceinline__ void load_line(const Real* p, int stride, Real (&v)[L]) {
 #pragma unroll
   for (int i = 0; i < L; ++i) v[i] = p[i * stride];
 }
-template <int L>
-__device__ __forceinline__ void store_line(double* p, int stride, const double (&v)[L]) {
+template <int L, typename Real>
+__device__ __forceinline__ void store_line(Real* p, int stride, const Real (&v)[L]) {
 #pragma unroll
   for (int i = 0; i < L; ++i) p[i * stride] = v[i];
 }
@@ -114,7 +114,8 @@ __device__ __forceinline__ void store_line(double* p, int stride, const double (
 // Monomial coefficients of the map per component: x = a0 + a1 xi1 + a2 xi2 + a3 xi3
 // + a12 xi1 xi2 + a13 xi1 xi3 + a23 xi2 xi3 + a123 xi1 xi2 xi3, stored as
 // cf[comp * 8 + m] with m in (0, 1, 2, 3, 12, 13, 23, 123) order.
-__device__ __forceinline__ void trilinear_coeffs(const double* __restrict__ X8, double* cf) {
+template <typename Real>
+__device__ __forceinline__ void trilinear_coeffs(const double* __restrict__ X8, Real* cf) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     double X[8];
@@ -134,24 +135,25 @@ __device__ __forceinline__ void trilinear_coeffs(const double* __restrict__ X8, 
       s23 += sy * sz * X[c];
       s123 += sx * sy * sz * X[c];
     }
-    cf[d * 8 + 0] = 0.125 * s0;
-    cf[d * 8 + 1] = 0.125 * s1;
-    cf[d * 8 + 2] = 0.125 * s2;
-    cf[d * 8 + 3] = 0.125 * s3;
-    cf[d * 8 + 4] = 0.125 * s12;
-    cf[d * 8 + 5] = 0.125 * s13;
-    cf[d * 8 + 6] = 0.125 * s23;
-    cf[d * 8 + 7] = 0.125 * s123;
+    cf[d * 8 + 0] = Real(0.125 * s0);
+    cf[d * 8 + 1] = Real(0.125 * s1);
+    cf[d * 8 + 2] = Real(0.125 * s2);
+    cf[d * 8 + 3] = Real(0.125 * s3);
+    cf[d * 8 + 4] = Real(0.125 * s12);
+    cf[d * 8 + 5] = Real(0.125 * s13);
+    cf[d * 8 + 6] = Real(0.125 * s23);
+    cf[d * 8 + 7] = Real(0.125 * s123);
   }
 }
 
 // Columns j0 = dx/dxi1, j1 = dx/dxi2, j2 = dx/dxi3 at (x1, x2, x3).
-__device__ __forceinline__ void trilinear_jacobian(const double* cf, double x1, double x2, double x3,
-                                                   double (&j0)[3], double (&j1)[3], double (&j2)[3]) {
-  const double x23 = x2 * x3, x13 = x1 * x3, x12 = x1 * x2;
+template <typename Real>
+__device__ __forceinline__ void trilinear_jacobian(const Real* cf, Real x1, Real x2, Real x3, Real (&j0)[3],
+                                                   Real (&j1)[3], Real (&j2)[3]) {
+  const Real x23 = x2 * x3, x13 = x1 * x3, x12 = x1 * x2;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double* a = cf + d * 8;
+    const Real* a = cf + d * 8;
     j0[d] = a[1] + a[4] * x2 + a[5] * x3 + a[7] * x23;
     j1[d] = a[2] + a[4] * x1 + a[6] * x3 + a[7] * x13;
     j2[d] = a[3] + a[5] * x1 + a[6] * x2 + a[7] * x12;
@@ -168,10 +170,10 @@ __device__ __forceinline__ double trilinear_point(const double* cf, int d, doubl
 // Rows of J^-1 are (j1 x j2, j2 x j0, j0 x j1) / detJ, so
 // G_ik = (nu w / detJ) (c_i . c_k) with c the three cross products.
 // Returns detJ.
-__device__ __forceinline__ double point_factors(const double (&j0)[3], const double (&j1)[3],
-                                                const double (&j2)[3], double alpha_w, double nu_w,
-                                                double (&f)[7]) {
-  double c0[3], c1[3], c2[3];
+template <typename Real>
+__device__ __forceinline__ Real point_factors(const Real (&j0)[3], const Real (&j1)[3], const Real (&j2)[3],
+                                              Real alpha_w, Real nu_w, Real (&f)[7]) {
+  Real c0[3], c1[3], c2[3];
   c0[0] = j1[1] * j2[2] - j1[2] * j2[1];
   c0[1] = j1[2] * j2[0] - j1[0] * j2[2];
   c0[2] = j1[0] * j2[1] - j1[1] * j2[0];
@@ -181,8 +183,8 @@ __device__ __forceinline__ double point_factors(const double (&j0)[3], const dou
   c2[0] = j0[1] * j1[2] - j0[2] * j1[1];
   c2[1] = j0[2] * j1[0] - j0[0] * j1[2];
   c2[2] = j0[0] * j1[1] - j0[1] * j1[0];
-  const double det = j0[0] * c0[0] + j0[1] * c0[1] + j0[2] * c0[2];
-  const double s = nu_w / det;
+  const Real det = j0[0] * c0[0] + j0[1] * c0[1] + j0[2] * c0[2];
+  const Real s = nu_w / det;
   f[0] = alpha_w * det;
   f[1] = s * (c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
   f[2] = s * (c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2]);
@@ -198,15 +200,15 @@ __device__ __forceinline__ double point_factors(const double (&j0)[3], const dou
 // ---------------------------------------------------------------------------
 // After the z-direction transpose has left [kz][jq][iq] in region D: B^T along
 // y, then B^T along x written straight to the E-vector.
-template <int N, int Q, int NE, int NT>
-__device__ __forceinline__ void transpose_y_x_store(const HxTables& T, double* smem, long long e0, long long E,
-                                                    double* __restrict__ yE) {
+template <int N, int Q, int NE, int NT, typename Real>
+__device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Real* smem, long long e0, long long E,
+                                                    Real* __restrict__ yE) {
   constexpr int Q3 = Q * Q * Q, N3 = N * N * N, SY = Q, SZ = Q * Q, R3 = 3 * Q3;
   for (int t = threadIdx.x; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
     const int kz = r / Q, iq = r - kz * Q;
-    double* line = smem + el * R3 + kz * SZ + iq;
-    double vin[Q], vout[N];
+    Real* line = smem + el * R3 + kz * SZ + iq;
+    Real vin[Q], vout[N];
     load_line<Q>(line, SY, vin);
     eo_apply<Q, N, 1>(T.Bte, T.Bto, vin, vout);
     store_line<N>(line, SY, vout);
@@ -216,7 +218,7 @@ __device__ __forceinline__ void transpose_y_x_store(const HxTables& T, double* s
     const int el = t / (N * N), r = t - el * (N * N);
     const int kz = r / N, j = r - kz * N;
     const long long e = e0 + el;
-    double vin[Q], vout[N];
+    Real vin[Q], vout[N];
     load_line<Q>(smem + el * R3 + kz * SZ + j * SY, 1, vin);
     eo_apply<Q, N, 1>(T.Bte, T.Bto, vin, vout);
     if (e < E) store_line<N>(yE + e * N3 + r * N, 1, vout);
@@ -226,14 +228,16 @@ __device__ __forceinline__ void transpose_y_x_store(const HxTables& T, double* s
 // ---------------------------------------------------------------------------
 // the operator kernel
 // ---------------------------------------------------------------------------
-template <int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
-__global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__ HxTables T, const HxApplyArgs A) {
+template <typename Real, int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
+__global__ void __launch_bounds__(NT, MINB)
+    apply_kernel(const __grid_constant__ HxTablesT<Real> T, const HxApplyArgsT<Real> A) {
   constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q, SY = Q, SZ = Q2, R3 = 3 * Q3;
   constexpr int CQ = (Q + 1) / 2, CN = (N + 1) / 2;
   static_assert(NT >= NE * Q2, "one thread per z-column");
   if (A.done != nullptr && *(volatile const int*)A.done) return;
-  extern __shared__ double smem[];
-  double* geo = smem + NE * R3;  // on-the-fly: NE x 24 map coefficients
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* smem = reinterpret_cast<Real*>(smem_raw);
+  Real* geo = smem + NE * R3;  // on-the-fly: NE x 24 map coefficients
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
 
@@ -241,13 +245,13 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
     // pull this block's factors toward L2 while the forward contractions run
     const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
     const char* base = reinterpret_cast<const char*>(A.factors + e0 * 7 * Q3);
-    const long long bytes = nel * 7 * Q3 * (long long)sizeof(double);
+    const long long bytes = nel * 7 * Q3 * (long long)sizeof(Real);
     for (long long off = (long long)tid * 128; off < bytes; off += (long long)NT * 128)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
   } else {
     for (int el = tid; el < NE; el += NT) {
       const long long e = e0 + el;
-      double X8[24];
+      double X8[24];  // corner coordinates stay FP64 until the map coefficients are formed
       for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
       trilinear_coeffs(X8, geo + el * 24);
     }
@@ -256,20 +260,20 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
   for (int t = tid; t < NE * N * N; t += NT) {
     const int el = t / (N * N), r = t - el * (N * N);
     const long long e = e0 + el;
-    double vin[N];
+    Real vin[N];
     if (e < A.E) {
       const int* Rp = A.R + e * N3 + r * N;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int g = __ldg(Rp + i);
-        vin[i] = (g >= 0) ? __ldg(A.x + g) : (A.constrained ? 0.0 : __ldg(A.x + (-g - 1)));
+        vin[i] = (g >= 0) ? __ldg(A.x + g) : (A.constrained ? Real(0) : __ldg(A.x + (-g - 1)));
       }
     } else {
 #pragma unroll
       for (int i = 0; i < N; ++i) vin[i] = 0.0;
     }
     const int k = r / N, j = r - k * N;
-    double vout[Q];
+    Real vout[Q];
     eo_apply<N, Q, 1>(T.Be, T.Bo, vin, vout);
     store_line<Q>(smem + el * R3 + k * SZ + j * SY, 1, vout);
   }
@@ -278,8 +282,8 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
   for (int t = tid; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
     const int k = r / Q, iq = r - k * Q;
-    double* line = smem + el * R3 + k * SZ + iq;
-    double vin[N], vout[Q];
+    Real* line = smem + el * R3 + k * SZ + iq;
+    Real vin[N], vout[Q];
     load_line<N>(line, SY, vin);
     eo_apply<N, Q, 1>(T.Be, T.Bo, vin, vout);
     store_line<Q>(line, SY, vout);
@@ -289,10 +293,10 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
   //    du/dxi_3 from the folded parts of that same contraction (kept in registers)
   const bool owner = tid < NE * Q2;
   const int cel = tid / Q2, c = tid - cel * Q2;
-  double du[Q];
+  Real du[Q];
   if (owner) {
-    double* col = smem + cel * R3 + c;
-    double vin[N], u[Q], ev[CN], od[CN], Eu[CQ], Ou[CQ], Ed[CQ], Od[CQ];
+    Real* col = smem + cel * R3 + c;
+    Real vin[N], u[Q], ev[CN], od[CN], Eu[CQ], Ou[CQ], Ed[CQ], Od[CQ];
     load_line<N>(col, SZ, vin);
     fold<N>(vin, ev, od);
     products<N, Q, 1>(T.Be, T.Bo, ev, od, Eu, Ou);
@@ -310,7 +314,7 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
     const int a = rr / Q, b = rr - a * Q;
     const int off = dir ? (a * SZ + b) : (a * SZ + b * SY);
     const int stride = dir ? SY : 1;
-    double uu[Q], d[Q];
+    Real uu[Q], d[Q];
     load_line<Q>(smem + el * R3 + off, stride, uu);
     eo_apply<Q, Q, -1>(T.De, T.Do, uu, d);
     store_line<Q>(smem + el * R3 + (1 + dir) * Q3 + off, stride, d);
@@ -318,20 +322,20 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
   __syncthreads();
   // 5. columns: pointwise v = m u (into D, over u), w = G grad u; then Dh^T along z of
   //    w_3 (folded parts kept in registers)
-  double Et[CQ], Ot[CQ];
+  Real Et[CQ], Ot[CQ];
   if (owner) {
     const long long e = e0 + cel;
-    double* Dc = smem + cel * R3 + c;
-    double* Xc = Dc + Q3;
-    double* Yc = Xc + Q3;
-    double w3[Q];
+    Real* Dc = smem + cel * R3 + c;
+    Real* Xc = Dc + Q3;
+    Real* Yc = Xc + Q3;
+    Real w3[Q];
 #pragma unroll
     for (int kq = 0; kq < Q; ++kq) {
       const int pt = kq * Q2 + c;
-      double f[7];
+      Real f[7];
       if (GEOM == HX_KGEOM_STORED) {
         if (e < A.E) {
-          const double* fe = A.factors + e * 7 * Q3 + pt;
+          const Real* fe = A.factors + e * 7 * Q3 + pt;
 #pragma unroll
           for (int m = 0; m < 7; ++m) f[m] = __ldg(fe + m * Q3);
         } else {
@@ -340,26 +344,26 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
         }
       } else {
         const int iq = c % Q, jq = c / Q;
-        double j0[3], j1[3], j2[3];
+        Real j0[3], j1[3], j2[3];
         trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
-        const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
-        double nu = A.nu;
-        if (NUF) nu = (e < A.E) ? __ldg(A.nu_q + e * Q3 + pt) : 0.0;
-        point_factors(j0, j1, j2, A.alpha * w, nu * w, f);
+        const Real w = T.wq[iq] * T.wq[jq] * T.wq[kq];
+        Real nu = Real(A.nu);
+        if (NUF) nu = (e < A.E) ? Real(__ldg(A.nu_q + e * Q3 + pt)) : Real(0);
+        point_factors(j0, j1, j2, Real(A.alpha) * w, nu * w, f);
         if (e >= A.E) {
 #pragma unroll
           for (int m = 0; m < 7; ++m) f[m] = 0.0;
         }
       }
-      const double u1 = Xc[kq * SZ], u2 = Yc[kq * SZ], u3 = du[kq];
+      const Real u1 = Xc[kq * SZ], u2 = Yc[kq * SZ], u3 = du[kq];
       Dc[kq * SZ] = f[0] * Dc[kq * SZ];
       Xc[kq * SZ] = f[1] * u1 + f[2] * u2 + f[3] * u3;
       Yc[kq * SZ] = f[2] * u1 + f[4] * u2 + f[5] * u3;
       w3[kq] = f[3] * u1 + f[5] * u2 + f[6] * u3;
     }
-    double ev[CQ], od[CQ];
+    Real ev[CQ], od[CQ];
     fold<Q>(w3, ev, od);
-    products<Q, Q, -1>(T.Dte2, T.Dto2, ev, od, Et, Ot);  // rows doubled: (2E, 2O)
+    products<Q, Q, -1>(T.Dte2, T.Dto2, ev, od, Et, Ot);  // rows Reald: (2E, 2O)
   }
   __syncthreads();
   // 6. Dh^T along x (X, in place) and along y (Y, in place)
@@ -370,8 +374,8 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
     const int a = rr / Q, b = rr - a * Q;
     const int off = dir ? (a * SZ + b) : (a * SZ + b * SY);
     const int stride = dir ? SY : 1;
-    double* line = smem + el * R3 + (1 + dir) * Q3 + off;
-    double w[Q], tw[Q];
+    Real* line = smem + el * R3 + (1 + dir) * Q3 + off;
+    Real w[Q], tw[Q];
     load_line<Q>(line, stride, w);
     eo_apply<Q, Q, -1>(T.Dte, T.Dto, w, tw);
     store_line<Q>(line, stride, tw);
@@ -379,8 +383,8 @@ __global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__
   __syncthreads();
   // 7. columns: V = v + t1 + t2 + Dh^T w_3 formed directly in folded form, then B^T along z
   if (owner) {
-    double* Dc = smem + cel * R3 + c;
-    double sv[Q], es[CQ], os[CQ], E[(N + 1) / 2], O[(N + 1) / 2], out[N];
+    Real* Dc = smem + cel * R3 + c;
+    Real sv[Q], es[CQ], os[CQ], E[(N + 1) / 2], O[(N + 1) / 2], out[N];
 #pragma unroll
     for (int kq = 0; kq < Q; ++kq) sv[kq] = Dc[kq * SZ] + Dc[Q3 + kq * SZ] + Dc[2 * Q3 + kq * SZ];
     fold<Q>(sv, es, os);
@@ -555,23 +559,26 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
 // ---------------------------------------------------------------------------
 // launch configuration per order
 // ---------------------------------------------------------------------------
-template <int P, int Q>
+template <int P, int Q, typename Real = double>
 struct Config {
-  // elements per block of the operator kernel (3 q^3 doubles each: ~40-75 KB per block)
-  static constexpr int NE = P == 1 ? 64 : P == 2 ? 32 : P == 3 ? 16 : P == 4 ? 8 : P == 5 ? 6 : P == 6 ? 4 : P == 7 ? 3 : 2;
+  // elements per block of the operator kernel (3 q^3 values each: ~40-75 KB per block);
+  // FP32 blocks take twice the elements while the block stays within 1024 threads
+  static constexpr int NE_D = P == 1 ? 64 : P == 2 ? 32 : P == 3 ? 16 : P == 4 ? 8 : P == 5 ? 6 : P == 6 ? 4 : P == 7 ? 3 : 2;
+  static constexpr int NE = (sizeof(Real) == 4 && 2 * NE_D * Q * Q <= 1024) ? 2 * NE_D : NE_D;
   // one thread per z-column, rounded up to whole warps
   static constexpr int NT = ((NE * Q * Q + 31) / 32) * 32;
   static_assert(NT <= 1024, "block too large");
   // resident blocks per SM the register budget is sized for (shared memory allows at least this)
-  static constexpr int MINB = P >= 7 ? 3 : NT >= 512 ? 2 : NT >= 384 ? 3 : 4;
+  static constexpr int MINB = (sizeof(Real) == 8 && P >= 7) ? 3 : NT >= 512 ? 2 : NT >= 384 ? 3 : 4;
   static constexpr int NE_DIAG = P <= 2 ? 8 : P <= 4 ? 2 : 1;
 };
 
-template <int P, int Q, int GEOM, bool NUF>
-cudaError_t launch_apply_impl(const HxTables& T, const HxApplyArgs& A, cudaStream_t s) {
-  constexpr int NE = Config<P, Q>::NE, NT = Config<P, Q>::NT, MINB = Config<P, Q>::MINB;
-  const size_t shmem = sizeof(double) * (size_t)(NE * 3 * Q * Q * Q + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
-  auto k = apply_kernel<P, Q, NE, NT, MINB, GEOM, NUF>;
+template <typename Real, int P, int Q, int GEOM, bool NUF>
+cudaError_t launch_apply_impl(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, cudaStream_t s) {
+  using C = Config<P, Q, Real>;
+  constexpr int NE = C::NE, NT = C::NT, MINB = C::MINB;
+  const size_t shmem = sizeof(Real) * (size_t)(NE * 3 * Q * Q * Q + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+  auto k = apply_kernel<Real, P, Q, NE, NT, MINB, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
   const long long blocks = (A.E + NE - 1) / NE;
@@ -580,11 +587,11 @@ cudaError_t launch_apply_impl(const HxTables& T, const HxApplyArgs& A, cudaStrea
   return cudaGetLastError();
 }
 
-template <int P, int Q>
-cudaError_t launch_apply_q(const HxTables& T, const HxApplyArgs& A, int geom, cudaStream_t s) {
-  if (geom == HX_KGEOM_STORED) return launch_apply_impl<P, Q, HX_KGEOM_STORED, false>(T, A, s);
-  if (A.nu_q) return launch_apply_impl<P, Q, HX_KGEOM_ONTHEFLY, true>(T, A, s);
-  return launch_apply_impl<P, Q, HX_KGEOM_ONTHEFLY, false>(T, A, s);
+template <typename Real, int P, int Q>
+cudaError_t launch_apply_q(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, int geom, cudaStream_t s) {
+  if (geom == HX_KGEOM_STORED) return launch_apply_impl<Real, P, Q, HX_KGEOM_STORED, false>(T, A, s);
+  if (A.nu_q) return launch_apply_impl<Real, P, Q, HX_KGEOM_ONTHEFLY, true>(T, A, s);
+  return launch_apply_impl<Real, P, Q, HX_KGEOM_ONTHEFLY, false>(T, A, s);
 }
 
 template <int P, int Q, int GEOM, bool NUF>
@@ -626,8 +633,13 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
 
 #define HX_DEFINE_ORDER(P)                                                                                 \
   cudaError_t hx_launch_apply_p##P(const HxTables& T, const HxApplyArgs& A, int geom, cudaStream_t s) {   \
-    if (T.q == P + 1) return hx::launch_apply_q<P, P + 1>(T, A, geom, s);                                 \
-    if (T.q == P + 2) return hx::launch_apply_q<P, P + 2>(T, A, geom, s);                                 \
+    if (T.q == P + 1) return hx::launch_apply_q<double, P, P + 1>(T, A, geom, s);                         \
+    if (T.q == P + 2) return hx::launch_apply_q<double, P, P + 2>(T, A, geom, s);                         \
+    return cudaErrorInvalidValue;                                                                          \
+  }                                                                                                        \
+  cudaError_t hx_launch_apply32_p##P(const HxTablesF& T, const HxApplyArgsF& A, int geom, cudaStream_t s) { \
+    if (T.q == P + 1) return hx::launch_apply_q<float, P, P + 1>(T, A, geom, s);                          \
+    if (T.q == P + 2) return hx::launch_apply_q<float, P, P + 2>(T, A, geom, s);                          \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_diag_p##P(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {     \

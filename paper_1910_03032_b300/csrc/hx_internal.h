@@ -8,19 +8,23 @@
 #include "hx_tables.h"
 
 // Arguments of the element-operator kernel (gather -> contractions ->
-// pointwise -> transposed contractions -> E-vector).
-struct HxApplyArgs {
+// pointwise -> transposed contractions -> E-vector), in scalar type T
+// (double: the operator; float: the inner solver of the mixed-precision refinement).
+template <typename T>
+struct HxApplyArgsT {
   long long E;            // number of elements
   const int* R;           // [E][n^3] restriction; g >= 0 free DoF, -(g+1) Dirichlet DoF
-  const double* x;        // L-vector input
-  double* yE;             // [E][n^3] E-vector output
-  const double* factors;  // stored geometry: [E][7][q^3] (m, G00, G01, G02, G11, G12, G22)
+  const T* x;             // L-vector input
+  T* yE;                  // [E][n^3] E-vector output
+  const T* factors;       // stored geometry: [E][7][q^3] (m, G00, G01, G02, G11, G12, G22)
   const double* X8;       // [E][8][3] element corner coordinates (on-the-fly geometry)
   const double* nu_q;     // [E][q^3] per-point viscosity or null (on-the-fly geometry)
   double alpha, nu;       // Helmholtz coefficients (on-the-fly geometry)
   int constrained;        // 1: Dirichlet DoFs of x read as zero
   const int* done;        // optional device flag: kernel returns at once when *done != 0
 };
+typedef HxApplyArgsT<double> HxApplyArgs;
+typedef HxApplyArgsT<float> HxApplyArgsF;
 
 // Arguments of the diagonal kernel (sum-factorized diag of the element matrices).
 struct HxDiagArgs {
@@ -46,11 +50,13 @@ enum { HX_KGEOM_STORED = 0, HX_KGEOM_ONTHEFLY = 1 };
 typedef cudaError_t (*hx_apply_launcher)(const HxTables&, const HxApplyArgs&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_diag_launcher)(const HxTables&, const HxDiagArgs&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cudaStream_t);
+typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, cudaStream_t);
 
 #define HX_DECLARE_ORDER(P)                                                                        \
   cudaError_t hx_launch_apply_p##P(const HxTables&, const HxApplyArgs&, int, cudaStream_t);       \
   cudaError_t hx_launch_diag_p##P(const HxTables&, const HxDiagArgs&, int, cudaStream_t);         \
-  cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);
+  cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);              \
+  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, cudaStream_t);
 HX_DECLARE_ORDER(1)
 HX_DECLARE_ORDER(2)
 HX_DECLARE_ORDER(3)
@@ -91,31 +97,48 @@ struct HxCgState {
 #define HX_RED_BLOCKS 1184  // 8 x 148 SMs: fixed grid of every reduction kernel
 #define HX_RED_THREADS 256
 
-struct HxCgBuffers {
+template <typename Real>
+struct HxCgBuffersT {
   long long n;
   const int* off;
   const int* idx;
   const unsigned char* dir;
-  double* x;
-  double* r;
-  double* p;
-  double* Ap;
-  double* dinv;
-  double* yE;
+  Real* x;
+  Real* r;
+  Real* p;
+  Real* Ap;
+  Real* dinv;
+  Real* yE;
   double* partial;  // [2 * HX_RED_BLOCKS]
   HxCgState* st;
 };
+typedef HxCgBuffersT<double> HxCgBuffers;
+typedef HxCgBuffersT<float> HxCgBuffersF;
 
 cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s);
 cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
                                   double value, double* dst, cudaStream_t s);
-cudaError_t hx_launch_cg_init(const HxCgBuffers& b, const double* bvec, const double* x0, double rtol, int max_it,
+template <typename Real>
+cudaError_t hx_launch_cg_init(const HxCgBuffersT<Real>& b, const Real* bvec, const Real* x0, double rtol, int max_it,
                               cudaStream_t s);
-cudaError_t hx_launch_cg_residual(const HxCgBuffers& b, cudaStream_t s);
-cudaError_t hx_launch_cg_start(const HxCgBuffers& b, cudaStream_t s);
-cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffers& b, cudaStream_t s);
-cudaError_t hx_launch_cg_update(const HxCgBuffers& b, cudaStream_t s);
-cudaError_t hx_launch_cg_direction(const HxCgBuffers& b, cudaStream_t s);
+template <typename Real>
+cudaError_t hx_launch_cg_residual(const HxCgBuffersT<Real>& b, cudaStream_t s);
+template <typename Real>
+cudaError_t hx_launch_cg_start(const HxCgBuffersT<Real>& b, cudaStream_t s);
+template <typename Real>
+cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffersT<Real>& b, cudaStream_t s);
+template <typename Real>
+cudaError_t hx_launch_cg_update(const HxCgBuffersT<Real>& b, cudaStream_t s);
+template <typename Real>
+cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s);
+// mixed-precision refinement helpers
+cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
+                                 int constrained, const float* x, float* y, cudaStream_t s);
+cudaError_t hx_launch_ir_residual(long long n, const double* b, const double* Ax, const unsigned char* dir, double* r,
+                                  double* partial, unsigned int* counter, double* rn2, cudaStream_t s);
+cudaError_t hx_launch_ir_scale_down(long long n, const double* r, const double* rn2, float* r32, cudaStream_t s);
+cudaError_t hx_launch_ir_update(long long n, double* x, const float* d, const double* rn2, cudaStream_t s);
+cudaError_t hx_launch_to_float(long long n, const double* a, float* b, cudaStream_t s);
 cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,
                           double* out, cudaStream_t s);
 cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,

@@ -137,10 +137,11 @@ __global__ void __launch_bounds__(kThreads) node_kernel(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 // E -> L assembly through the transpose map (atomic-free, fixed summation order)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double gather_sum(long long g, const int* __restrict__ off, const int* __restrict__ idx,
-                                             const double* __restrict__ yE) {
+template <typename Real>
+__device__ __forceinline__ Real gather_sum(long long g, const int* __restrict__ off, const int* __restrict__ idx,
+                                           const Real* __restrict__ yE) {
   const int k0 = __ldg(off + g), k1 = __ldg(off + g + 1);
-  double s = 0.0;
+  Real s = Real(0);
   for (int k = k0; k < k1; ++k) s += __ldg(yE + __ldg(idx + k));
   return s;
 }
@@ -148,14 +149,15 @@ __device__ __forceinline__ double gather_sum(long long g, const int* __restrict_
 #define HX_GRID_STRIDE(g, n) \
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (n); g += (long long)gridDim.x * blockDim.x)
 
+template <typename Real>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const int* __restrict__ off,
-                                                             const int* __restrict__ idx, const double* __restrict__ yE,
+                                                             const int* __restrict__ idx, const Real* __restrict__ yE,
                                                              const unsigned char* __restrict__ dir, int constrained,
-                                                             const double* __restrict__ x, double dir_const,
-                                                             double* __restrict__ y) {
+                                                             const Real* __restrict__ x, double dir_const,
+                                                             Real* __restrict__ y) {
   HX_GRID_STRIDE(g, n) {
-    double s;
-    if (constrained && dir[g]) s = x ? x[g] : dir_const;
+    Real s;
+    if (constrained && dir[g]) s = x ? x[g] : Real(dir_const);
     else s = gather_sum(g, off, idx, yE);
     y[g] = s;
   }
@@ -173,18 +175,21 @@ __global__ void __launch_bounds__(kThreads) masked_copy_kernel(long long n, cons
 }
 
 // ---------------------------------------------------------------------------
-// Jacobi-PCG (Sec. 5.3: CG on the SPD Helmholtz / Poisson systems), fused passes
+// Jacobi-PCG (Sec. 5.3: CG on the SPD Helmholtz / Poisson systems), fused passes.
+// Vectors in Real (double: the FP64 solver; float: the inner solver of the
+// mixed-precision refinement); every reduction accumulates in double.
 // ---------------------------------------------------------------------------
 // x = P x0 (or 0), r = P b; sums ||P b||^2.
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffers B, const double* __restrict__ b,
-                                                                  const double* __restrict__ x0, double rtol, int max_it) {
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffersT<Real> B, const Real* __restrict__ b,
+                                                                  const Real* __restrict__ x0, double rtol, int max_it) {
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, B.n) {
     const bool d = B.dir[g];
-    const double bg = d ? 0.0 : b[g];
+    const Real bg = d ? Real(0) : b[g];
     B.r[g] = bg;
-    B.x[g] = (x0 && !d) ? x0[g] : 0.0;
-    acc[0] += bg * bg;
+    B.x[g] = (x0 && !d) ? x0[g] : Real(0);
+    acc[0] += (double)bg * (double)bg;
   }
   double out[1];
   if (last_block_reduce<1>(acc, B.partial, &B.st->count[0], out) && threadIdx.x == 0) {
@@ -201,18 +206,20 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffers B, 
 }
 
 // r -= A_c x (after an apply of the initial guess into Ap).
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffers B) {
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffersT<Real> B) {
   HX_GRID_STRIDE(g, B.n) { B.r[g] -= B.Ap[g]; }
 }
 
 // z = D^-1 r, p = z; rz = (r, z), rr = (r, r); finishes at once if rr <= tol^2 ||b||^2.
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffers B) {
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffersT<Real> B) {
   double acc[2] = {0.0, 0.0};
   HX_GRID_STRIDE(g, B.n) {
-    const double r = B.r[g], z = B.dinv[g] * r;
+    const Real r = B.r[g], z = B.dinv[g] * r;
     B.p[g] = z;
-    acc[0] += r * z;
-    acc[1] += r * r;
+    acc[0] += (double)r * (double)z;
+    acc[1] += (double)r * (double)r;
   }
   double out[2];
   if (last_block_reduce<2>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
@@ -229,14 +236,15 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffers B)
 }
 
 // Ap = assemble(yE) with Dirichlet rows Ap = p; pAp = (p, Ap); alpha = rz / pAp.
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuffers B) {
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuffersT<Real> B) {
   if (*(volatile int*)&B.st->done) return;
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, B.n) {
-    const double pg = B.p[g];
-    const double ap = B.dir[g] ? pg : gather_sum(g, B.off, B.idx, B.yE);
+    const Real pg = B.p[g];
+    const Real ap = B.dir[g] ? pg : gather_sum(g, B.off, B.idx, B.yE);
     B.Ap[g] = ap;
-    acc[0] += pg * ap;
+    acc[0] += (double)pg * (double)ap;
   }
   double out[1];
   if (last_block_reduce<1>(acc, B.partial, &B.st->count[2], out) && threadIdx.x == 0) {
@@ -251,17 +259,18 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuf
 }
 
 // x += alpha p, r -= alpha Ap, z = D^-1 r; rr = (r, r), rz' = (r, z); convergence test.
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffers B) {
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<Real> B) {
   if (*(volatile int*)&B.st->done) return;
-  const double a = B.st->alpha;
+  const Real a = Real(B.st->alpha);
   double acc[2] = {0.0, 0.0};
   HX_GRID_STRIDE(g, B.n) {
-    const double pg = B.p[g];
+    const Real pg = B.p[g];
     B.x[g] += a * pg;
-    const double r = B.r[g] - a * B.Ap[g];
+    const Real r = B.r[g] - a * B.Ap[g];
     B.r[g] = r;
-    acc[0] += r * r;
-    acc[1] += r * (B.dinv[g] * r);
+    acc[0] += (double)r * (double)r;
+    acc[1] += (double)r * (double)(B.dinv[g] * r);
   }
   double out[2];
   if (last_block_reduce<2>(acc, B.partial, &B.st->count[3], out) && threadIdx.x == 0) {
@@ -284,10 +293,49 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffers B
 }
 
 // p = D^-1 r + beta p.
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffers B) {
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffersT<Real> B) {
   if (*(volatile int*)&B.st->done) return;
-  const double beta = B.st->beta;
+  const Real beta = Real(B.st->beta);
   HX_GRID_STRIDE(g, B.n) { B.p[g] = B.dinv[g] * B.r[g] + beta * B.p[g]; }
+}
+
+// ---------------------------------------------------------------------------
+// mixed-precision iterative refinement (FP64 outer residual, FP32 inner CG)
+// ---------------------------------------------------------------------------
+// r = P b - Ax (FP64), out = ||r||^2.
+__global__ void __launch_bounds__(HX_RED_THREADS) ir_residual_kernel(long long n, const double* __restrict__ b,
+                                                                      const double* __restrict__ Ax,
+                                                                      const unsigned char* __restrict__ dir,
+                                                                      double* __restrict__ r, double* partial,
+                                                                      unsigned int* counter, double* out) {
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, n) {
+    const double v = dir[g] ? 0.0 : b[g] - Ax[g];
+    r[g] = v;
+    acc[0] += v * v;
+  }
+  double res[1];
+  if (last_block_reduce<1>(acc, partial, counter, res) && threadIdx.x == 0) *out = res[0];
+}
+
+// r32 = r / ||r|| rounded to FP32 (||r||^2 read from the device).
+__global__ void __launch_bounds__(kThreads) ir_scale_down_kernel(long long n, const double* __restrict__ r,
+                                                                  const double* __restrict__ rn2, float* __restrict__ r32) {
+  const double inv = (*rn2 > 0.0) ? 1.0 / sqrt(*rn2) : 0.0;
+  HX_GRID_STRIDE(g, n) { r32[g] = (float)(r[g] * inv); }
+}
+
+// x += ||r|| d (FP64 accumulation of the FP32 correction).
+__global__ void __launch_bounds__(kThreads) ir_update_kernel(long long n, double* __restrict__ x,
+                                                              const float* __restrict__ d, const double* __restrict__ rn2) {
+  const double s = sqrt(*rn2);
+  HX_GRID_STRIDE(g, n) { x[g] += s * (double)d[g]; }
+}
+
+__global__ void __launch_bounds__(kThreads) to_float_kernel(long long n, const double* __restrict__ a,
+                                                             float* __restrict__ b) {
+  HX_GRID_STRIDE(g, n) { b[g] = (float)a[g]; }
 }
 
 __global__ void __launch_bounds__(HX_RED_THREADS) dot_kernel(long long n, const double* __restrict__ a,
@@ -348,7 +396,13 @@ cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int*
 
 cudaError_t hx_launch_assemble(long long n, const int* off, const int* idx, const double* yE, const unsigned char* dir,
                                int constrained, const double* x, double dir_const, double* y, cudaStream_t s) {
-  assemble_kernel<<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, dir_const, y);
+  assemble_kernel<double><<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, dir_const, y);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
+                                 int constrained, const float* x, float* y, cudaStream_t s) {
+  assemble_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, 0.0, y);
   return cudaGetLastError();
 }
 
@@ -363,29 +417,62 @@ cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned
   return cudaGetLastError();
 }
 
-cudaError_t hx_launch_cg_init(const HxCgBuffers& b, const double* bvec, const double* x0, double rtol, int max_it,
+template <typename Real>
+cudaError_t hx_launch_cg_init(const HxCgBuffersT<Real>& b, const Real* bvec, const Real* x0, double rtol, int max_it,
                               cudaStream_t s) {
-  cg_init_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b, bvec, x0, rtol, max_it);
+  cg_init_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b, bvec, x0, rtol, max_it);
   return cudaGetLastError();
 }
-cudaError_t hx_launch_cg_residual(const HxCgBuffers& b, cudaStream_t s) {
-  cg_residual_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+template <typename Real>
+cudaError_t hx_launch_cg_residual(const HxCgBuffersT<Real>& b, cudaStream_t s) {
+  cg_residual_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
-cudaError_t hx_launch_cg_start(const HxCgBuffers& b, cudaStream_t s) {
-  cg_start_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+template <typename Real>
+cudaError_t hx_launch_cg_start(const HxCgBuffersT<Real>& b, cudaStream_t s) {
+  cg_start_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
-cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffers& b, cudaStream_t s) {
-  cg_assemble_pap_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+template <typename Real>
+cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffersT<Real>& b, cudaStream_t s) {
+  cg_assemble_pap_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
-cudaError_t hx_launch_cg_update(const HxCgBuffers& b, cudaStream_t s) {
-  cg_update_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+template <typename Real>
+cudaError_t hx_launch_cg_update(const HxCgBuffersT<Real>& b, cudaStream_t s) {
+  cg_update_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
-cudaError_t hx_launch_cg_direction(const HxCgBuffers& b, cudaStream_t s) {
-  cg_direction_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+template <typename Real>
+cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s) {
+  cg_direction_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+#define HX_CG_INSTANTIATE(R)                                                                              \
+  template cudaError_t hx_launch_cg_init<R>(const HxCgBuffersT<R>&, const R*, const R*, double, int, cudaStream_t); \
+  template cudaError_t hx_launch_cg_residual<R>(const HxCgBuffersT<R>&, cudaStream_t);                 \
+  template cudaError_t hx_launch_cg_start<R>(const HxCgBuffersT<R>&, cudaStream_t);                    \
+  template cudaError_t hx_launch_cg_assemble_pap<R>(const HxCgBuffersT<R>&, cudaStream_t);             \
+  template cudaError_t hx_launch_cg_update<R>(const HxCgBuffersT<R>&, cudaStream_t);                   \
+  template cudaError_t hx_launch_cg_direction<R>(const HxCgBuffersT<R>&, cudaStream_t);
+HX_CG_INSTANTIATE(double)
+HX_CG_INSTANTIATE(float)
+
+cudaError_t hx_launch_ir_residual(long long n, const double* b, const double* Ax, const unsigned char* dir, double* r,
+                                  double* partial, unsigned int* counter, double* rn2, cudaStream_t s) {
+  ir_residual_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, b, Ax, dir, r, partial, counter, rn2);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_ir_scale_down(long long n, const double* r, const double* rn2, float* r32, cudaStream_t s) {
+  ir_scale_down_kernel<<<grid_for(n), kThreads, 0, s>>>(n, r, rn2, r32);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_ir_update(long long n, double* x, const float* d, const double* rn2, cudaStream_t s) {
+  ir_update_kernel<<<grid_for(n), kThreads, 0, s>>>(n, x, d, rn2);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_to_float(long long n, const double* a, float* b, cudaStream_t s) {
+  to_float_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, b);
   return cudaGetLastError();
 }
 cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,

@@ -21,38 +21,46 @@
 #define HX_NMAX (HX_PMAX + 1)
 #define HX_H(x) (((x) + 1) / 2)
 
-struct HxTables {
+template <typename T>
+struct HxTablesT {
   int p, q;
   // folded B (sigma = +1): M = q, L = n
-  double Be[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
-  double Bo[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
+  T Be[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
+  T Bo[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
   // folded B^T (sigma = +1): M = n, L = q
-  double Bte[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
-  double Bto[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
+  T Bte[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
+  T Bto[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
   // folded Dh (sigma = -1): M = L = q
-  double De[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  double Do[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T De[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Do[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
   // folded Dh^T (sigma = -1)
-  double Dte[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  double Dto[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Dte[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Dto[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
   // Dh applied to an input given by the folded parts (E, O) of a centro-symmetric
   // interpolation along the same direction: the input's even/odd parts are 2E and 2O
   // (E alone for the middle entry of odd q), so the columns b < q/2 are doubled.
-  double De2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  double Do2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T De2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Do2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
   // Dh^T with the rows a < q/2 doubled: its folded outputs (2E, 2O) are then exactly the
   // even/odd parts of the result, ready to feed the next contraction along the same direction.
-  double Dte2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  double Dto2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Dte2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Dto2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
   // unfolded tables, row-major
-  double B[HX_QMAX * HX_NMAX];
-  double D[HX_QMAX * HX_NMAX];
-  double xq[HX_QMAX];    // Gauss points on [-1, 1]
-  double wq[HX_QMAX];    // Gauss weights
-  double xn[HX_NMAX];    // Gauss-Lobatto nodes
+  T B[HX_QMAX * HX_NMAX];
+  T D[HX_QMAX * HX_NMAX];
+  T xq[HX_QMAX];    // Gauss points on [-1, 1]
+  T wq[HX_QMAX];    // Gauss weights
+  T xn[HX_NMAX];    // Gauss-Lobatto nodes
 };
+
+// FP64 tables (the operator path) and their FP32 rounding (the inner solver of
+// the mixed-precision refinement)
+typedef HxTablesT<double> HxTables;
+typedef HxTablesT<float> HxTablesF;
 
 #ifdef __cplusplus
 // Host construction (basis.cpp). Returns 0 on success.
 int hx_build_tables(int p, int q, HxTables* t);
+// Round every table entry to FP32.
+void hx_tables_to_float(const HxTables& d, HxTablesF* f);
 #endif

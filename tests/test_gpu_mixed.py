@@ -1,0 +1,86 @@
+"""Mixed precision (FP64 iterative refinement around an FP32 Jacobi-PCG) vs the FP64 oracle.
+
+Tolerances.  FP32 operator apply: relative 2e-5 in the 2-norm (FP32 unit
+roundoff 6e-8 times the ~10^2 terms of each sum-factorized output, on inputs
+rounded to FP32 before the oracle sees them).  Mixed solve: the FP64
+residual it reports is recomputed in FP64, so the 1e-10 target is checked
+exactly as for the FP64 solver; its solution must agree with the oracle's
+FP64 solution to 1e-8 (both solved to 1e-10).
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from tests.gpu_common import case, mms_exact, rel_err, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hx():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("p,shape", [(1, (5, 5, 3)), (2, (5, 5, 3)), (3, (5, 5, 3)), (4, (5, 3, 3)), (5, (4, 3, 2)),
+                                     (6, (3, 3, 1)), (7, (2, 2, 2)), (8, (3, 3, 1))])
+@pytest.mark.parametrize("geom", [0, 1])
+def test_fp32_apply_matches_oracle(hx, p, shape, geom):
+    from oracle import fem
+    V, EV, om = case(shape, p)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1.7, 0.45, geom_mode=geom)
+    x32 = S.random_vector(om.n_dof, 3032).astype(np.float32)
+    y = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
+    ref = fem.Operator(om, 1.7, 0.45).apply(x32.astype(np.float64), constrained=True)
+    assert rel_err(y, ref) <= 2e-5, rel_err(y, ref)
+
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("geom", [0, 1])
+def test_mixed_solve_reaches_fp64_tolerance(hx, p, geom):
+    """4^3 perturbed mesh, alpha = nu = 1, manufactured right-hand side (the small config at p = 4..8)."""
+    from oracle import fem
+    from oracle.solve import jacobi_pcg
+    shape = (4, 4, 4) if p <= 5 else (3, 3, 3)
+    V, EV, om = case(shape, p)
+    mesh = hx.Mesh.structured(*shape, p, p + 2, V)
+    op = hx.Operator(mesh, 1.0, 1.0, geom_mode=geom)
+    f = (1.0 + 3 * np.pi ** 2) * mms_exact(mesh.qpoint_coords().cpu().numpy())
+    b = op.load_vector(to_dev(f))
+    x, info = op.solve_mixed(b, rtol=1e-10, inner_rtol=1e-5)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    assert 1 <= info["refinements"] <= 6
+    # the residual it reports is the FP64 one: recompute it independently
+    r = torch.where(torch.as_tensor(om.dirichlet, device="cuda"), torch.zeros_like(b), b) - op.apply(x, constrained=True)
+    bn = torch.linalg.norm(torch.where(torch.as_tensor(om.dirichlet, device="cuda"), torch.zeros_like(b), b))
+    assert float(torch.linalg.norm(r) / bn) <= 1.01e-10
+    uo, its, rel, conv = jacobi_pcg(fem.Operator(om, 1.0, 1.0), b.cpu().numpy(), 1e-10)
+    assert rel_err(x.cpu().numpy(), uo) <= 1e-8
+
+
+@pytest.mark.parametrize("geom", [0, 1])
+def test_mixed_solve_helmholtz_time_step(hx, geom):
+    """alpha = 1/dt = 1000, nu = 1e-2 (the sweep's coefficients) on an 8^3 Q_4 mesh, random RHS."""
+    p, shape = 4, (8, 8, 8)
+    V, EV, om = case(shape, p)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1000.0, 1e-2, geom_mode=geom)
+    b = to_dev(S.random_vector(om.n_dof, 77))
+    x64, i64 = op.solve(b, rtol=1e-10)
+    x, info = op.solve_mixed(b, rtol=1e-10)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    assert rel_err(x.cpu().numpy(), x64.cpu().numpy()) <= 1e-8
+    # a second solve after new coefficients refreshes the FP32 factors
+    op.set_coefficients(10.0, 0.5)
+    x2, info2 = op.solve_mixed(b, rtol=1e-10)
+    x2_64, _ = op.solve(b, rtol=1e-10)
+    assert info2["status"] == 0 and rel_err(x2.cpu().numpy(), x2_64.cpu().numpy()) <= 1e-8
+
+
+def test_mixed_solve_status(hx):
+    p, shape = 2, (3, 3, 3)
+    V, EV, om = case(shape, p)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1.0, 1.0)
+    b = to_dev(S.random_vector(om.n_dof, 2))
+    x, info = op.solve_mixed(b, rtol=1e-10, max_it=2, raise_on_fail=False)
+    assert info["status"] == hx.HX_ERR_NOT_CONVERGED
+    x, info = op.solve_mixed(torch.zeros_like(b))
+    assert info["status"] == 0 and info["refinements"] == 0 and not x.any()

@@ -213,3 +213,12 @@ def test_argument_errors(hx):
     with pytest.raises(hx.HxError) as ei:
         hx.Mesh.general(2, 4, V, S.structured_elem_vert(1, 1, 1), 27, np.full((1, 27), 99, np.int64))
     assert ei.value.status == hx.HX_ERR_ARG
+
+
+def test_destroy_mesh_before_operator(hx):
+    """Freeing the mesh first and the operator afterwards touches no freed memory."""
+    V = S.structured_vertices(2, 2, 2, 0.1, 3)
+    m = hx.hx_mesh_create_structured(2, 2, 2, 2, 4, V)
+    op = hx.hx_op_create(m, 1.0, 1.0)
+    hx.hx_mesh_destroy(m)
+    hx.hx_op_destroy(op)
