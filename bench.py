@@ -432,6 +432,7 @@ def run_sweep(hx, torch):
         for geom in ("stored", "onthefly"):
             mesh, op, b = make_problem(hx, torch, p, N, geom)
             t_med, t_mean = time_applies(op, torch, b)
+            t32 = time_applies_f32(op, torch, b.float())
             x = torch.zeros_like(b)
             run_step(op, b, x)  # warm
             torch.cuda.synchronize()
@@ -445,6 +446,7 @@ def run_sweep(hx, torch):
                         "alg_tflops": flops / t_mean / 1e12, "fp64_frac": flops / t_mean / 1e12 / FP64_PEAK_TFLOPS,
                         "pcg_s": t_pcg, "pcg_iterations": info["iterations"],
                         "pcg_gdofs": mesh.n_dof * (info["iterations"] + 1) / t_pcg / 1e9,
+                        "apply_f32_gdofs": mesh.n_dof / t32 / 1e9,
                         "true_rel_residual": info["true_rel_residual"]})
             del op, mesh, b, x
             torch.cuda.empty_cache()

@@ -196,14 +196,28 @@ __device__ __forceinline__ Real point_factors(const Real (&j0)[3], const Real (&
 }
 
 // ---------------------------------------------------------------------------
-// stages shared by the apply and load-vector kernels (region D at stride R3)
+// shared-memory layout of one element's q^3 region: [z][y][x] with row stride
+// SY (q rounded up to odd, so x-line tasks of consecutive threads fall in
+// different banks) and plane stride SZ = q SY
+// ---------------------------------------------------------------------------
+template <int Q>
+struct Layout {
+  static constexpr int SY = (Q % 2 == 0) ? Q + 1 : Q;
+  static constexpr int SZ = Q * SY;
+  static constexpr int RG = Q * SZ;  // one region
+  static constexpr int R3 = 3 * RG;  // the three regions D, X, Y of one element
+};
+
+// ---------------------------------------------------------------------------
+// stages shared by the apply and load-vector kernels (region D of each element)
 // ---------------------------------------------------------------------------
 // After the z-direction transpose has left [kz][jq][iq] in region D: B^T along
 // y, then B^T along x written straight to the E-vector.
 template <int N, int Q, int NE, int NT, typename Real>
 __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Real* smem, long long e0, long long E,
                                                     Real* __restrict__ yE) {
-  constexpr int Q3 = Q * Q * Q, N3 = N * N * N, SY = Q, SZ = Q * Q, R3 = 3 * Q3;
+  using Lt = Layout<Q>;
+  constexpr int N3 = N * N * N, SY = Lt::SY, SZ = Lt::SZ, R3 = Lt::R3;
   for (int t = threadIdx.x; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
     const int kz = r / Q, iq = r - kz * Q;
@@ -231,7 +245,9 @@ __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Re
 template <typename Real, int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
 __global__ void __launch_bounds__(NT, MINB)
     apply_kernel(const __grid_constant__ HxTablesT<Real> T, const HxApplyArgsT<Real> A) {
-  constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q, SY = Q, SZ = Q2, R3 = 3 * Q3;
+  using Lt = Layout<Q>;
+  constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q;
+  constexpr int SY = Lt::SY, SZ = Lt::SZ, RG = Lt::RG, R3 = Lt::R3;
   constexpr int CQ = (Q + 1) / 2, CN = (N + 1) / 2;
   static_assert(NT >= NE * Q2, "one thread per z-column");
   if (A.done != nullptr && *(volatile const int*)A.done) return;
@@ -270,7 +286,7 @@ __global__ void __launch_bounds__(NT, MINB)
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < N; ++i) vin[i] = 0.0;
+      for (int i = 0; i < N; ++i) vin[i] = Real(0);
     }
     const int k = r / N, j = r - k * N;
     Real vout[Q];
@@ -292,10 +308,11 @@ __global__ void __launch_bounds__(NT, MINB)
   // 3. columns: B along z -> u (stored for the x/y derivatives);
   //    du/dxi_3 from the folded parts of that same contraction (kept in registers)
   const bool owner = tid < NE * Q2;
-  const int cel = tid / Q2, c = tid - cel * Q2;
+  const int cel = tid / Q2, c = tid - cel * Q2;         // element, column (jq, iq) = (c / q, c % q)
+  const int cs = (c / Q) * SY + (c % Q);                // the column's offset in a region
   Real du[Q];
   if (owner) {
-    Real* col = smem + cel * R3 + c;
+    Real* col = smem + cel * R3 + cs;
     Real vin[N], u[Q], ev[CN], od[CN], Eu[CQ], Ou[CQ], Ed[CQ], Od[CQ];
     load_line<N>(col, SZ, vin);
     fold<N>(vin, ev, od);
@@ -317,7 +334,7 @@ __global__ void __launch_bounds__(NT, MINB)
     Real uu[Q], d[Q];
     load_line<Q>(smem + el * R3 + off, stride, uu);
     eo_apply<Q, Q, -1>(T.De, T.Do, uu, d);
-    store_line<Q>(smem + el * R3 + (1 + dir) * Q3 + off, stride, d);
+    store_line<Q>(smem + el * R3 + (1 + dir) * RG + off, stride, d);
   }
   __syncthreads();
   // 5. columns: pointwise v = m u (into D, over u), w = G grad u; then Dh^T along z of
@@ -325,9 +342,9 @@ __global__ void __launch_bounds__(NT, MINB)
   Real Et[CQ], Ot[CQ];
   if (owner) {
     const long long e = e0 + cel;
-    Real* Dc = smem + cel * R3 + c;
-    Real* Xc = Dc + Q3;
-    Real* Yc = Xc + Q3;
+    Real* Dc = smem + cel * R3 + cs;
+    Real* Xc = Dc + RG;
+    Real* Yc = Xc + RG;
     Real w3[Q];
 #pragma unroll
     for (int kq = 0; kq < Q; ++kq) {
@@ -340,7 +357,7 @@ __global__ void __launch_bounds__(NT, MINB)
           for (int m = 0; m < 7; ++m) f[m] = __ldg(fe + m * Q3);
         } else {
 #pragma unroll
-          for (int m = 0; m < 7; ++m) f[m] = 0.0;
+          for (int m = 0; m < 7; ++m) f[m] = Real(0);
         }
       } else {
         const int iq = c % Q, jq = c / Q;
@@ -352,7 +369,7 @@ __global__ void __launch_bounds__(NT, MINB)
         point_factors(j0, j1, j2, Real(A.alpha) * w, nu * w, f);
         if (e >= A.E) {
 #pragma unroll
-          for (int m = 0; m < 7; ++m) f[m] = 0.0;
+          for (int m = 0; m < 7; ++m) f[m] = Real(0);
         }
       }
       const Real u1 = Xc[kq * SZ], u2 = Yc[kq * SZ], u3 = du[kq];
@@ -363,7 +380,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     Real ev[CQ], od[CQ];
     fold<Q>(w3, ev, od);
-    products<Q, Q, -1>(T.Dte2, T.Dto2, ev, od, Et, Ot);  // rows Reald: (2E, 2O)
+    products<Q, Q, -1>(T.Dte2, T.Dto2, ev, od, Et, Ot);  // rows doubled: (2E, 2O)
   }
   __syncthreads();
   // 6. Dh^T along x (X, in place) and along y (Y, in place)
@@ -374,7 +391,7 @@ __global__ void __launch_bounds__(NT, MINB)
     const int a = rr / Q, b = rr - a * Q;
     const int off = dir ? (a * SZ + b) : (a * SZ + b * SY);
     const int stride = dir ? SY : 1;
-    Real* line = smem + el * R3 + (1 + dir) * Q3 + off;
+    Real* line = smem + el * R3 + (1 + dir) * RG + off;
     Real w[Q], tw[Q];
     load_line<Q>(line, stride, w);
     eo_apply<Q, Q, -1>(T.Dte, T.Dto, w, tw);
@@ -383,10 +400,10 @@ __global__ void __launch_bounds__(NT, MINB)
   __syncthreads();
   // 7. columns: V = v + t1 + t2 + Dh^T w_3 formed directly in folded form, then B^T along z
   if (owner) {
-    Real* Dc = smem + cel * R3 + c;
+    Real* Dc = smem + cel * R3 + cs;
     Real sv[Q], es[CQ], os[CQ], E[(N + 1) / 2], O[(N + 1) / 2], out[N];
 #pragma unroll
-    for (int kq = 0; kq < Q; ++kq) sv[kq] = Dc[kq * SZ] + Dc[Q3 + kq * SZ] + Dc[2 * Q3 + kq * SZ];
+    for (int kq = 0; kq < Q; ++kq) sv[kq] = Dc[kq * SZ] + Dc[RG + kq * SZ] + Dc[2 * RG + kq * SZ];
     fold<Q>(sv, es, os);
 #pragma unroll
     for (int b = 0; b < CQ; ++b) es[b] += Ot[b];
@@ -403,7 +420,8 @@ __global__ void __launch_bounds__(NT, MINB)
 // Load vector: bE = (B x B x B)^T (w detJ f) per element.
 template <int P, int Q, int NE, int NT>
 __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTables T, const HxLoadArgs A) {
-  constexpr int N = P + 1, Q2 = Q * Q, Q3 = Q2 * Q, SZ = Q2, R3 = 3 * Q3;
+  using Lt = Layout<Q>;
+  constexpr int N = P + 1, Q2 = Q * Q, Q3 = Q2 * Q, SY = Lt::SY, SZ = Lt::SZ, R3 = Lt::R3;
   static_assert(NT >= NE * Q2, "one thread per z-column");
   extern __shared__ double smem[];
   double* geo = smem + NE * R3;
@@ -434,7 +452,7 @@ __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTabl
       V[kq] = vv;
     }
     eo_apply<Q, N, 1>(T.Bte, T.Bto, V, out);
-    store_line<N>(smem + cel * R3 + c, SZ, out);
+    store_line<N>(smem + cel * R3 + jq * SY + iq, SZ, out);
   }
   __syncthreads();
   transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
@@ -577,7 +595,7 @@ template <typename Real, int P, int Q, int GEOM, bool NUF>
 cudaError_t launch_apply_impl(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, cudaStream_t s) {
   using C = Config<P, Q, Real>;
   constexpr int NE = C::NE, NT = C::NT, MINB = C::MINB;
-  const size_t shmem = sizeof(Real) * (size_t)(NE * 3 * Q * Q * Q + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+  const size_t shmem = sizeof(Real) * (size_t)(NE * Layout<Q>::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
   auto k = apply_kernel<Real, P, Q, NE, NT, MINB, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
@@ -619,7 +637,7 @@ cudaError_t launch_diag_q(const HxTables& T, const HxDiagArgs& A, int geom, cuda
 template <int P, int Q>
 cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s) {
   constexpr int NE = Config<P, Q>::NE, NT = Config<P, Q>::NT;
-  const size_t shmem = sizeof(double) * (size_t)(NE * 3 * Q * Q * Q + NE * 24);
+  const size_t shmem = sizeof(double) * (size_t)(NE * Layout<Q>::R3 + NE * 24);
   auto k = load_kernel<P, Q, NE, NT>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
