@@ -189,7 +189,7 @@ void hx_tables_to_float(const HxTables& d, HxTablesF* f) {
   auto cp = [](const double* a, float* b, int n) {
     for (int i = 0; i < n; ++i) b[i] = (float)a[i];
   };
-  const int H = HX_H(HX_QMAX) * HX_H(HX_QMAX);
+  const int H = HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX);
   cp(d.Be, f->Be, H);
   cp(d.Bo, f->Bo, H);
   cp(d.Bte, f->Bte, H);

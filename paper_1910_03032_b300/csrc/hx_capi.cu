@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -547,6 +548,7 @@ HxCgBuffers cg_buffers(const hx_op* op) {
   b.yE = op->yE;
   b.partial = op->partial;
   b.st = op->st;
+  b.cond = 0ull;
   return b;
 }
 
@@ -570,8 +572,11 @@ hx_status ensure_solver(hx_op* op) {
 }
 
 // One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
-cudaError_t cg_iteration(const hx_op* op, cudaStream_t s) {
-  const HxCgBuffers b = cg_buffers(op);
+// One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
+// cond: the conditional handle of an enclosing graph while loop (0 outside one).
+cudaError_t cg_iteration(const hx_op* op, cudaStream_t s, unsigned long long cond = 0ull) {
+  HxCgBuffers b = cg_buffers(op);
+  b.cond = cond;
   cudaError_t e = element_apply(op, op->p, 1, &op->st->done, s);
   if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
   if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
@@ -579,24 +584,51 @@ cudaError_t cg_iteration(const hx_op* op, cudaStream_t s) {
   return e;
 }
 
-constexpr int kChunk = 16;  // CG iterations per graph launch (finished iterations exit at once)
+constexpr int kChunk = 16;  // CG iterations per launch of the fallback (non-conditional) path
 
-void ensure_graph(hx_op* op) {
-  if (op->graph || op->graph_failed) return;
+// A graph holding one while node whose body is captured from body(handle); the body's
+// last kernel keeps the loop going while its CG has not finished.  Returns false when
+// the driver refuses conditional nodes (the caller then falls back to chunked launches).
+bool build_while_graph(cudaStream_t s, const std::function<cudaError_t(unsigned long long)>& body,
+                       cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(op->stream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  // the parameter union has no default constructor: zero raw storage instead
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  np->type = cudaGraphNodeTypeConditional;
+  np->conditional.handle = h;
+  np->conditional.type = cudaGraphCondTypeWhile;
+  np->conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, np);
   if (e == cudaSuccess) {
-    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) e = cg_iteration(op, op->stream);
-    cudaError_t e2 = cudaStreamEndCapture(op->stream, &g);
-    if (e == cudaSuccess) e = e2;
+    cudaGraph_t bodyg = np->conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t eb = body((unsigned long long)h);
+      e = cudaStreamEndCapture(s, &bodyg);
+      if (eb != cudaSuccess) e = eb;
+    }
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&op->graph, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    op->graph = nullptr;
-    op->graph_failed = true;  // fall back to direct launches of the same kernels
+    *out = nullptr;
+    return false;
   }
+  return true;
+}
+
+void ensure_graph(hx_op* op) {
+  if (op->graph || op->graph_failed) return;
+  if (!build_while_graph(op->stream, [op](unsigned long long h) { return cg_iteration(op, op->stream, h); },
+                         &op->graph))
+    op->graph_failed = true;  // fall back to chunks of direct launches of the same kernels
 }
 
 hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int max_it, int use_x0,
@@ -620,16 +652,21 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   }
   HX_TRY(hx_launch_cg_start(buf, st), "cg start");
   op->launches += 2;
-  for (;;) {
+  if (op->graph) {
+    // the whole iteration runs on the device: one graph launch, one synchronization
+    HX_TRY(cudaGraphLaunch(op->graph, st), "graph launch");
     HX_TRY(cudaMemcpyAsync(op->st_host, op->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
     HX_TRY(cudaStreamSynchronize(st), "solver sync");
-    if (op->st_host->done) break;
-    if (op->graph) {
-      HX_TRY(cudaGraphLaunch(op->graph, st), "graph launch");
-    } else {
+    op->launches += 4 * (long long)op->st_host->loops;
+    if (!op->st_host->done) return fail(HX_ERR_CUDA, "CG graph loop ended before the solver finished");
+  } else {
+    for (;;) {
+      HX_TRY(cudaMemcpyAsync(op->st_host, op->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
+      HX_TRY(cudaStreamSynchronize(st), "solver sync");
+      if (op->st_host->done) break;
       for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration(op, st), "cg iteration");
+      op->launches += 4 * kChunk;
     }
-    op->launches += 4 * kChunk;
   }
   const HxCgState cs = *op->st_host;
   // true residual ||P b - A_c x|| with one extra apply
@@ -740,6 +777,7 @@ HxCgBuffersF cg_buffers32(const hx_op* op) {
   b.yE = op->yE32;
   b.partial = op->partial;
   b.st = op->st32;
+  b.cond = 0ull;
   return b;
 }
 
@@ -770,8 +808,9 @@ hx_status ensure_mixed(hx_op* op) {
   return HX_OK;
 }
 
-cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s) {
-  const HxCgBuffersF b = cg_buffers32(op);
+cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s, unsigned long long cond = 0ull) {
+  HxCgBuffersF b = cg_buffers32(op);
+  b.cond = cond;
   cudaError_t e = element_apply32(op, op->p32, &op->st32->done, s);
   if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
   if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
@@ -781,20 +820,9 @@ cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s) {
 
 void ensure_graph32(hx_op* op) {
   if (op->graph32 || op->graph32_failed) return;
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(op->stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) e = cg_iteration32(op, op->stream);
-    cudaError_t e2 = cudaStreamEndCapture(op->stream, &g);
-    if (e == cudaSuccess) e = e2;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&op->graph32, g, 0);
-  if (g) cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    op->graph32 = nullptr;
+  if (!build_while_graph(op->stream, [op](unsigned long long h) { return cg_iteration32(op, op->stream, h); },
+                         &op->graph32))
     op->graph32_failed = true;
-  }
 }
 
 // FP64 residual r = P b - A_c x into op->r, ||r||^2 into op->rn2 (x in op->x).
@@ -845,16 +873,20 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
            "inner init");
     HX_TRY(hx_launch_cg_start(buf, st), "inner start");
     op->launches += 3;
-    for (;;) {
+    if (op->graph32) {
+      HX_TRY(cudaGraphLaunch(op->graph32, st), "graph launch");
       HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
       HX_TRY(cudaStreamSynchronize(st), "solver sync");
-      if (op->st_host->done) break;
-      if (op->graph32) {
-        HX_TRY(cudaGraphLaunch(op->graph32, st), "graph launch");
-      } else {
+      op->launches += 4 * (long long)op->st_host->loops;
+      if (!op->st_host->done) return fail(HX_ERR_CUDA, "inner CG graph loop ended before the solver finished");
+    } else {
+      for (;;) {
+        HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
+        HX_TRY(cudaStreamSynchronize(st), "solver sync");
+        if (op->st_host->done) break;
         for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration32(op, st), "inner iteration");
+        op->launches += 4 * kChunk;
       }
-      op->launches += 4 * kChunk;
     }
     const HxCgState cs = *op->st_host;
     inner_total += cs.iter;

@@ -90,6 +90,7 @@ struct HxCgState {
   int iter;         // completed iterations
   int max_it;
   int done;         // 0 running, 1 finished
+  int loops;        // iterations of a graph while-loop body (a hard stop for the loop)
   int status;       // HX_OK / HX_ERR_NOT_CONVERGED / HX_ERR_BREAKDOWN
   unsigned int count[4];  // last-block counters, one per reduction kernel
 };
@@ -111,6 +112,7 @@ struct HxCgBuffersT {
   Real* yE;
   double* partial;  // [2 * HX_RED_BLOCKS]
   HxCgState* st;
+  unsigned long long cond;  // CUDA graph conditional handle of the enclosing while loop, or 0
 };
 typedef HxCgBuffersT<double> HxCgBuffers;
 typedef HxCgBuffersT<float> HxCgBuffersF;

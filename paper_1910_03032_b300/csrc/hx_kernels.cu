@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffersT<Re
     s->iter = 0;
     s->max_it = max_it;
     s->done = 0;
+    s->loops = 0;
     s->status = 0;
     s->rz = s->alpha = s->beta = 0.0;
     s->rr = out[0];
@@ -295,6 +296,14 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<
 // p = D^-1 r + beta p.
 template <typename Real>
 __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffersT<Real> B) {
+  if (B.cond != 0ull && blockIdx.x == 0 && threadIdx.x == 0) {
+    // last kernel of a CUDA-graph while-loop body: continue only while CG runs, and never
+    // for more bodies than the iteration cap allows
+    HxCgState* s = B.st;
+    s->loops += 1;
+    const bool stop = *(volatile int*)&s->done || s->loops > s->max_it + 1;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)B.cond, stop ? 0u : 1u);
+  }
   if (*(volatile int*)&B.st->done) return;
   const Real beta = Real(B.st->beta);
   HX_GRID_STRIDE(g, B.n) { B.p[g] = B.dinv[g] * B.r[g] + beta * B.p[g]; }

@@ -19,32 +19,32 @@
 #define HX_PMAX 8
 #define HX_QMAX 10
 #define HX_NMAX (HX_PMAX + 1)
-#define HX_H(x) (((x) + 1) / 2)
+#define HX_HALF_UP(x) (((x) + 1) / 2)
 
 template <typename T>
 struct HxTablesT {
   int p, q;
   // folded B (sigma = +1): M = q, L = n
-  T Be[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
-  T Bo[HX_H(HX_QMAX) * HX_H(HX_NMAX)];
+  T Be[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_NMAX)];
+  T Bo[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_NMAX)];
   // folded B^T (sigma = +1): M = n, L = q
-  T Bte[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
-  T Bto[HX_H(HX_NMAX) * HX_H(HX_QMAX)];
+  T Bte[HX_HALF_UP(HX_NMAX) * HX_HALF_UP(HX_QMAX)];
+  T Bto[HX_HALF_UP(HX_NMAX) * HX_HALF_UP(HX_QMAX)];
   // folded Dh (sigma = -1): M = L = q
-  T De[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  T Do[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T De[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
+  T Do[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
   // folded Dh^T (sigma = -1)
-  T Dte[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  T Dto[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Dte[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
+  T Dto[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
   // Dh applied to an input given by the folded parts (E, O) of a centro-symmetric
   // interpolation along the same direction: the input's even/odd parts are 2E and 2O
   // (E alone for the middle entry of odd q), so the columns b < q/2 are doubled.
-  T De2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  T Do2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T De2[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
+  T Do2[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
   // Dh^T with the rows a < q/2 doubled: its folded outputs (2E, 2O) are then exactly the
   // even/odd parts of the result, ready to feed the next contraction along the same direction.
-  T Dte2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
-  T Dto2[HX_H(HX_QMAX) * HX_H(HX_QMAX)];
+  T Dte2[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
+  T Dto2[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
   // unfolded tables, row-major
   T B[HX_QMAX * HX_NMAX];
   T D[HX_QMAX * HX_NMAX];
