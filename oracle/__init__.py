@@ -30,10 +30,10 @@ closed forms, exact polynomial integrals, invariants and brute force.
 """
 from .basis import gll_nodes, gauss_rule, lagrange_values, lagrange_derivatives, legendre
 from .fem import StructuredMesh, Mesh, Operator, ReferenceElement, load_vector, l2_error, trilinear_map
-from .solve import jacobi_pcg
+from .solve import jacobi_pcg, jacobi_pcg_nullspace
 
 __all__ = [
     "gll_nodes", "gauss_rule", "lagrange_values", "lagrange_derivatives", "legendre",
     "StructuredMesh", "Mesh", "Operator", "ReferenceElement", "load_vector", "l2_error",
-    "trilinear_map", "jacobi_pcg",
+    "trilinear_map", "jacobi_pcg", "jacobi_pcg_nullspace",
 ]

@@ -39,3 +39,54 @@ def jacobi_pcg(op, b, rtol=1e-10, max_it=10000):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, max_it, rel, False
+
+
+def jacobi_pcg_nullspace(op, b, rtol=1e-10, max_it=10000):
+    """Jacobi-PCG for the pure-Neumann Poisson problem (no Dirichlet DoFs, alpha = 0).
+
+    The operator K has the constants as null space (Sec. 5.3).  Following the
+    paper: the right-hand side is made orthogonal to the null space, every
+    preconditioner application is followed by an orthogonalization against it,
+    and the solution is closed with the mean-zero condition int p dx = 0
+    (Sec. 4.2, Eq. (meanZero)), i.e. m1 . x = 0 with m1_i = int phi_i dx.
+
+    Returns (x, iterations, final relative recurrence residual, converged).
+    """
+    from .fem import Operator
+    mesh = op.mesh
+    n = mesh.n_dof
+    b = np.asarray(b, dtype=np.float64)
+    bc = b - b.mean()                        # orthogonal to the constants
+    d = op.diagonal()
+    x = np.zeros(n)
+    r = bc.copy()
+    bnorm = np.linalg.norm(bc)
+    m1 = Operator(mesh, 1.0, 0.0).apply(np.ones(n))   # m1_i = int phi_i dx
+    if bnorm == 0.0:
+        return x, 0, 0.0, True
+
+    def precond(v):
+        z = v / d
+        return z - z.mean()                  # orthogonalization step
+
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    rel = 1.0
+    for it in range(1, max_it + 1):
+        Ap = op.apply(p)
+        pAp = p @ Ap
+        if not pAp > 0.0:
+            raise FloatingPointError("CG breakdown: p^T A p <= 0")
+        a = rz / pAp
+        x += a * p
+        r -= a * Ap
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= rtol:
+            break
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    x -= (m1 @ x) / m1.sum()                 # mean-zero closure
+    return x, it, rel, rel <= rtol
