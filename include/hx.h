@@ -115,6 +115,18 @@ HX_API hx_status hx_mesh_create(int p, int q, int64_t n_vert, const double* vert
 HX_API hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const double* vert_xyz,
                                            hx_mesh** out);
 
+/*
+ * As hx_mesh_create_structured, with the Dirichlet DoFs on a chosen set of box
+ * faces: bit 0 x = min, bit 1 x = max, bit 2 y = min, bit 3 y = max, bit 4 z = min,
+ * bit 5 z = max (63 = all faces; 0 = pure Neumann).  An operator with alpha = 0 on a
+ * mesh without Dirichlet DoFs is the pure-Neumann Poisson operator of the pressure
+ * step (Sec. 4.2): its solves remove the mean of b, orthogonalize every
+ * preconditioned residual against the constants (Sec. 5.3) and return the
+ * solution with zero mean, int x dx = 0 (Eq. (meanZero)).
+ */
+HX_API hx_status hx_mesh_create_box(int nx, int ny, int nz, int p, int q, const double* vert_xyz,
+                                    int dirichlet_faces, hx_mesh** out);
+
 /* Frees the mesh (NULL is ignored).  Operators built on it must be destroyed first. */
 HX_API void hx_mesh_destroy(hx_mesh* mesh);
 

@@ -52,6 +52,7 @@ SIGNATURES = {
     "hx_last_error": (ctypes.c_char_p, []),
     "hx_mesh_create": (_I, [_I, _I, _I64, _P, _I64, _P, _I64, _P, _P, ctypes.POINTER(_P)]),
     "hx_mesh_create_structured": (_I, [_I, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
+    "hx_mesh_create_box": (_I, [_I, _I, _I, _I, _I, _P, _I, ctypes.POINTER(_P)]),
     "hx_mesh_destroy": (None, [_P]),
     "hx_mesh_info": (_I, _SIZES),
     "hx_mesh_qpoint_coords": (_I, [_P, _P, _P]),
@@ -174,6 +175,16 @@ def hx_mesh_create_structured(nx, ny, nz, p, q, vert_xyz):
         raise ValueError("vert_xyz must be ((nx+1)(ny+1)(nz+1), 3)")
     out = ctypes.c_void_p()
     _check(_lib.hx_mesh_create_structured(nx, ny, nz, p, q, ctypes.c_void_p(vert_xyz.ctypes.data), ctypes.byref(out)))
+    return out
+
+
+def hx_mesh_create_box(nx, ny, nz, p, q, vert_xyz, dirichlet_faces=63):
+    vert_xyz = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    if vert_xyz.shape != ((nx + 1) * (ny + 1) * (nz + 1), 3):
+        raise ValueError("vert_xyz must be ((nx+1)(ny+1)(nz+1), 3)")
+    out = ctypes.c_void_p()
+    _check(_lib.hx_mesh_create_box(nx, ny, nz, p, q, ctypes.c_void_p(vert_xyz.ctypes.data), int(dirichlet_faces),
+                                   ctypes.byref(out)))
     return out
 
 
@@ -322,6 +333,10 @@ class Mesh:
     @classmethod
     def structured(cls, nx, ny, nz, p, q, vert_xyz):
         return cls(hx_mesh_create_structured(nx, ny, nz, p, q, vert_xyz))
+
+    @classmethod
+    def box(cls, nx, ny, nz, p, q, vert_xyz, dirichlet_faces=63):
+        return cls(hx_mesh_create_box(nx, ny, nz, p, q, vert_xyz, dirichlet_faces))
 
     @classmethod
     def general(cls, p, q, vert_xyz, elem_vert, n_dof, restriction, dirichlet=None):

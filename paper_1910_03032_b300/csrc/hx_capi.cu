@@ -77,6 +77,7 @@ struct hx_mesh {
   int* idx = nullptr;            // [E n^3] E-vector positions, increasing per DoF
   unsigned char* dir = nullptr;  // [n_dof]
   double* X8 = nullptr;          // [E][8][3]
+  long long n_dirichlet = 0;     // Dirichlet DoFs (0: no boundary condition fixes the constants)
 };
 
 struct hx_op {
@@ -108,6 +109,10 @@ struct hx_op {
   cudaGraphExec_t graph32 = nullptr;
   bool graph32_failed = false;
   bool mixed_stale = true;      // FP32 factors / diagonal need refreshing from the FP64 ones
+  // pure Neumann Poisson (alpha = 0, no Dirichlet DoF): constants span the null space
+  bool singular = false;
+  double* m1 = nullptr;         // [n_dof] m1_i = int phi_i dx (mean-zero closure)
+  double* vol = nullptr;        // [2] device: sum of m1 (the domain volume), and a dot-product slot
 };
 
 namespace {
@@ -181,6 +186,7 @@ hx_status build_mesh(int p, int q, long long n_vert, const double* vert, long lo
   m->N3 = N3;
   m->E = E;
   m->n_dof = n_dof;
+  for (long long g = 0; g < n_dof; ++g) m->n_dirichlet += dmask[g];
   cudaGetDevice(&m->device);
   if (hx_build_tables(p, q, &m->T) == 0) hx_tables_to_float(m->T, &m->T32);
   else {
@@ -228,7 +234,8 @@ hx_status hx_mesh_create(int p, int q, int64_t n_vert, const double* vert_xyz, i
   return build_mesh(p, q, n_vert, vert_xyz, n_elem, elem_vert, n_dof, restriction, dirichlet, out);
 }
 
-hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const double* vert_xyz, hx_mesh** out) {
+hx_status hx_mesh_create_box(int nx, int ny, int nz, int p, int q, const double* vert_xyz, int dirichlet_faces,
+                             hx_mesh** out) {
   if (!out) return fail(HX_ERR_ARG, "out is NULL");
   *out = nullptr;
   hx_status s = check_order(p, q);
@@ -259,8 +266,16 @@ hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const 
   for (long long K = 0; K < gz; ++K)
     for (long long J = 0; J < gy; ++J)
       for (long long I = 0; I < gx; ++I, ++g)
-        dir[g] = (I == 0 || I == gx - 1 || J == 0 || J == gy - 1 || K == 0 || K == gz - 1) ? 1 : 0;
+        dir[g] = (((dirichlet_faces & 1) && I == 0) || ((dirichlet_faces & 2) && I == gx - 1) ||
+                  ((dirichlet_faces & 4) && J == 0) || ((dirichlet_faces & 8) && J == gy - 1) ||
+                  ((dirichlet_faces & 16) && K == 0) || ((dirichlet_faces & 32) && K == gz - 1))
+                     ? 1
+                     : 0;
   return build_mesh(p, q, n_vert, vert_xyz, E, ev.data(), n_dof, R.data(), dir.data(), out);
+}
+
+hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const double* vert_xyz, hx_mesh** out) {
+  return hx_mesh_create_box(nx, ny, nz, p, q, vert_xyz, 63, out);
 }
 
 void hx_mesh_destroy(hx_mesh* m) {
@@ -358,6 +373,8 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->dinv32);
   dfree(op->rn2);
   dfree(op->st32);
+  dfree(op->m1);
+  dfree(op->vol);
   delete op;
 }
 
@@ -376,6 +393,8 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
   cudaError_t e;
   op->alpha = alpha;
   op->nu = nu;
+  // alpha = 0 with nothing fixed on the boundary: K alone, singular on the constants
+  op->singular = (alpha == 0.0 && m->n_dirichlet == 0);
   if (op->geom == HX_GEOM_STORED) {
     HX_TRY(hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s), "geometry kernel");
     ++nl;
@@ -448,6 +467,20 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
     int nl = 0;
     if ((st = setup_coefficients(op, alpha, nu, nu_q, bad, s, &nl))) break;
     op->launches += nl;
+    if (m->n_dirichlet == 0) {
+      // m1_i = int phi_i dx and its sum (the volume), for the mean-zero closure of a
+      // pure Neumann Poisson solve (Sec. 4.2, Eq. (meanZero))
+      if ((st = dalloc(&op->m1, (size_t)m->n_dof, "mass row sums")) || (st = dalloc(&op->vol, 2, "volume"))) break;
+      HxLoadArgs la;
+      la.E = m->E;
+      la.X8 = m->X8;
+      la.fq = nullptr;
+      la.yE = op->yE;
+      e = load_launcher(m->p)(m->T, la, s);
+      if (e == cudaSuccess) e = hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->m1, s);
+      if (e != cudaSuccess) { st = cuda_fail(e, "mass row sums"); break; }
+      op->launches += 2;
+    }
     e = cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = cuda_fail(e, "operator setup"); break; }
@@ -549,6 +582,7 @@ HxCgBuffers cg_buffers(const hx_op* op) {
   b.partial = op->partial;
   b.st = op->st;
   b.cond = 0ull;
+  b.nullspace = op->singular ? 1 : 0;
   return b;
 }
 
@@ -558,7 +592,7 @@ hx_status ensure_solver(hx_op* op) {
   hx_status s;
   if ((s = dalloc(&op->x, n, "cg x")) || (s = dalloc(&op->r, n, "cg r")) || (s = dalloc(&op->p, n, "cg p")) ||
       (s = dalloc(&op->Ap, n, "cg Ap")) || (s = dalloc(&op->dinv, n, "cg dinv")) ||
-      (s = dalloc(&op->partial, 2 * HX_RED_BLOCKS, "cg partials")) || (s = dalloc(&op->scalars, 2, "scalars")) ||
+      (s = dalloc(&op->partial, HX_RED_VALUES * HX_RED_BLOCKS, "cg partials")) || (s = dalloc(&op->scalars, 2, "scalars")) ||
       (s = dalloc(&op->counters, 2, "counters")) || (s = dalloc(&op->st, 1, "cg state")))
     return s;
   HX_TRY(cudaMallocHost((void**)&op->st_host, sizeof(HxCgState)), "pinned state");
@@ -643,6 +677,11 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   HX_TRY(cudaStreamWaitEvent(st, op->ev, 0), "stream wait");
   const HxCgBuffers buf = cg_buffers(op);
   const long long launches0 = op->launches;
+  if (op->singular) {
+    // pure Neumann: remove the mean of b (orthogonal to the constant null space, Sec. 5.3)
+    HX_TRY(hx_launch_cg_mean(buf, b, st), "cg mean");
+    op->launches += 1;
+  }
   HX_TRY(hx_launch_cg_init(buf, b, use_x0 ? x : nullptr, rtol, max_it, st), "cg init");
   if (use_x0) {
     HX_TRY(element_apply(op, op->x, 1, nullptr, st), "cg x0 apply");
@@ -652,6 +691,10 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   }
   HX_TRY(hx_launch_cg_start(buf, st), "cg start");
   op->launches += 2;
+  if (op->singular) {
+    HX_TRY(hx_launch_cg_direction(buf, st), "cg first direction");  // p = z - mean z
+    op->launches += 1;
+  }
   if (op->graph) {
     // the whole iteration runs on the device: one graph launch, one synchronization
     HX_TRY(cudaGraphLaunch(op->graph, st), "graph launch");
@@ -669,10 +712,19 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
     }
   }
   const HxCgState cs = *op->st_host;
+  if (op->singular) {
+    // mean-zero closure int x dx = m1 . x = 0 (Sec. 4.2, Eq. (meanZero)); K 1 = 0 keeps the residual
+    HX_TRY(hx_launch_sum(m->n_dof, op->m1, op->partial, op->counters, op->vol, st), "volume");
+    HX_TRY(hx_launch_dot(m->n_dof, op->m1, op->x, op->partial, op->counters, op->vol + 1, st), "mean");
+    HX_TRY(hx_launch_shift(m->n_dof, op->x, op->vol + 1, op->vol, st), "mean shift");
+    op->launches += 3;
+  }
   // true residual ||P b - A_c x|| with one extra apply
   HX_TRY(element_apply(op, op->x, 1, nullptr, st), "residual apply");
   HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "residual assembly");
-  HX_TRY(hx_launch_resnorm(m->n_dof, b, op->Ap, m->dir, op->partial, op->counters, op->scalars, st), "residual norm");
+  HX_TRY(hx_launch_resnorm(m->n_dof, b, op->Ap, m->dir, op->partial, op->counters, op->scalars, st,
+                           op->singular ? &op->st->shift : nullptr),
+         "residual norm");
   op->launches += 3;
   double rn2 = 0.0;
   HX_TRY(cudaMemcpyAsync(&rn2, op->scalars, sizeof(double), cudaMemcpyDeviceToHost, st), "residual read");
@@ -778,6 +830,7 @@ HxCgBuffersF cg_buffers32(const hx_op* op) {
   b.partial = op->partial;
   b.st = op->st32;
   b.cond = 0ull;
+  b.nullspace = op->singular ? 1 : 0;
   return b;
 }
 
@@ -827,6 +880,7 @@ void ensure_graph32(hx_op* op) {
 
 // FP64 residual r = P b - A_c x into op->r, ||r||^2 into op->rn2 (x in op->x).
 hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_t st) {
+  const double* shift = op->singular ? &op->st->shift : nullptr;  // pure Neumann: b minus its mean
   const hx_mesh* m = op->mesh;
   if (x_is_zero) {
     HX_TRY(cudaMemsetAsync(op->Ap, 0, sizeof(double) * m->n_dof, st), "zero");
@@ -836,7 +890,7 @@ hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_
            "refinement assembly");
     op->launches += 2;
   }
-  HX_TRY(hx_launch_ir_residual(m->n_dof, b, op->Ap, m->dir, op->r, op->partial, op->counters, op->rn2, st),
+  HX_TRY(hx_launch_ir_residual(m->n_dof, b, op->Ap, m->dir, op->r, op->partial, op->counters, op->rn2, st, shift),
          "refinement residual");
   op->launches += 1;
   return HX_OK;
@@ -854,6 +908,10 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
   ensure_graph32(op);
   const long long launches0 = op->launches;
   HX_TRY(cudaMemsetAsync(op->x, 0, sizeof(double) * m->n_dof, st), "x init");
+  if (op->singular) {
+    HX_TRY(hx_launch_cg_mean(cg_buffers(op), b, st), "mean of b");
+    op->launches += 1;
+  }
   if ((s = outer_residual(op, b, true, st))) return s;
   double rn2 = 0.0;
   HX_TRY(cudaMemcpyAsync(&rn2, op->rn2, sizeof(double), cudaMemcpyDeviceToHost, st), "norm read");
@@ -869,10 +927,18 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
     }
     // inner FP32 Jacobi-PCG on A_c d = r / ||r|| from d = 0
     HX_TRY(hx_launch_ir_scale_down(m->n_dof, op->r, op->rn2, op->r32, st), "scale down");
+    if (op->singular) {
+      HX_TRY(hx_launch_cg_mean(buf, (const float*)op->r32, st), "inner mean");
+      op->launches += 1;
+    }
     HX_TRY(hx_launch_cg_init(buf, (const float*)op->r32, (const float*)nullptr, inner_rtol, max_it - inner_total, st),
            "inner init");
     HX_TRY(hx_launch_cg_start(buf, st), "inner start");
     op->launches += 3;
+    if (op->singular) {
+      HX_TRY(hx_launch_cg_direction(buf, st), "inner first direction");
+      op->launches += 1;
+    }
     if (op->graph32) {
       HX_TRY(cudaGraphLaunch(op->graph32, st), "graph launch");
       HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
@@ -913,6 +979,12 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
       break;
     }
     prev = rel;
+  }
+  if (op->singular) {
+    HX_TRY(hx_launch_sum(m->n_dof, op->m1, op->partial, op->counters, op->vol, st), "volume");
+    HX_TRY(hx_launch_dot(m->n_dof, op->m1, op->x, op->partial, op->counters, op->vol + 1, st), "mean");
+    HX_TRY(hx_launch_shift(m->n_dof, op->x, op->vol + 1, op->vol, st), "mean shift");
+    op->launches += 3;
   }
   HX_TRY(cudaMemcpyAsync(x, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, st), "solution copy");
   HX_TRY(cudaStreamSynchronize(st), "solver sync");

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTabl
         trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
         const double det = j0[0] * (j1[1] * j2[2] - j1[2] * j2[1]) + j0[1] * (j1[2] * j2[0] - j1[0] * j2[2]) +
                            j0[2] * (j1[0] * j2[1] - j1[1] * j2[0]);
-        vv = T.wq[iq] * T.wq[jq] * T.wq[kq] * det * __ldg(A.fq + e * Q3 + kq * Q2 + c);
+        vv = T.wq[iq] * T.wq[jq] * T.wq[kq] * det * (A.fq ? __ldg(A.fq + e * Q3 + kq * Q2 + c) : 1.0);
       }
       V[kq] = vv;
     }

@@ -40,7 +40,7 @@ struct HxDiagArgs {
 struct HxLoadArgs {
   long long E;
   const double* X8;
-  const double* fq;       // [E][q^3] source values at the quadrature points
+  const double* fq;       // [E][q^3] source values at the quadrature points (null: f = 1)
   double* yE;
 };
 
@@ -91,11 +91,14 @@ struct HxCgState {
   int max_it;
   int done;         // 0 running, 1 finished
   int loops;        // iterations of a graph while-loop body (a hard stop for the loop)
+  double shift;     // null-space mode: mean of b, removed from the right-hand side
+  double zmean;     // null-space mode: mean of D^-1 r, removed from the preconditioned residual
   int status;       // HX_OK / HX_ERR_NOT_CONVERGED / HX_ERR_BREAKDOWN
   unsigned int count[4];  // last-block counters, one per reduction kernel
 };
 
 #define HX_RED_BLOCKS 1184  // 8 x 148 SMs: fixed grid of every reduction kernel
+#define HX_RED_VALUES 4     // partial sums per block at most (partial buffers hold HX_RED_VALUES x HX_RED_BLOCKS)
 #define HX_RED_THREADS 256
 
 template <typename Real>
@@ -110,9 +113,10 @@ struct HxCgBuffersT {
   Real* Ap;
   Real* dinv;
   Real* yE;
-  double* partial;  // [2 * HX_RED_BLOCKS]
+  double* partial;  // [HX_RED_VALUES * HX_RED_BLOCKS]
   HxCgState* st;
   unsigned long long cond;  // CUDA graph conditional handle of the enclosing while loop, or 0
+  int nullspace;            // 1: singular operator with the constants as null space (pure Neumann Poisson)
 };
 typedef HxCgBuffersT<double> HxCgBuffers;
 typedef HxCgBuffersT<float> HxCgBuffersF;
@@ -137,14 +141,22 @@ cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s);
 cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s);
 cudaError_t hx_launch_ir_residual(long long n, const double* b, const double* Ax, const unsigned char* dir, double* r,
-                                  double* partial, unsigned int* counter, double* rn2, cudaStream_t s);
+                                  double* partial, unsigned int* counter, double* rn2, cudaStream_t s,
+                                  const double* shift = nullptr);
 cudaError_t hx_launch_ir_scale_down(long long n, const double* r, const double* rn2, float* r32, cudaStream_t s);
 cudaError_t hx_launch_ir_update(long long n, double* x, const float* d, const double* rn2, cudaStream_t s);
 cudaError_t hx_launch_to_float(long long n, const double* a, float* b, cudaStream_t s);
 cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,
                           double* out, cudaStream_t s);
 cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,
-                              unsigned int* counter, double* out, cudaStream_t s);
+                              unsigned int* counter, double* out, cudaStream_t s, const double* shift = nullptr);
+// null-space (pure Neumann) helpers
+template <typename Real>
+cudaError_t hx_launch_cg_mean(const HxCgBuffersT<Real>& b, const Real* v, cudaStream_t s);
+cudaError_t hx_launch_sum(long long n, const double* v, double* partial, unsigned int* counter, double* out,
+                          cudaStream_t s);
+// x -= (*num) / (*den)
+cudaError_t hx_launch_shift(long long n, double* x, const double* num, const double* den, cudaStream_t s);
 
 // Sets the message hx_last_error() returns on this thread (for entry points
 // defined outside hx_capi.cu).

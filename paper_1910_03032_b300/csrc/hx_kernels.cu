@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffersT<Re
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, B.n) {
     const bool d = B.dir[g];
-    const Real bg = d ? Real(0) : b[g];
+    const Real bg = d ? Real(0) : (B.nullspace ? Real((double)b[g] - B.st->shift) : b[g]);
     B.r[g] = bg;
     B.x[g] = (x0 && !d) ? x0[g] : Real(0);
     acc[0] += (double)bg * (double)bg;
@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffersT<Re
     s->max_it = max_it;
     s->done = 0;
     s->loops = 0;
+    s->zmean = 0.0;
     s->status = 0;
     s->rz = s->alpha = s->beta = 0.0;
     s->rr = out[0];
@@ -213,27 +214,46 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffers
 }
 
 // z = D^-1 r, p = z; rz = (r, z), rr = (r, r); finishes at once if rr <= tol^2 ||b||^2.
+// Null-space mode also sums z and r: the preconditioned residual is orthogonalized against
+// the constants (z - mean z, Sec. 5.3) and p is finished by a direction pass with beta = 0.
 template <typename Real>
 __global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffersT<Real> B) {
-  double acc[2] = {0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   HX_GRID_STRIDE(g, B.n) {
     const Real r = B.r[g], z = B.dinv[g] * r;
     B.p[g] = z;
     acc[0] += (double)r * (double)z;
     acc[1] += (double)r * (double)r;
+    acc[2] += (double)z;
+    acc[3] += (double)r;
   }
-  double out[2];
-  if (last_block_reduce<2>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
+  double out[4];
+  if (last_block_reduce<4>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
     HxCgState* s = B.st;
-    s->rz = out[0];
+    double rz = out[0];
+    if (B.nullspace) {
+      s->zmean = out[2] / (double)B.n;
+      rz -= s->zmean * out[3];
+      s->beta = 0.0;
+    }
+    s->rz = rz;
     s->rr = out[1];
-    if (!isfinite(out[0]) || !isfinite(out[1])) {
+    if (!isfinite(rz) || !isfinite(out[1])) {
       s->status = -6;  // HX_ERR_BREAKDOWN
       s->done = 1;
     } else if (out[1] <= s->tol2) {
       s->done = 1;
     }
   }
+}
+
+// st->shift = mean of v over all DoFs.
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_mean_kernel(HxCgBuffersT<Real> B, const Real* __restrict__ v) {
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, B.n) { acc[0] += (double)v[g]; }
+  double out[1];
+  if (last_block_reduce<1>(acc, B.partial, &B.st->count[0], out) && threadIdx.x == 0) B.st->shift = out[0] / (double)B.n;
 }
 
 // Ap = assemble(yE) with Dirichlet rows Ap = p; pAp = (p, Ap); alpha = rz / pAp.
@@ -260,25 +280,34 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuf
 }
 
 // x += alpha p, r -= alpha Ap, z = D^-1 r; rr = (r, r), rz' = (r, z); convergence test.
+// Null-space mode: rz' = (r, z - mean z) and the mean is kept for the direction pass.
 template <typename Real>
 __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<Real> B) {
   if (*(volatile int*)&B.st->done) return;
   const Real a = Real(B.st->alpha);
-  double acc[2] = {0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   HX_GRID_STRIDE(g, B.n) {
     const Real pg = B.p[g];
     B.x[g] += a * pg;
     const Real r = B.r[g] - a * B.Ap[g];
     B.r[g] = r;
+    const Real z = B.dinv[g] * r;
     acc[0] += (double)r * (double)r;
-    acc[1] += (double)r * (double)(B.dinv[g] * r);
+    acc[1] += (double)r * (double)z;
+    acc[2] += (double)z;
+    acc[3] += (double)r;
   }
-  double out[2];
-  if (last_block_reduce<2>(acc, B.partial, &B.st->count[3], out) && threadIdx.x == 0) {
+  double out[4];
+  if (last_block_reduce<4>(acc, B.partial, &B.st->count[3], out) && threadIdx.x == 0) {
     HxCgState* s = B.st;
     s->iter += 1;
     s->rr = out[0];
-    if (!isfinite(out[0]) || !isfinite(out[1])) {
+    double rz = out[1];
+    if (B.nullspace) {
+      s->zmean = out[2] / (double)B.n;
+      rz -= s->zmean * out[3];
+    }
+    if (!isfinite(out[0]) || !isfinite(rz)) {
       s->status = -6;
       s->done = 1;
     } else if (out[0] <= s->tol2) {
@@ -287,8 +316,8 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<
       s->status = -5;  // HX_ERR_NOT_CONVERGED
       s->done = 1;
     } else {
-      s->beta = out[1] / s->rz;
-      s->rz = out[1];
+      s->beta = rz / s->rz;
+      s->rz = rz;
     }
   }
 }
@@ -305,8 +334,8 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffer
     cudaGraphSetConditional((cudaGraphConditionalHandle)B.cond, stop ? 0u : 1u);
   }
   if (*(volatile int*)&B.st->done) return;
-  const Real beta = Real(B.st->beta);
-  HX_GRID_STRIDE(g, B.n) { B.p[g] = B.dinv[g] * B.r[g] + beta * B.p[g]; }
+  const Real beta = Real(B.st->beta), zm = Real(B.st->zmean);
+  HX_GRID_STRIDE(g, B.n) { B.p[g] = (B.dinv[g] * B.r[g] - zm) + beta * B.p[g]; }
 }
 
 // ---------------------------------------------------------------------------
@@ -317,10 +346,12 @@ __global__ void __launch_bounds__(HX_RED_THREADS) ir_residual_kernel(long long n
                                                                       const double* __restrict__ Ax,
                                                                       const unsigned char* __restrict__ dir,
                                                                       double* __restrict__ r, double* partial,
-                                                                      unsigned int* counter, double* out) {
+                                                                      unsigned int* counter, double* out,
+                                                                      const double* __restrict__ shift) {
+  const double sh = shift ? *shift : 0.0;
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, n) {
-    const double v = dir[g] ? 0.0 : b[g] - Ax[g];
+    const double v = dir[g] ? 0.0 : (b[g] - sh) - Ax[g];
     r[g] = v;
     acc[0] += v * v;
   }
@@ -342,6 +373,20 @@ __global__ void __launch_bounds__(kThreads) ir_update_kernel(long long n, double
   HX_GRID_STRIDE(g, n) { x[g] += s * (double)d[g]; }
 }
 
+__global__ void __launch_bounds__(HX_RED_THREADS) sum_kernel(long long n, const double* __restrict__ v, double* partial,
+                                                              unsigned int* counter, double* out) {
+  double acc[1] = {0.0};
+  HX_GRID_STRIDE(g, n) { acc[0] += v[g]; }
+  double res[1];
+  if (last_block_reduce<1>(acc, partial, counter, res) && threadIdx.x == 0) *out = res[0];
+}
+
+__global__ void __launch_bounds__(kThreads) shift_kernel(long long n, double* __restrict__ x, const double* __restrict__ num,
+                                                          const double* __restrict__ den) {
+  const double c = *num / *den;
+  HX_GRID_STRIDE(g, n) { x[g] -= c; }
+}
+
 __global__ void __launch_bounds__(kThreads) to_float_kernel(long long n, const double* __restrict__ a,
                                                              float* __restrict__ b) {
   HX_GRID_STRIDE(g, n) { b[g] = (float)a[g]; }
@@ -360,10 +405,12 @@ __global__ void __launch_bounds__(HX_RED_THREADS) dot_kernel(long long n, const 
 __global__ void __launch_bounds__(HX_RED_THREADS) resnorm_kernel(long long n, const double* __restrict__ b,
                                                                   const double* __restrict__ Ax,
                                                                   const unsigned char* __restrict__ dir,
-                                                                  double* partial, unsigned int* counter, double* out) {
+                                                                  double* partial, unsigned int* counter, double* out,
+                                                                  const double* __restrict__ shift) {
+  const double sh = shift ? *shift : 0.0;
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, n) {
-    const double r = dir[g] ? 0.0 : b[g] - Ax[g];
+    const double r = dir[g] ? 0.0 : (b[g] - sh) - Ax[g];
     acc[0] += r * r;
   }
   double res[1];
@@ -457,19 +504,35 @@ cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s) 
   cg_direction_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
+template <typename Real>
+cudaError_t hx_launch_cg_mean(const HxCgBuffersT<Real>& b, const Real* v, cudaStream_t s) {
+  cg_mean_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b, v);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_sum(long long n, const double* v, double* partial, unsigned int* counter, double* out,
+                          cudaStream_t s) {
+  sum_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, v, partial, counter, out);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_shift(long long n, double* x, const double* num, const double* den, cudaStream_t s) {
+  shift_kernel<<<grid_for(n), kThreads, 0, s>>>(n, x, num, den);
+  return cudaGetLastError();
+}
 #define HX_CG_INSTANTIATE(R)                                                                              \
   template cudaError_t hx_launch_cg_init<R>(const HxCgBuffersT<R>&, const R*, const R*, double, int, cudaStream_t); \
   template cudaError_t hx_launch_cg_residual<R>(const HxCgBuffersT<R>&, cudaStream_t);                 \
   template cudaError_t hx_launch_cg_start<R>(const HxCgBuffersT<R>&, cudaStream_t);                    \
   template cudaError_t hx_launch_cg_assemble_pap<R>(const HxCgBuffersT<R>&, cudaStream_t);             \
   template cudaError_t hx_launch_cg_update<R>(const HxCgBuffersT<R>&, cudaStream_t);                   \
-  template cudaError_t hx_launch_cg_direction<R>(const HxCgBuffersT<R>&, cudaStream_t);
+  template cudaError_t hx_launch_cg_direction<R>(const HxCgBuffersT<R>&, cudaStream_t);                \
+  template cudaError_t hx_launch_cg_mean<R>(const HxCgBuffersT<R>&, const R*, cudaStream_t);
 HX_CG_INSTANTIATE(double)
 HX_CG_INSTANTIATE(float)
 
 cudaError_t hx_launch_ir_residual(long long n, const double* b, const double* Ax, const unsigned char* dir, double* r,
-                                  double* partial, unsigned int* counter, double* rn2, cudaStream_t s) {
-  ir_residual_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, b, Ax, dir, r, partial, counter, rn2);
+                                  double* partial, unsigned int* counter, double* rn2, cudaStream_t s,
+                                  const double* shift) {
+  ir_residual_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, b, Ax, dir, r, partial, counter, rn2, shift);
   return cudaGetLastError();
 }
 cudaError_t hx_launch_ir_scale_down(long long n, const double* r, const double* rn2, float* r32, cudaStream_t s) {
@@ -490,7 +553,7 @@ cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double*
   return cudaGetLastError();
 }
 cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,
-                              unsigned int* counter, double* out, cudaStream_t s) {
-  resnorm_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, b, Ax, dir, partial, counter, out);
+                              unsigned int* counter, double* out, cudaStream_t s, const double* shift) {
+  resnorm_kernel<<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(n, b, Ax, dir, partial, counter, out, shift);
   return cudaGetLastError();
 }
