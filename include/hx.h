@@ -254,6 +254,36 @@ HX_API hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, doubl
 HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream);
 
 /*
+ * Batched solves.  A batch binds n independent problems A_i x_i = b_i (each an
+ * operator with its own mesh, order and coefficients: the three velocity
+ * Helmholtz solves and the pressure Poisson solve of one projection step,
+ * Sec. 4.2 and Sec. 5.3, or unrelated instances) and builds one CUDA graph in
+ * which every instance's whole Jacobi-PCG — initialization, the iterations as a
+ * device-side while loop, the mean-zero closure for pure-Neumann instances, the
+ * true residual and the copy to x_i — is an independent branch.  hx_batch_solve
+ * is then one graph launch and one synchronization for all instances, which
+ * run concurrently on the GPU.  Not in the paper's method as such (it batches
+ * its sub-problem solves).
+ *   ops       host array of n operators (not owned; they must outlive the batch)
+ *   b, x      host arrays of n device pointers (n_dof_i doubles each), bound at
+ *             creation: the graph reads b_i and writes x_i on every solve
+ *   rtol, max_it  stopping rule of every instance (as hx_solve_pcg, x0 = 0)
+ * The graph captures the operators' coefficients: after hx_op_set_coefficients on
+ * an HX_GEOM_ONTHEFLY operator, create the batch again.  Synchronous create.
+ */
+typedef struct hx_batch hx_batch;
+HX_API hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, double* const* x, double rtol,
+                                 int max_it, hx_batch** out);
+
+/* Solve every instance (after the caller's prior work on `stream`); infos: host array of n
+ * results or NULL.  Returns HX_OK when all converged, else the first failing status.
+ * Synchronous. */
+HX_API hx_status hx_batch_solve(hx_batch* batch, void* stream, hx_solve_info* infos);
+
+/* Frees the batch (not its operators or vectors); NULL is ignored. */
+HX_API void hx_batch_destroy(hx_batch* batch);
+
+/*
  * Operator apply that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc.  Examples are code running while a stream is captured into a

@@ -69,6 +69,9 @@ SIGNATURES = {
     "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "hx_solve_pcg_mixed": (_I, [_P, _P, _P, _D, _I, _D, _P, ctypes.POINTER(SolveInfo)]),
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
+    "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, ctypes.POINTER(_P)]),
+    "hx_batch_solve": (_I, [_P, _P, _P]),
+    "hx_batch_destroy": (None, [_P]),
     "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
 }
 
@@ -302,6 +305,48 @@ def hx_op_apply_f32(op, x, y, stream=None):
     _check(_lib.hx_op_apply_f32(op, _fptr(x, n, "x"), _fptr(y, n, "y"), _stream(stream)))
 
 
+def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000):
+    """ops: operator handles; b, x: CUDA float64 tensors (n_dof_i each), bound to the batch."""
+    n = len(ops)
+    if not (len(b) == len(x) == n) or n < 1:
+        raise ValueError("ops, b and x must have the same positive length")
+    H = (ctypes.c_void_p * n)(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops])
+    Bp = (ctypes.c_void_p * n)(*[_dptr(bi, hx_op_info(o)[1], f"b[{i}]").value for i, (o, bi) in enumerate(zip(ops, b))])
+    Xp = (ctypes.c_void_p * n)(*[_dptr(xi, hx_op_info(o)[1], f"x[{i}]").value for i, (o, xi) in enumerate(zip(ops, x))])
+    out = ctypes.c_void_p()
+    _check(_lib.hx_batch_create(n, ctypes.cast(H, ctypes.c_void_p), ctypes.cast(Bp, ctypes.c_void_p),
+                                ctypes.cast(Xp, ctypes.c_void_p), float(rtol), int(max_it), ctypes.byref(out)))
+    return out
+
+
+def hx_batch_solve(batch, n, stream=None, raise_on_fail=True):
+    infos = (SolveInfo * n)()
+    st = _lib.hx_batch_solve(batch, _stream(stream), ctypes.cast(infos, ctypes.c_void_p))
+    if raise_on_fail or st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_BREAKDOWN):
+        _check(st)
+    return [i.as_dict() for i in infos]
+
+
+def hx_batch_destroy(batch):
+    _lib.hx_batch_destroy(batch)
+
+
+class Batch:
+    """Owning handle of a batch; keeps its operators and vectors alive."""
+
+    def __init__(self, ops, b, x, rtol=1e-10, max_it=10000):
+        self.ops, self.b, self.x = list(ops), list(b), list(x)
+        self.handle = hx_batch_create([o.handle for o in self.ops], self.b, self.x, rtol, max_it)
+
+    def solve(self, stream=None, raise_on_fail=True):
+        return hx_batch_solve(self.handle, len(self.ops), stream, raise_on_fail)
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h is not None and _lib is not None:
+            _lib.hx_batch_destroy(h)
+
+
 def _iptr(t, n, name):
     """Device pointer of a contiguous int32 CUDA tensor with n elements."""
     if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.int32" or not t.is_contiguous():
@@ -415,5 +460,5 @@ class Operator:
             _lib.hx_op_destroy(h)
 
 
-__all__ = list(SIGNATURES) + ["Mesh", "Operator", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
+__all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
                               "HX_GEOM_ONTHEFLY"]

@@ -1035,3 +1035,194 @@ hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched solves: every instance's whole Jacobi-PCG is a branch of one graph
+// ---------------------------------------------------------------------------
+struct hx_batch {
+  int n = 0;
+  std::vector<hx_op*> ops;
+  std::vector<const double*> b;
+  std::vector<double*> x;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  HxCgState* st_host = nullptr;  // pinned, n states
+  double* rn2_host = nullptr;    // pinned, n true-residual norms
+};
+
+namespace {
+
+// Capture `fn` (kernel launches on s) into a new graph and add it to G as a child node.
+hx_status add_captured_child(cudaGraph_t G, cudaStream_t s, const cudaGraphNode_t* deps, size_t ndeps,
+                             const std::function<cudaError_t()>& fn, cudaGraphNode_t* node) {
+  cudaGraph_t g = nullptr;
+  HX_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "batch capture");
+  cudaError_t e = fn();
+  cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e != cudaSuccess ? e : e2, "batch capture");
+  }
+  e = cudaGraphAddChildGraphNode(node, G, deps, ndeps, g);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "batch child node");
+  return HX_OK;
+}
+
+hx_status build_batch_graph(hx_batch* B, double rtol, int max_it) {
+  cudaGraph_t G = nullptr;
+  HX_TRY(cudaGraphCreate(&G, 0), "batch graph");
+  hx_status s = HX_OK;
+  cudaStream_t cs = B->stream;
+  for (int i = 0; i < B->n && s == HX_OK; ++i) {
+    hx_op* op = B->ops[i];
+    const hx_mesh* m = op->mesh;
+    const double* bi = B->b[i];
+    double* xi = B->x[i];
+    const HxCgBuffers buf = cg_buffers(op);
+    cudaGraphNode_t init = nullptr, loop = nullptr, tail = nullptr;
+    // 1. initialization: r = P b (mean removed for pure Neumann), z = D^-1 r, p
+    s = add_captured_child(G, cs, nullptr, 0, [&]() {
+      cudaError_t e = cudaSuccess;
+      if (op->singular) e = hx_launch_cg_mean(buf, bi, cs);
+      if (e == cudaSuccess) e = hx_launch_cg_init(buf, bi, (const double*)nullptr, rtol, max_it, cs);
+      if (e == cudaSuccess) e = hx_launch_cg_start(buf, cs);
+      if (e == cudaSuccess && op->singular) e = hx_launch_cg_direction(buf, cs);
+      return e;
+    }, &init);
+    if (s) break;
+    // 2. the CG iterations as a device-side while loop
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = h;
+    np->conditional.type = cudaGraphCondTypeWhile;
+    np->conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&loop, G, &init, nullptr, 1, np);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = np->conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t eb = cg_iteration(op, cs, (unsigned long long)h);
+        e = cudaStreamEndCapture(cs, &body);
+        if (eb != cudaSuccess) e = eb;
+      }
+    }
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "batch while node");
+      break;
+    }
+    // 3. mean-zero closure (pure Neumann), true residual, solution copy
+    s = add_captured_child(G, cs, &loop, 1, [&]() {
+      cudaError_t e3 = cudaSuccess;
+      if (op->singular) {
+        e3 = hx_launch_sum(m->n_dof, op->m1, op->partial, op->counters, op->vol, cs);
+        if (e3 == cudaSuccess) e3 = hx_launch_dot(m->n_dof, op->m1, op->x, op->partial, op->counters, op->vol + 1, cs);
+        if (e3 == cudaSuccess) e3 = hx_launch_shift(m->n_dof, op->x, op->vol + 1, op->vol, cs);
+      }
+      if (e3 == cudaSuccess) e3 = element_apply(op, op->x, 1, nullptr, cs);
+      if (e3 == cudaSuccess)
+        e3 = hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, cs);
+      if (e3 == cudaSuccess)
+        e3 = hx_launch_resnorm(m->n_dof, bi, op->Ap, m->dir, op->partial, op->counters, op->scalars, cs,
+                               op->singular ? &op->st->shift : nullptr);
+      if (e3 == cudaSuccess)
+        e3 = cudaMemcpyAsync(xi, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, cs);
+      return e3;
+    }, &tail);
+  }
+  if (s == HX_OK) {
+    cudaError_t e = cudaGraphInstantiate(&B->exec, G, 0);
+    if (e != cudaSuccess) s = cuda_fail(e, "batch graph instantiate");
+  }
+  cudaGraphDestroy(G);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, double* const* x, double rtol, int max_it,
+                          hx_batch** out) {
+  if (!out) return fail(HX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !ops || !b || !x) return fail(HX_ERR_ARG, "need n >= 1 and non-NULL arrays");
+  if (!(rtol >= 0.0) || max_it < 0) return fail(HX_ERR_ARG, "rtol must be >= 0 and max_it >= 0");
+  for (int i = 0; i < n; ++i)
+    if (!ops[i] || !b[i] || !x[i]) return fail(HX_ERR_ARG, "instance %d: NULL operator or vector", i);
+  hx_batch* B = new (std::nothrow) hx_batch();
+  if (!B) return fail(HX_ERR_OOM, "host allocation failed");
+  B->n = n;
+  B->ops.assign(ops, ops + n);
+  B->b.assign(b, b + n);
+  B->x.assign(x, x + n);
+  hx_status s = HX_OK;
+  for (int i = 0; i < n && s == HX_OK; ++i) {
+    s = ensure_solver(ops[i]);
+    if (s == HX_OK && cudaStreamSynchronize(ops[i]->stream) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "sync");
+  }
+  cudaError_t e = cudaSuccess;
+  if (s == HX_OK) e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && s == HX_OK) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess && s == HX_OK) e = cudaMallocHost((void**)&B->st_host, sizeof(HxCgState) * n);
+  if (e == cudaSuccess && s == HX_OK) e = cudaMallocHost((void**)&B->rn2_host, sizeof(double) * n);
+  if (e != cudaSuccess && s == HX_OK) s = cuda_fail(e, "batch resources");
+  if (s == HX_OK) s = build_batch_graph(B, rtol, max_it);
+  if (s != HX_OK) {
+    hx_batch_destroy(B);
+    return s;
+  }
+  *out = B;
+  return HX_OK;
+}
+
+hx_status hx_batch_solve(hx_batch* B, void* stream, hx_solve_info* infos) {
+  if (!B) return fail(HX_ERR_ARG, "batch is NULL");
+  HX_TRY(cudaEventRecord(B->ev, (cudaStream_t)stream), "event record");
+  HX_TRY(cudaStreamWaitEvent(B->stream, B->ev, 0), "stream wait");
+  HX_TRY(cudaGraphLaunch(B->exec, B->stream), "batch graph launch");
+  for (int i = 0; i < B->n; ++i) {
+    HX_TRY(cudaMemcpyAsync(B->st_host + i, B->ops[i]->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, B->stream),
+           "state read");
+    HX_TRY(cudaMemcpyAsync(B->rn2_host + i, B->ops[i]->scalars, sizeof(double), cudaMemcpyDeviceToHost, B->stream),
+           "residual read");
+  }
+  HX_TRY(cudaStreamSynchronize(B->stream), "batch sync");
+  hx_status worst = HX_OK;
+  for (int i = 0; i < B->n; ++i) {
+    const HxCgState& cs = B->st_host[i];
+    const double bn = std::sqrt(cs.bb);
+    B->ops[i]->launches += 4 * (long long)cs.loops + 8;
+    if (infos) {
+      hx_solve_info& inf = infos[i];
+      inf.iterations = cs.iter;
+      inf.status = cs.done ? cs.status : HX_ERR_CUDA;
+      inf.b_norm = bn;
+      inf.rel_residual = bn > 0 ? std::sqrt(cs.rr) / bn : 0.0;
+      inf.true_rel_residual = bn > 0 ? std::sqrt(B->rn2_host[i]) / bn : std::sqrt(B->rn2_host[i]);
+      inf.kernel_launches = 4 * cs.loops + 8;
+      inf.refinements = 0;
+    }
+    if (!cs.done) worst = HX_ERR_CUDA;
+    else if (cs.status != HX_OK && worst == HX_OK) worst = cs.status;
+  }
+  if (worst != HX_OK) return fail(worst, "at least one batch instance did not converge");
+  return HX_OK;
+}
+
+void hx_batch_destroy(hx_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->ev) cudaEventDestroy(B->ev);
+  if (B->stream) cudaStreamDestroy(B->stream);
+  if (B->st_host) cudaFreeHost(B->st_host);
+  if (B->rn2_host) cudaFreeHost(B->rn2_host);
+  delete B;
+}
+
+}  // extern "C"

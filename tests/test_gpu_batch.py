@@ -1,0 +1,47 @@
+"""Batched solves: independent instances of different order, size and coefficients (and a
+pure-Neumann Poisson instance) in one graph launch; each must equal its own FP64 solve."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from tests.gpu_common import rel_err, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batch_matches_individual_solves():
+    hx = require_gpu()
+    specs = [  # (N, p, alpha, nu, dirichlet faces)
+        (3, 2, 1000.0, 1e-2, 63), (2, 5, 0.0, 1.0, 63), (4, 3, 50.0, 3e-3, 63),
+        (2, 8, 1.0, 0.5, 63), (3, 4, 0.0, 1.0, 0), (5, 2, 1e4, 1e-4, 63),
+    ]
+    ops, bs, xs, refs = [], [], [], []
+    for k, (N, p, a, nu, faces) in enumerate(specs):
+        V = S.structured_vertices(N, N, N, 0.1, 100 + k)
+        mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=faces)
+        op = hx.Operator(mesh, a, nu)
+        b = to_dev(S.random_vector(mesh.n_dof, 200 + k))
+        x_ref, info = op.solve(b, rtol=1e-10)
+        assert info["status"] == 0
+        ops.append(op)
+        bs.append(b)
+        xs.append(torch.full_like(b, float("nan")))
+        refs.append((x_ref, info))
+    batch = hx.Batch(ops, bs, xs, rtol=1e-10)
+    for rep in range(2):  # the bound graph is reusable
+        infos = batch.solve()
+        for (x_ref, info), x, bi in zip(refs, xs, infos):
+            assert bi["status"] == 0 and bi["iterations"] == info["iterations"]
+            assert bi["true_rel_residual"] <= 1.01e-10
+            assert rel_err(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-14
+
+
+def test_batch_reports_failures():
+    hx = require_gpu()
+    V = S.structured_vertices(3, 3, 3, 0.1, 9)
+    op = hx.Operator(hx.Mesh.structured(3, 3, 3, 2, 4, V), 1.0, 1.0)
+    b = to_dev(S.random_vector(op.n_dof, 1))
+    x = torch.zeros_like(b)
+    batch = hx.Batch([op], [b], [x], rtol=1e-14, max_it=2)
+    infos = batch.solve(raise_on_fail=False)
+    assert infos[0]["status"] == hx.HX_ERR_NOT_CONVERGED and infos[0]["iterations"] == 2
