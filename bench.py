@@ -368,6 +368,8 @@ def run_hx(args, world, rank, local):
     torch.cuda.empty_cache()
     if rank == 0 and args.sweep:
         line["sweep"] = run_sweep(hx, torch)
+    if rank == 0 and args.batch:
+        line["batch"] = run_batch(hx, torch, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -424,6 +426,71 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
                              "kernel": f"apply_kernel<float,P={p},Q={q}> (+ assembly, timed together)"}}
 
 
+def batch_specs(seed=4444, n=64):
+    """64 seeded instances: N in [8, 32] elements per direction, p in {2..8}, alpha 0 (Poisson) or
+    1/dt with dt log-uniform in [1e-4, 1e-2], nu log-uniform in [1e-4, 1]."""
+    u = (S.uniform_pm1(seed, 5 * n).reshape(n, 5) + 1.0) / 2.0  # U[0, 1)
+    specs = []
+    for i in range(n):
+        N = 8 + int(u[i, 0] * 25)
+        p = 2 + int(u[i, 1] * 7)
+        alpha = 0.0 if u[i, 2] < 0.5 else 1.0 / (10.0 ** (-4 + 2 * u[i, 3]))
+        nu = 10.0 ** (-4 + 4 * u[i, 4])
+        specs.append((N, p, alpha, nu))
+    return specs
+
+
+def run_batch(hx, torch, args):
+    """configs[3]: 64 independent instances in one graph launch vs one solve after another, plus the
+    projection-step set (3 velocity Helmholtz + 1 pure-Neumann pressure Poisson, 64^3, p = 5)."""
+    def build(specs, faces_of):
+        ops, bs, xs = [], [], []
+        for k, (N, p, a, nu) in enumerate(specs):
+            V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED + k)
+            mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=faces_of(k))
+            op = hx.Operator(mesh, a, nu)
+            xq = mesh.qpoint_coords()
+            f = torch.sin(math.pi * xq[..., 0]) * torch.sin(math.pi * xq[..., 1]) * torch.cos(math.pi * xq[..., 2])
+            ops.append(op)
+            bs.append(op.load_vector(f.contiguous()))
+            xs.append(torch.zeros_like(bs[-1]))
+            del xq, f
+        return ops, bs, xs
+
+    def timed(fn, reps):
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            out = fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps, out
+
+    res = {}
+    for name, specs, faces_of in [
+            ("batch64", batch_specs(), lambda k: 63),
+            ("projection_step", [(64, 5, 1000.0, 1e-2)] * 3 + [(64, 5, 0.0, 1.0)], lambda k: 63 if k < 3 else 0)]:
+        ops, bs, xs = build(specs, faces_of)
+        batch = hx.Batch(ops, bs, xs, rtol=RTOL, max_it=20000)
+        seq = lambda: [hx.hx_solve_pcg(o.handle, b, x, RTOL, 20000, False) for o, b, x in zip(ops, bs, xs)]
+        seq()
+        batch.solve()
+        t_seq, infos_seq = timed(seq, args.batch_reps)
+        t_bat, infos = timed(batch.solve, args.batch_reps)
+        dof_applies = sum(o.n_dof * (i["iterations"] + 1) for o, i in zip(ops, infos))
+        res[name] = {"instances": len(ops), "n_dof_total": sum(o.n_dof for o in ops),
+                     "iterations_total": sum(i["iterations"] for i in infos),
+                     "converged": all(i["status"] == 0 for i in infos),
+                     "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
+                     "batched_s": t_bat, "sequential_s": t_seq, "speedup": t_seq / t_bat,
+                     "batched_gdofs": dof_applies / t_bat / 1e9, "timing": f"{args.batch_reps} reps after 1 warm-up"}
+        del batch, ops, bs, xs
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_sweep(hx, torch):
     """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
     out = []
@@ -463,6 +530,8 @@ def main():
     ap.add_argument("--n", type=int, default=96)
     ap.add_argument("--geom", default="stored", choices=["stored", "onthefly"])
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="add the batched-solve measurement (configs[3])")
+    ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--inner-rtol", type=float, default=1e-5)
