@@ -368,6 +368,8 @@ def run_hx(args, world, rank, local):
     torch.cuda.empty_cache()
     if rank == 0 and args.sweep:
         line["sweep"] = run_sweep(hx, torch)
+    if rank == 0 and args.grad:
+        line["grad"] = run_grad(hx, torch, args)
     if rank == 0 and args.batch:
         line["batch"] = run_batch(hx, torch, args)
     if rank == 0:
@@ -441,7 +443,7 @@ def batch_specs(seed=4444, n=64):
 
 
 def run_batch(hx, torch, args):
-    """configs[3]: 64 independent instances in one graph launch vs one solve after another, plus the
+    """64 independent instances (8^3..40^3, p = 2..8) in one graph launch vs one solve after another, plus the
     projection-step set (3 velocity Helmholtz + 1 pure-Neumann pressure Poisson, 64^3, p = 5)."""
     def build(specs, faces_of):
         ops, bs, xs = [], [], []
@@ -491,6 +493,71 @@ def run_batch(hx, torch, args):
     return res
 
 
+def run_grad(hx, torch, args):
+    """Forward solve + adjoint solve + gradient contraction of L = 1/2 (u - u*)^T M (u - u*) on a
+    perturbed 32^3 mesh, p = 4: nu log-normal (median 1e-2, sigma 0.5) per quadrature point, f a sum
+    of Fourier modes up to wavenumber 4, u* = 0.  Times the whole differentiable step and the
+    gradient kernel alone."""
+    import paper_1910_03032_b300.autograd as ag
+    N, p = 32, 4
+    q = p + 2
+    V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED)
+    mesh = hx.Mesh.structured(N, N, N, p, q, V)
+    E = mesh.n_elem
+    nu = torch.as_tensor(np.exp(np.log(1e-2) + 0.5 * S.uniform_pm1(91, E * q ** 3)).reshape(E, q ** 3),
+                         device="cuda")
+    xq = mesh.qpoint_coords()
+    f = torch.zeros(E, q ** 3, dtype=torch.float64, device="cuda")
+    amp = S.uniform_pm1(92, 64)
+    for k in range(1, 5):
+        for a in range(3):
+            c = amp[4 * (k - 1) + a]
+            f += c * torch.sin(math.pi * k * xq[..., a]) * torch.cos(math.pi * (k - 1) * xq[..., (a + 1) % 3])
+    del xq
+    alpha = 1000.0
+    op = hx.Operator(mesh, alpha, 0.0, nu)
+    mass = hx.Operator(mesh, 1.0, 0.0)
+
+    def step():
+        nu_t = nu.clone().requires_grad_(True)
+        f_t = f.clone().requires_grad_(True)
+        u = ag.solve(op, alpha, nu_t, f_t, rtol=RTOL)
+        L = 0.5 * torch.dot(u, ag.apply(mass, u))
+        L.backward()
+        return L, nu_t.grad, f_t.grad
+
+    for _ in range(2):
+        step()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        L, gnu, gf = step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_step = e0.elapsed_time(e1) / 1e3 / reps
+    u, _ = op.solve(op.load_vector(f), rtol=RTOL)
+    lam = mass.apply(u)
+    dnu = torch.empty_like(nu)
+    dff = torch.empty_like(nu)
+    for _ in range(3):
+        hx.hx_op_gradient(op.handle, u, lam, dnu, dff)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(20):
+        hx.hx_op_gradient(op.handle, u, lam, dnu, dff)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_k = e0.elapsed_time(e1) / 1e3 / 20
+    bytes_k = 8 * (2 * mesh.n_dof + 2 * E * q ** 3 + 24 * E) + 4 * E * (p + 1) ** 3
+    return {"mesh": f"{N}^3", "p": p, "q": q, "n_dof": mesh.n_dof, "loss": L.item(),
+            "step_s": t_step, "grad_kernel_ms": 1e3 * t_k,
+            "grad_kernel_gbs": bytes_k / t_k / 1e9, "grad_kernel_bytes": bytes_k,
+            "timing": f"{reps} steps after 2 warm-up; kernel: 20 launches after 3"}
+
+
 def run_sweep(hx, torch):
     """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
     out = []
@@ -530,7 +597,8 @@ def main():
     ap.add_argument("--n", type=int, default=96)
     ap.add_argument("--geom", default="stored", choices=["stored", "onthefly"])
     ap.add_argument("--sweep", action="store_true")
-    ap.add_argument("--batch", action="store_true", help="add the batched-solve measurement (configs[3])")
+    ap.add_argument("--batch", action="store_true", help="add the batched-solve measurement (64 instances; projection-step set)")
+    ap.add_argument("--grad", action="store_true", help="add the adjoint-gradient measurement (32^3, p = 4)")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")

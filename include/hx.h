@@ -254,6 +254,20 @@ HX_API hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, doubl
 HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream);
 
 /*
+ * Adjoint gradient contraction (not in the paper, which solves forward problems):
+ * for a loss L(u) of the solution of A_c(nu) u = P b(f), with lam solving
+ * A_c lam = P dL/du (hx_solve_pcg with b = dL/du), writes at every quadrature point
+ *   dnu_q[e][q] = dL/dnu_q = -w_q detJ_q (J^-T grad lam)_q . (J^-T grad u)_q
+ *   df_q[e][q]  = dL/df_q  =  w_q detJ_q lam(x_q)      (f_q as in hx_op_load_vector)
+ * by the operator's forward sum-factorized contractions applied to u and lam and a
+ * pointwise contraction with the geometric factor recomputed from the vertices.
+ * u, lam: device, n_dof (Dirichlet entries read as zero); dnu_q, df_q: device,
+ * n_elem x q^3.  Stream-ordered.
+ */
+HX_API hx_status hx_op_gradient(hx_op* op, const double* u, const double* lam, double* dnu_q, double* df_q,
+                                void* stream);
+
+/*
  * Batched solves.  A batch binds n independent problems A_i x_i = b_i (each an
  * operator with its own mesh, order and coefficients: the three velocity
  * Helmholtz solves and the pressure Poisson solve of one projection step,

@@ -43,17 +43,27 @@ def gradients(mesh, alpha, nu_q, f_q, u_target):
     g = Operator(mesh, 1.0, 0.0).apply(d)
     L = 0.5 * d @ g
     lam = solve_dense(op, g)
+    dnu, df = point_gradients(mesh, u, lam)
+    return L, dnu, df, u, lam
+
+
+def point_gradients(mesh, u, lam, elems=None):
+    """(dL/dnu, dL/df) at the quadrature points of ``elems`` (default: all) from u and lam.
+
+    Dirichlet entries of u and lam enter as given (zero for solutions of A_c).
+    """
     ref = mesh.ref
-    _, J = trilinear_map(mesh.vertices[mesh.elem_vert], ref.xi)
-    detJ = np.linalg.det(J)                                   # (E, Q)
+    es = np.arange(mesh.n_elem) if elems is None else np.asarray(elems)
+    _, J = trilinear_map(mesh.vertices[mesh.elem_vert[es]], ref.xi)
+    detJ = np.linalg.det(J)                                   # (e, Q)
     Jinv = np.linalg.inv(J)
     wdet = ref.w[None, :] * detJ
-    uE = u[mesh.restriction]                                  # (E, N)
-    lE = lam[mesh.restriction]
+    R = np.stack([mesh.element_dofs(e) for e in es]) if mesh.restriction is None else mesh.restriction[es]
+    uE, lE = u[R], lam[R]                                     # (e, N)
     # physical gradients at every point: (J^-T dphi)^T coefficient vectors
-    gphys = np.einsum("qnd,eqdk->eqnk", ref.dPhi, Jinv)       # (E, Q, N, 3)
+    gphys = np.einsum("qnd,eqdk->eqnk", ref.dPhi, Jinv)       # (e, Q, N, 3)
     gu = np.einsum("eqnk,en->eqk", gphys, uE)
     gl = np.einsum("eqnk,en->eqk", gphys, lE)
     dnu = -wdet * np.einsum("eqk,eqk->eq", gl, gu)
-    df = wdet * (lE @ ref.Phi.T)                              # (E, Q)
-    return L, dnu, df, u, lam
+    df = wdet * (lE @ ref.Phi.T)                              # (e, Q)
+    return dnu, df

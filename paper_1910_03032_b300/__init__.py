@@ -69,6 +69,7 @@ SIGNATURES = {
     "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "hx_solve_pcg_mixed": (_I, [_P, _P, _P, _D, _I, _D, _P, ctypes.POINTER(SolveInfo)]),
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
+    "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
     "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, ctypes.POINTER(_P)]),
     "hx_batch_solve": (_I, [_P, _P, _P]),
     "hx_batch_destroy": (None, [_P]),
@@ -305,6 +306,12 @@ def hx_op_apply_f32(op, x, y, stream=None):
     _check(_lib.hx_op_apply_f32(op, _fptr(x, n, "x"), _fptr(y, n, "y"), _stream(stream)))
 
 
+def hx_op_gradient(op, u, lam, dnu_q, df_q, stream=None):
+    E, n, _, q = hx_op_info(op)
+    _check(_lib.hx_op_gradient(op, _dptr(u, n, "u"), _dptr(lam, n, "lam"), _dptr(dnu_q, E * q ** 3, "dnu_q"),
+                               _dptr(df_q, E * q ** 3, "df_q"), _stream(stream)))
+
+
 def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000):
     """ops: operator handles; b, x: CUDA float64 tensors (n_dof_i each), bound to the batch."""
     n = len(ops)
@@ -410,6 +417,7 @@ class Operator:
         self.mesh = mesh  # keeps the mesh alive
         self.handle = hx_op_create(mesh.handle, alpha, nu, nu_q, geom_mode, stream)
         self.n_dof = mesh.n_dof
+        self.coef_token = object()
 
     def apply(self, x, y=None, constrained=False, stream=None):
         import torch
@@ -431,6 +439,7 @@ class Operator:
 
     def set_coefficients(self, alpha, nu, nu_q=None, stream=None):
         hx_op_set_coefficients(self.handle, alpha, nu, nu_q, stream)
+        self.coef_token = object()  # identifies the coefficients now set
 
     def launch_count(self):
         return hx_op_launch_count(self.handle)
@@ -447,6 +456,15 @@ class Operator:
         x = torch.empty_like(b)
         info = hx_solve_pcg_mixed(self.handle, b, x, rtol, max_it, inner_rtol, stream, raise_on_fail)
         return x, info
+
+    def gradient(self, u, lam, stream=None):
+        """(dL/dnu_q, dL/df_q), each n_elem x q^3, from the solution u and the adjoint lam."""
+        import torch
+        shape = (self.mesh.n_elem, self.mesh.q ** 3)
+        dnu = torch.empty(shape, dtype=torch.float64, device="cuda")
+        df = torch.empty(shape, dtype=torch.float64, device="cuda")
+        hx_op_gradient(self.handle, u, lam, dnu, df, stream)
+        return dnu, df
 
     def apply_f32(self, x, stream=None):
         import torch

@@ -1226,3 +1226,26 @@ void hx_batch_destroy(hx_batch* B) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// adjoint gradients
+// ---------------------------------------------------------------------------
+extern "C" hx_status hx_op_gradient(hx_op* op, const double* u, const double* lam, double* dnu_q, double* df_q,
+                                    void* stream) {
+  if (!op || !u || !lam || !dnu_q || !df_q) return fail(HX_ERR_ARG, "NULL argument");
+  static const hx_grad_launcher t[] = {nullptr, hx_launch_grad_p1, hx_launch_grad_p2, hx_launch_grad_p3,
+                                       hx_launch_grad_p4, hx_launch_grad_p5, hx_launch_grad_p6,
+                                       hx_launch_grad_p7, hx_launch_grad_p8};
+  const hx_mesh* m = op->mesh;
+  HxGradArgs a;
+  a.E = m->E;
+  a.R = m->R;
+  a.u = u;
+  a.lam = lam;
+  a.X8 = m->X8;
+  a.dnu = dnu_q;
+  a.df = df_q;
+  HX_TRY(t[m->p](m->T, a, (cudaStream_t)stream), "gradient kernel");
+  op->launches += 1;
+  return HX_OK;
+}

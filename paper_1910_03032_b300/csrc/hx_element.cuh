@@ -458,6 +458,123 @@ __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTabl
   transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
 }
 
+// Adjoint gradients at every quadrature point (not part of the paper's method):
+//   dnu_q = -w_q detJ_q (J^-T grad lam)_q . (J^-T grad u)_q,   df_q = w_q detJ_q lam(x_q),
+// the derivatives of L(u(nu, f)) through A_c lam = dL/du.  Both vectors go through the
+// forward sum-factorized stages of the operator kernel side by side (six regions per
+// element: D, X, Y for u, then for lam); the pointwise stage contracts the gradients
+// with the geometric factor recomputed from the element vertices.
+template <int P, int Q, int NE, int NT>
+__global__ void __launch_bounds__(NT) grad_kernel(const __grid_constant__ HxTables T, const HxGradArgs A) {
+  using Lt = Layout<Q>;
+  constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q;
+  constexpr int SY = Lt::SY, SZ = Lt::SZ, RG = Lt::RG, R6 = 6 * RG;
+  constexpr int CQ = (Q + 1) / 2, CN = (N + 1) / 2;
+  static_assert(NT >= NE * Q2, "one thread per z-column");
+  extern __shared__ double smem[];
+  double* geo = smem + NE * R6;
+  const long long e0 = (long long)blockIdx.x * NE;
+  const int tid = threadIdx.x;
+  for (int el = tid; el < NE; el += NT) {
+    const long long e = e0 + el;
+    double X8[24];
+    for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
+    trilinear_coeffs(X8, geo + el * 24);
+  }
+  // 1. gather (Dirichlet entries as zero) and B along x, for u (v = 0) and lam (v = 1)
+  for (int t = tid; t < 2 * NE * N * N; t += NT) {
+    const int v = t / (NE * N * N), tt = t - v * NE * N * N;
+    const int el = tt / (N * N), r = tt - el * (N * N);
+    const long long e = e0 + el;
+    const double* src = v ? A.lam : A.u;
+    double vin[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int g = (e < A.E) ? __ldg(A.R + e * N3 + r * N + i) : -1;
+      vin[i] = (g >= 0) ? __ldg(src + g) : 0.0;
+    }
+    const int k = r / N, j = r - k * N;
+    double vout[Q];
+    eo_apply<N, Q, 1>(T.Be, T.Bo, vin, vout);
+    store_line<Q>(smem + el * R6 + v * 3 * RG + k * SZ + j * SY, 1, vout);
+  }
+  __syncthreads();
+  // 2. B along y
+  for (int t = tid; t < 2 * NE * N * Q; t += NT) {
+    const int v = t / (NE * N * Q), tt = t - v * NE * N * Q;
+    const int el = tt / (N * Q), r = tt - el * (N * Q);
+    const int k = r / Q, iq = r - k * Q;
+    double* line = smem + el * R6 + v * 3 * RG + k * SZ + iq;
+    double vin[N], vout[Q];
+    load_line<N>(line, SY, vin);
+    eo_apply<N, Q, 1>(T.Be, T.Bo, vin, vout);
+    store_line<Q>(line, SY, vout);
+  }
+  __syncthreads();
+  // 3. columns: B along z (values kept in D) and d/dxi_3 (kept in registers), both vectors
+  const bool owner = tid < NE * Q2;
+  const int cel = tid / Q2, c = tid - cel * Q2;
+  const int cs = (c / Q) * SY + (c % Q);
+  double du[Q], dl[Q];
+  if (owner) {
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      double* col = smem + cel * R6 + v * 3 * RG + cs;
+      double vin[N], val[Q], ev[CN], od[CN], E[CQ], O[CQ], Ed[CQ], Od[CQ], d[Q];
+      load_line<N>(col, SZ, vin);
+      fold<N>(vin, ev, od);
+      products<N, Q, 1>(T.Be, T.Bo, ev, od, E, O);
+      combine<Q, 1>(E, O, val);
+      store_line<Q>(col, SZ, val);
+      products<Q, Q, -1>(T.De2, T.Do2, E, O, Ed, Od);
+      combine<Q, -1>(Ed, Od, d);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) (v ? dl : du)[k] = d[k];
+    }
+  }
+  __syncthreads();
+  // 4. d/dxi_1 and d/dxi_2 of both vectors
+  for (int t = tid; t < 4 * NE * Q2; t += NT) {
+    const int v = t / (2 * NE * Q2), tt = t - v * 2 * NE * Q2;
+    const int el = tt / (2 * Q2), r = tt - el * (2 * Q2);
+    const int dir = r >= Q2;
+    const int rr = r - dir * Q2;
+    const int a = rr / Q, b = rr - a * Q;
+    const int off = dir ? (a * SZ + b) : (a * SZ + b * SY);
+    const int stride = dir ? SY : 1;
+    double* base = smem + el * R6 + v * 3 * RG;
+    double uu[Q], d[Q];
+    load_line<Q>(base + off, stride, uu);
+    eo_apply<Q, Q, -1>(T.De, T.Do, uu, d);
+    store_line<Q>(base + (1 + dir) * RG + off, stride, d);
+  }
+  __syncthreads();
+  // 5. columns: the pointwise contractions, written with consecutive points in consecutive threads
+  if (owner) {
+    const long long e = e0 + cel;
+    const double* U = smem + cel * R6 + cs;
+    const double* Lm = U + 3 * RG;
+    const int iq = c % Q, jq = c / Q;
+#pragma unroll
+    for (int kq = 0; kq < Q; ++kq) {
+      double j0[3], j1[3], j2[3], f[7];
+      trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
+      const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
+      point_factors(j0, j1, j2, w, w, f);  // f[0] = w detJ, f[1..6] = w detJ J^-1 J^-T
+      const double u1 = U[RG + kq * SZ], u2 = U[2 * RG + kq * SZ], u3 = du[kq];
+      const double l1 = Lm[RG + kq * SZ], l2 = Lm[2 * RG + kq * SZ], l3 = dl[kq];
+      const double g1 = f[1] * u1 + f[2] * u2 + f[3] * u3;
+      const double g2 = f[2] * u1 + f[4] * u2 + f[5] * u3;
+      const double g3 = f[3] * u1 + f[5] * u2 + f[6] * u3;
+      if (e < A.E) {
+        const long long o = e * Q3 + kq * Q2 + c;
+        A.dnu[o] = -(l1 * g1 + l2 * g2 + l3 * g3);
+        A.df[o] = f[0] * Lm[kq * SZ];
+      }
+    }
+  }
+}
+
 // Diagonal of the element matrices, sum-factorized:
 // diag[k][j][i] = sum_{c,b,a} m (BB_ai BB_bj BB_ck) + G00 DD_ai BB_bj BB_ck + G11 BB_ai DD_bj BB_ck
 //   + G22 BB_ai BB_bj DD_ck + 2 G01 BD_ai BD_bj BB_ck + 2 G02 BD_ai BB_bj BD_ck + 2 G12 BB_ai BD_bj BD_ck
@@ -635,6 +752,20 @@ cudaError_t launch_diag_q(const HxTables& T, const HxDiagArgs& A, int geom, cuda
 }
 
 template <int P, int Q>
+cudaError_t launch_grad_q(const HxTables& T, const HxGradArgs& A, cudaStream_t s) {
+  constexpr int NE = Config<P, Q>::NE_D > 1 ? Config<P, Q>::NE_D / 2 : 1;
+  constexpr int NT = ((NE * Q * Q + 31) / 32) * 32;
+  const size_t shmem = sizeof(double) * (size_t)(NE * 6 * Layout<Q>::RG + NE * 24);
+  auto k = grad_kernel<P, Q, NE, NT>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  if (err != cudaSuccess) return err;
+  const long long blocks = (A.E + NE - 1) / NE;
+  if (blocks == 0) return cudaSuccess;
+  k<<<(unsigned)blocks, NT, shmem, s>>>(T, A);
+  return cudaGetLastError();
+}
+
+template <int P, int Q>
 cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s) {
   constexpr int NE = Config<P, Q>::NE, NT = Config<P, Q>::NT;
   const size_t shmem = sizeof(double) * (size_t)(NE * Layout<Q>::R3 + NE * 24);
@@ -663,6 +794,11 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
   cudaError_t hx_launch_diag_p##P(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {     \
     if (T.q == P + 1) return hx::launch_diag_q<P, P + 1>(T, A, geom, s);                                  \
     if (T.q == P + 2) return hx::launch_diag_q<P, P + 2>(T, A, geom, s);                                  \
+    return cudaErrorInvalidValue;                                                                          \
+  }                                                                                                        \
+  cudaError_t hx_launch_grad_p##P(const HxTables& T, const HxGradArgs& A, cudaStream_t s) {               \
+    if (T.q == P + 1) return hx::launch_grad_q<P, P + 1>(T, A, s);                                        \
+    if (T.q == P + 2) return hx::launch_grad_q<P, P + 2>(T, A, s);                                        \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_load_p##P(const HxTables& T, const HxLoadArgs& A, cudaStream_t s) {               \

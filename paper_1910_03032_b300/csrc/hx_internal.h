@@ -44,6 +44,17 @@ struct HxLoadArgs {
   double* yE;
 };
 
+// Arguments of the adjoint-gradient kernel: per-point dL/dnu and dL/df from u and lam.
+struct HxGradArgs {
+  long long E;
+  const int* R;           // restriction (Dirichlet entries read as zero)
+  const double* u;        // forward solution (L-vector)
+  const double* lam;      // adjoint solution (L-vector)
+  const double* X8;       // [E][8][3]
+  double* dnu;            // [E][q^3] out: -w detJ (J^-T grad lam).(J^-T grad u)
+  double* df;             // [E][q^3] out: w detJ lam(x_q)
+};
+
 enum { HX_KGEOM_STORED = 0, HX_KGEOM_ONTHEFLY = 1 };
 
 // Per-order launchers (one translation unit per p; q in {p+1, p+2}).
@@ -51,12 +62,14 @@ typedef cudaError_t (*hx_apply_launcher)(const HxTables&, const HxApplyArgs&, in
 typedef cudaError_t (*hx_diag_launcher)(const HxTables&, const HxDiagArgs&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cudaStream_t);
 typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, cudaStream_t);
+typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cudaStream_t);
 
 #define HX_DECLARE_ORDER(P)                                                                        \
   cudaError_t hx_launch_apply_p##P(const HxTables&, const HxApplyArgs&, int, cudaStream_t);       \
   cudaError_t hx_launch_diag_p##P(const HxTables&, const HxDiagArgs&, int, cudaStream_t);         \
   cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);              \
-  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, cudaStream_t);
+  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, cudaStream_t);  \
+  cudaError_t hx_launch_grad_p##P(const HxTables&, const HxGradArgs&, cudaStream_t);
 HX_DECLARE_ORDER(1)
 HX_DECLARE_ORDER(2)
 HX_DECLARE_ORDER(3)
