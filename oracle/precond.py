@@ -1,0 +1,75 @@
+"""Oracle for the preconditioners of Sec. 5.1 and Sec. 5.2 (test infrastructure only).
+
+Collocated mass (Sec. 5.1): integrating the mass form with the Gauss-Lobatto rule
+at the nodes of the nodal basis makes it diagonal,
+    Mc_ii = sum over elements K and local nodes l of K with global id i of
+            w_a w_b w_c detJ_K(xi_l),   l = (a, b, c),
+where w are the Gauss-Lobatto weights w_j = 2 / (p (p+1) P_p(x_j)^2).
+
+Low-order refined operator (Sec. 5.2): A_LOR = c M_LOR + nu K_LOR is the
+standard Q1 discretization on the mesh obtained by cutting every element along
+the Cartesian product of its Gauss-Lobatto points.  The DoFs are shared with the
+high-order space (the identity maps one to the other).  Each sub-element is the
+image of a box of the reference cube under the element's trilinear map.  That
+image is itself trilinear in the sub-element's local coordinates, with the
+mapped Gauss-Lobatto nodes as corners.  So the LOR mesh is a p = 1 mesh on the
+mapped nodes, and its operator is the ``fem.Operator`` of that mesh.  For
+"standard" quadrature we read 2 Gauss points per direction, which integrates
+the Q1 mass exactly on affine sub-elements.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .basis import gll_nodes, legendre
+from .fem import Mesh, Operator, trilinear_map
+
+
+def gll_weights(p: int) -> np.ndarray:
+    """Gauss-Lobatto weights of the p+1 nodes: 2 / (p (p+1) P_p(x_j)^2)."""
+    x = gll_nodes(p)
+    P, _ = legendre(p, x)
+    return 2.0 / (p * (p + 1) * P * P)
+
+
+def collocated_mass_element(mesh: Mesh, elems=None) -> np.ndarray:
+    """(e, (p+1)^3) element diagonals w_a w_b w_c detJ at the local nodes (node index a + n b + n^2 c)."""
+    p, n = mesh.p, mesh.p + 1
+    w = gll_weights(p)
+    es = np.arange(mesh.n_elem) if elems is None else np.asarray(elems)
+    _, J = trilinear_map(mesh.vertices[mesh.elem_vert[es]], mesh.ref.node_xi)
+    c, b, a = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    w3 = (w[a] * w[b] * w[c]).ravel()
+    return w3[None, :] * np.linalg.det(J)
+
+
+def collocated_mass_diagonal(mesh: Mesh, alpha: float = 1.0) -> np.ndarray:
+    """alpha Mc as an n_dof vector (unconstrained: Dirichlet rows keep their value)."""
+    d = np.zeros(mesh.n_dof)
+    np.add.at(d, mesh.restriction, alpha * collocated_mass_element(mesh))
+    return d
+
+
+def lor_mesh(mesh: Mesh) -> Mesh:
+    """The p = 1, q = 2 mesh of the Gauss-Lobatto refined sub-elements (same DoFs and Dirichlet mask).
+
+    Sub-element (s, t, u) of element K has corners at local nodes (s + dx, t + dy, u + dz),
+    corner index dx + 2 dy + 4 dz; sub-elements are numbered K p^3 + s + p t + p^2 u.
+    """
+    p, n = mesh.p, mesh.p + 1
+    R = mesh.restriction                                        # (E, n^3)
+    u, t, s = np.meshgrid(np.arange(p), np.arange(p), np.arange(p), indexing="ij")
+    s, t, u = s.ravel(), t.ravel(), u.ravel()                   # sub-element order s fastest
+    corners = []
+    for c in range(8):
+        dx, dy, dz = c & 1, (c >> 1) & 1, (c >> 2) & 1
+        corners.append((s + dx) + n * (t + dy) + n * n * (u + dz))
+    L = np.stack(corners, axis=1)                               # (p^3, 8) local node ids
+    sub = R[:, L].reshape(-1, 8)                                # (E p^3, 8) global ids
+    X = mesh.node_coords()
+    return Mesh(1, 2, X, sub, sub, mesh.n_dof, mesh.dirichlet)
+
+
+def lor_operator(mesh: Mesh, alpha: float, nu: float) -> Operator:
+    """A_LOR = alpha M_LOR + nu K_LOR (Sec. 5.2) as the oracle operator of the refined p = 1 mesh."""
+    return Operator(lor_mesh(mesh), alpha, nu)

@@ -1,0 +1,126 @@
+"""Oracle preconditioners (collocated mass, Sec. 5.1; low-order refined operator, Sec. 5.2) pinned by
+closed forms and published spectral bounds."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import synthetic as S
+from oracle import fem, precond
+from oracle.basis import gll_nodes
+
+
+def one_element(p, A=None):
+    V = S.structured_vertices(1, 1, 1, 0.0, 1)
+    if A is not None:
+        V = S.affine_map(V, np.asarray(A, dtype=float), np.array([0.3, -0.2, 0.1]))
+    return fem.StructuredMesh(1, 1, 1, p, p + 2, V, S.structured_elem_vert(1, 1, 1), dirichlet_boundary=False)
+
+
+SHEAR = [[1.5, 0.3, 0.0], [0.0, 0.8, 0.2], [0.1, 0.0, 1.2]]
+
+
+def test_gll_weights_closed_forms():
+    assert np.allclose(precond.gll_weights(1), [1, 1], rtol=0, atol=1e-15)
+    assert np.allclose(precond.gll_weights(2), [1 / 3, 4 / 3, 1 / 3], rtol=0, atol=1e-15)
+    assert np.allclose(precond.gll_weights(3), [1 / 6, 5 / 6, 5 / 6, 1 / 6], rtol=0, atol=1e-15)
+    assert np.allclose(precond.gll_weights(4), [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_gll_rule_exact_to_degree_2p_minus_1(p):
+    x, w = gll_nodes(p), precond.gll_weights(p)
+    for k in range(2 * p):
+        exact = float(Fraction(2, k + 1)) if k % 2 == 0 else 0.0
+        assert abs(w @ x ** k - exact) <= 1e-14
+    # and not beyond: x^(2p) is integrated with an error
+    assert abs(w @ x ** (2 * p) - 2.0 / (2 * p + 1)) > 1e-7
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_collocated_mass_sums_to_volume(p):
+    """detJ of a trilinear map has degree <= 2 per variable; GLL with p >= 2 integrates it exactly."""
+    shape = (3, 2, 2)
+    V = S.structured_vertices(*shape, 0.1, 7)
+    mesh = fem.StructuredMesh(*shape, p, p + 2, V, S.structured_elem_vert(*shape))
+    d = precond.collocated_mass_diagonal(mesh, 2.5)
+    assert abs(d.sum() - 2.5) <= 1e-13
+    assert np.all(d > 0)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("A", [None, SHEAR])
+def test_collocated_mass_spectral_bounds(p, A):
+    """On an affine element M and Mc are tensor products of the 1D forms scaled by the constant detJ,
+    and the 1D pencil has eigenvalues in [p / (2p + 1), 1], both attained (the mode P_p gives the
+    lower end): so the 3D spectrum of Mc^-1 M spans [(p / (2p + 1))^3, 1]."""
+    mesh = one_element(p, A)
+    M = fem.Operator(mesh, 1.0, 0.0).assembled()
+    d = precond.collocated_mass_diagonal(mesh)
+    ev = sl.eigh(M, np.diag(d), eigvals_only=True)
+    lo = (p / (2 * p + 1)) ** 3
+    assert abs(ev.min() - lo) <= 1e-12 and abs(ev.max() - 1.0) <= 1e-12
+
+
+def test_lor_of_p1_is_the_mesh_itself():
+    """For p = 1 the refined mesh is the original mesh: A_LOR = the q = 2 operator of Q_1."""
+    shape = (3, 2, 2)
+    V = S.structured_vertices(*shape, 0.1, 8)
+    m1 = fem.StructuredMesh(*shape, 1, 2, V, S.structured_elem_vert(*shape))
+    A = fem.Operator(m1, 2.0, 0.7).assembled()
+    AL = precond.lor_operator(m1, 2.0, 0.7).assembled()
+    assert np.abs(A - AL).max() <= 1e-15 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("p", [2, 4, 7])
+def test_lor_volume_and_null_space(p):
+    shape = (2, 2, 2)
+    V = S.structured_vertices(*shape, 0.1, 9)
+    mesh = fem.StructuredMesh(*shape, p, p + 2, V, S.structured_elem_vert(*shape))
+    one = np.ones(mesh.n_dof)
+    ML = precond.lor_operator(mesh, 1.0, 0.0)
+    KL = precond.lor_operator(mesh, 0.0, 1.0)
+    assert abs(one @ ML.apply(one) - 1.0) <= 1e-13
+    assert np.abs(KL.apply(one)).max() <= 1e-13 * np.abs(KL.assembled()).max()
+    # every sub-element is positively oriented: the LOR mass diagonal is positive
+    assert np.all(ML.diagonal() > 0)
+
+
+@pytest.mark.parametrize("p", range(2, 9))
+def test_lor_stiffness_equivalence_1d(p):
+    """On one box element, functions of x alone (zero at the x = const faces) reduce both stiffness
+    forms to 1D times the same constant: K_LOR <= K (the piecewise-linear interpolant has the mean
+    slope on every sub-interval) and K <= (pi^2 / 4) K_LOR (the FEM-SEM equivalence on Gauss-Lobatto
+    points); for p = 2 the single interior mode gives exactly 4/3."""
+    mesh = one_element(p, np.diag([2.0, 0.7, 1.3]))
+    n = p + 1
+    K = fem.Operator(mesh, 0.0, 1.0).assembled()
+    KL = precond.lor_operator(mesh, 0.0, 1.0).assembled()
+    V = np.zeros((n ** 3, n - 2))
+    for i in range(1, n - 1):
+        for k in range(n):
+            for j in range(n):
+                V[i + n * j + n * n * k, i - 1] = 1.0
+    ev = sl.eigh(V.T @ K @ V, V.T @ KL @ V, eigvals_only=True)
+    assert ev.min() >= 1.0 - 1e-12 and ev.max() <= np.pi ** 2 / 4
+    if p == 2:
+        assert abs(ev[0] - 4.0 / 3.0) <= 1e-12
+
+
+def test_lor_condition_bounded_in_p():
+    """kappa(A_LOR^-1 A) stays bounded as p grows while kappa(diag(A)^-1 A) grows (Sec. 5.2)."""
+    shape = (2, 2, 2)
+    V = S.structured_vertices(*shape, 0.1, 10)
+    kl, kj = [], []
+    for p in (2, 4, 6):
+        mesh = fem.StructuredMesh(*shape, p, p + 2, V, S.structured_elem_vert(*shape))
+        A = fem.Operator(mesh, 1.0, 1.0).assembled(constrained=True)
+        AL = precond.lor_operator(mesh, 1.0, 1.0).assembled(constrained=True)
+        ev = sl.eigh(A, AL, eigvals_only=True)
+        kl.append(ev.max() / ev.min())
+        d = np.diag(A)
+        ej = sl.eigh(A, np.diag(d), eigvals_only=True)
+        kj.append(ej.max() / ej.min())
+    assert max(kl) <= 12.0
+    assert kj[-1] > 5 * kl[-1] and kj[-1] > 2 * kj[0]
