@@ -254,6 +254,40 @@ HX_API hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, doubl
 HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream);
 
 /*
+ * Preconditioners of the PCG solves (Sec. 5).
+ *   HX_PREC_JACOBI           z = diag(A)^-1 r, the exact diagonal of alpha M + nu K (default)
+ *   HX_PREC_COLLOCATED_MASS  z = (alpha Mc)^-1 r, Mc the mass matrix integrated with the
+ *                            Gauss-Lobatto rule at the nodes of the nodal basis, which is
+ *                            diagonal and spectrally equivalent to M independently of h and
+ *                            p (Sec. 5.1): the preconditioner of mass-dominated solves
+ * Dirichlet rows use z = r in both.
+ */
+#define HX_PREC_JACOBI 0
+#define HX_PREC_COLLOCATED_MASS 1
+
+/*
+ * alpha Mc as a vector (Sec. 5.1): diag[i] = alpha sum over elements K and local nodes
+ * l = (a, b, c) of K with global id i of w_a w_b w_c detJ_K(xi_l), w the Gauss-Lobatto
+ * weights.  Unconstrained (Dirichlet rows keep their value).  diag: device, n_dof.
+ * Stream-ordered.
+ */
+HX_API hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream);
+
+/*
+ * Select the preconditioner of hx_solve_pcg, hx_solve_pcg_host, hx_solve_pcg_mixed and
+ * batched solves of this operator (kind: HX_PREC_*).  HX_PREC_COLLOCATED_MASS needs
+ * alpha > 0 (HX_ERR_ARG otherwise, also from a later hx_op_set_coefficients with
+ * alpha <= 0).  It follows later hx_op_set_coefficients calls.  Stream-ordered.
+ */
+HX_API hx_status hx_op_set_preconditioner(hx_op* op, int kind, void* stream);
+
+/*
+ * z = the current preconditioner applied to r (as one PCG step applies it).
+ * r, z: device, n_dof.  Sets up the solver workspace on first use.  Stream-ordered.
+ */
+HX_API hx_status hx_op_precond_apply(hx_op* op, const double* r, double* z, void* stream);
+
+/*
  * Adjoint gradient contraction (not in the paper, which solves forward problems):
  * for a loss L(u) of the solution of A_c(nu) u = P b(f), with lam solving
  * A_c lam = P dL/du (hx_solve_pcg with b = dL/du), writes at every quadrature point

@@ -28,6 +28,8 @@ HX_ERR_BREAKDOWN = -6
 HX_ERR_UNSUPPORTED = -7
 HX_GEOM_STORED = 0
 HX_GEOM_ONTHEFLY = 1
+HX_PREC_JACOBI = 0
+HX_PREC_COLLOCATED_MASS = 1
 
 _NAMES = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_CUDA", -3: "HX_ERR_OOM", -4: "HX_ERR_INVALID_MESH",
           -5: "HX_ERR_NOT_CONVERGED", -6: "HX_ERR_BREAKDOWN", -7: "HX_ERR_UNSUPPORTED"}
@@ -70,6 +72,9 @@ SIGNATURES = {
     "hx_solve_pcg_mixed": (_I, [_P, _P, _P, _D, _I, _D, _P, ctypes.POINTER(SolveInfo)]),
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
     "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
+    "hx_op_collocated_mass": (_I, [_P, _P, _P]),
+    "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, _P]),
+    "hx_op_precond_apply": (_I, [_P, _P, _P, _P]),
     "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, ctypes.POINTER(_P)]),
     "hx_batch_solve": (_I, [_P, _P, _P]),
     "hx_batch_destroy": (None, [_P]),
@@ -312,6 +317,20 @@ def hx_op_gradient(op, u, lam, dnu_q, df_q, stream=None):
                                _dptr(df_q, E * q ** 3, "df_q"), _stream(stream)))
 
 
+def hx_op_collocated_mass(op, diag, stream=None):
+    n = hx_op_info(op)[1]
+    _check(_lib.hx_op_collocated_mass(op, _dptr(diag, n, "diag"), _stream(stream)))
+
+
+def hx_op_set_preconditioner(op, kind, stream=None):
+    _check(_lib.hx_op_set_preconditioner(op, int(kind), _stream(stream)))
+
+
+def hx_op_precond_apply(op, r, z, stream=None):
+    n = hx_op_info(op)[1]
+    _check(_lib.hx_op_precond_apply(op, _dptr(r, n, "r"), _dptr(z, n, "z"), _stream(stream)))
+
+
 def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000):
     """ops: operator handles; b, x: CUDA float64 tensors (n_dof_i each), bound to the batch."""
     n = len(ops)
@@ -457,6 +476,22 @@ class Operator:
         info = hx_solve_pcg_mixed(self.handle, b, x, rtol, max_it, inner_rtol, stream, raise_on_fail)
         return x, info
 
+    def collocated_mass(self, stream=None):
+        """alpha Mc, the Gauss-Lobatto collocated (diagonal) mass, as an n_dof vector."""
+        import torch
+        d = torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+        hx_op_collocated_mass(self.handle, d, stream)
+        return d
+
+    def set_preconditioner(self, kind, stream=None):
+        hx_op_set_preconditioner(self.handle, kind, stream)
+
+    def precond_apply(self, r, stream=None):
+        import torch
+        z = torch.empty_like(r)
+        hx_op_precond_apply(self.handle, r, z, stream)
+        return z
+
     def gradient(self, u, lam, stream=None):
         """(dL/dnu_q, dL/df_q), each n_elem x q^3, from the solution u and the adjoint lam."""
         import torch
@@ -479,4 +514,4 @@ class Operator:
 
 
 __all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
-                              "HX_GEOM_ONTHEFLY"]
+                              "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS"]

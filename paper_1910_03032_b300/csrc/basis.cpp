@@ -178,7 +178,12 @@ int hx_build_tables(int p, int q, HxTables* t) {
   std::memcpy(t->B, B.data(), sizeof(double) * q * n);
   std::memcpy(t->D, D.data(), sizeof(double) * q * n);
   for (int i = 0; i < q; ++i) { t->xq[i] = xq[i]; t->wq[i] = wq[i]; }
-  for (int i = 0; i < n; ++i) t->xn[i] = xn[i];
+  for (int i = 0; i < n; ++i) {
+    double P, Pm;
+    legendre_pair(p, xn[i], &P, &Pm);
+    t->xn[i] = xn[i];
+    t->wn[i] = 2.0 / (p * (p + 1.0) * P * P);
+  }
   return 0;
 }
 
@@ -207,4 +212,5 @@ void hx_tables_to_float(const HxTables& d, HxTablesF* f) {
   cp(d.xq, f->xq, HX_QMAX);
   cp(d.wq, f->wq, HX_QMAX);
   cp(d.xn, f->xn, HX_NMAX);
+  cp(d.wn, f->wn, HX_NMAX);
 }

@@ -113,6 +113,9 @@ struct hx_op {
   bool singular = false;
   double* m1 = nullptr;         // [n_dof] m1_i = int phi_i dx (mean-zero closure)
   double* vol = nullptr;        // [2] device: sum of m1 (the domain volume), and a dot-product slot
+  // preconditioner: HX_PREC_JACOBI (dinv = 1 / diag A) or HX_PREC_COLLOCATED_MASS (1 / (alpha Mc))
+  int prec = HX_PREC_JACOBI;
+  double* pdiag = nullptr;      // [n_dof] alpha Mc (collocated mass)
 };
 
 namespace {
@@ -375,12 +378,31 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->st32);
   dfree(op->m1);
   dfree(op->vol);
+  dfree(op->pdiag);
   delete op;
 }
 
 }  // extern "C"
 
 namespace {
+
+// dinv = the inverse of the preconditioner's diagonal (Dirichlet rows 1): diag(A) for
+// Jacobi, alpha Mc for the collocated mass (Sec. 5.1).  Counts its launches in *nl.
+hx_status refresh_dinv(hx_op* op, cudaStream_t s, int* nl) {
+  const hx_mesh* m = op->mesh;
+  const double* d = op->diag;
+  if (op->prec == HX_PREC_COLLOCATED_MASS) {
+    if (!(op->alpha > 0.0)) return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
+    HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
+    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->pdiag, s),
+           "collocated mass assembly");
+    *nl += 2;
+    d = op->pdiag;
+  }
+  HX_TRY(hx_launch_dinv(m->n_dof, d, m->dir, op->dinv, s), "dinv");
+  *nl += 1;
+  return HX_OK;
+}
 
 // Coefficient-dependent setup, stream-ordered and allocation-free: stored
 // factors (alpha, nu) and the assembled diagonal (and its inverse once the
@@ -417,11 +439,12 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
   HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
          "diagonal assembly");
   nl += 2;
-  if (op->dinv) {
-    HX_TRY(hx_launch_dinv(m->n_dof, op->diag, m->dir, op->dinv, s), "dinv");
-    ++nl;
-  }
   if (launches) *launches = nl;
+  if (op->dinv) {
+    hx_status st = refresh_dinv(op, s, &nl);
+    if (launches) *launches = nl;
+    if (st) return st;
+  }
   return HX_OK;
 }
 
@@ -600,9 +623,10 @@ hx_status ensure_solver(hx_op* op) {
   HX_TRY(cudaEventCreateWithFlags(&op->ev, cudaEventDisableTiming), "solver event");
   HX_TRY(cudaMemsetAsync(op->st, 0, sizeof(HxCgState), op->stream), "state init");
   HX_TRY(cudaMemsetAsync(op->counters, 0, 2 * sizeof(unsigned int), op->stream), "counter init");
-  HX_TRY(hx_launch_dinv(n, op->diag, op->mesh->dir, op->dinv, op->stream), "dinv");
-  op->launches += 1;
-  return HX_OK;
+  int nl = 0;
+  s = refresh_dinv(op, op->stream, &nl);
+  op->launches += nl;
+  return s;
 }
 
 // One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
@@ -1249,3 +1273,53 @@ extern "C" hx_status hx_op_gradient(hx_op* op, const double* u, const double* la
   op->launches += 1;
   return HX_OK;
 }
+
+// ---------------------------------------------------------------------------
+// preconditioners (Sec. 5.1)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream) {
+  if (!op || !diag) return fail(HX_ERR_ARG, "NULL argument");
+  const hx_mesh* m = op->mesh;
+  cudaStream_t s = (cudaStream_t)stream;
+  HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, diag, s),
+         "collocated mass assembly");
+  op->launches += 2;
+  return HX_OK;
+}
+
+hx_status hx_op_set_preconditioner(hx_op* op, int kind, void* stream) {
+  if (!op) return fail(HX_ERR_ARG, "op is NULL");
+  if (kind != HX_PREC_JACOBI && kind != HX_PREC_COLLOCATED_MASS) return fail(HX_ERR_ARG, "unknown preconditioner");
+  if (kind == HX_PREC_COLLOCATED_MASS) {
+    if (!(op->alpha > 0.0)) return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
+    if (!op->pdiag) {
+      hx_status st = dalloc(&op->pdiag, (size_t)op->mesh->n_dof, "preconditioner diagonal");
+      if (st) return st;
+    }
+  }
+  op->prec = kind;
+  op->mixed_stale = true;  // the FP32 inverse diagonal follows at the next mixed solve
+  if (!op->dinv) return HX_OK;  // applied when the solver workspace is set up
+  int nl = 0;
+  hx_status st = refresh_dinv(op, (cudaStream_t)stream, &nl);
+  op->launches += nl;
+  return st;
+}
+
+hx_status hx_op_precond_apply(hx_op* op, const double* r, double* z, void* stream) {
+  if (!op || !r || !z) return fail(HX_ERR_ARG, "NULL argument");
+  hx_status st = ensure_solver(op);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the solver workspace is set up on the solver stream: order after it
+  HX_TRY(cudaEventRecord(op->ev, op->stream), "event record");
+  HX_TRY(cudaStreamWaitEvent(s, op->ev, 0), "stream wait");
+  HX_TRY(hx_launch_scale(op->mesh->n_dof, op->dinv, r, z, s), "preconditioner apply");
+  op->launches += 1;
+  return HX_OK;
+}
+
+}  // extern "C"

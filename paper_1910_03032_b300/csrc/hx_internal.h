@@ -134,6 +134,9 @@ struct HxCgBuffersT {
 typedef HxCgBuffersT<double> HxCgBuffers;
 typedef HxCgBuffersT<float> HxCgBuffersF;
 
+cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, double alpha, double* dE,
+                            cudaStream_t s);
+cudaError_t hx_launch_scale(long long n, const double* d, const double* r, double* z, cudaStream_t s);
 cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s);
 cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
                                   double value, double* dst, cudaStream_t s);

@@ -134,6 +134,35 @@ __global__ void __launch_bounds__(kThreads) node_kernel(const __grid_constant__ 
   }
 }
 
+// Collocated mass at the local nodes (Sec. 5.1): the mass form integrated with the
+// Gauss-Lobatto rule at the nodes of the nodal basis is diagonal,
+//   dE[e][l] = alpha w_a w_b w_c detJ_e(xi_l),   l = (a, b, c).
+__global__ void __launch_bounds__(kThreads) cmass_kernel(const __grid_constant__ HxTables T, long long E, int EB,
+                                                          const double* __restrict__ X8, double alpha,
+                                                          double* __restrict__ dE) {
+  extern __shared__ double cf[];
+  const int n = T.p + 1, N3 = n * n * n;
+  const long long e0 = (long long)blockIdx.x * EB;
+  for (int el = threadIdx.x; el < EB; el += blockDim.x) {
+    const long long e = e0 + el;
+    double x8[24];
+    for (int c = 0; c < 24; ++c) x8[c] = (e < E) ? X8[e * 24 + c] : 0.0;
+    hx::trilinear_coeffs(x8, cf + el * 24);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < EB * N3; t += blockDim.x) {
+    const int el = t / N3, l = t - el * N3;
+    const long long e = e0 + el;
+    if (e >= E) continue;
+    const int a = l % n, b = (l / n) % n, c = l / (n * n);
+    double j0[3], j1[3], j2[3];
+    hx::trilinear_jacobian(cf + el * 24, T.xn[a], T.xn[b], T.xn[c], j0, j1, j2);
+    const double det = j0[0] * (j1[1] * j2[2] - j1[2] * j2[1]) + j0[1] * (j1[2] * j2[0] - j1[0] * j2[2]) +
+                       j0[2] * (j1[0] * j2[1] - j1[1] * j2[0]);
+    dE[e * N3 + l] = alpha * T.wn[a] * T.wn[b] * T.wn[c] * det;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // E -> L assembly through the transpose map (atomic-free, fixed summation order)
 // ---------------------------------------------------------------------------
@@ -459,6 +488,26 @@ cudaError_t hx_launch_assemble(long long n, const int* off, const int* idx, cons
 cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s) {
   assemble_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, 0.0, y);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, double alpha, double* dE,
+                            cudaStream_t s) {
+  const int EB = 8;
+  const long long blocks = (E + EB - 1) / EB;
+  if (blocks == 0) return cudaSuccess;
+  cmass_kernel<<<(unsigned)blocks, kThreads, sizeof(double) * 24 * EB, s>>>(T, E, EB, X8, alpha, dE);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kThreads) scale_kernel(long long n, const double* __restrict__ d,
+                                                          const double* __restrict__ r, double* __restrict__ z) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x)
+    z[g] = d[g] * r[g];
+}
+
+cudaError_t hx_launch_scale(long long n, const double* d, const double* r, double* z, cudaStream_t s) {
+  scale_kernel<<<grid_for(n), kThreads, 0, s>>>(n, d, r, z);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ struct HxTablesT {
   T xq[HX_QMAX];    // Gauss points on [-1, 1]
   T wq[HX_QMAX];    // Gauss weights
   T xn[HX_NMAX];    // Gauss-Lobatto nodes
+  T wn[HX_NMAX];    // Gauss-Lobatto weights 2 / (p (p+1) P_p(x_j)^2) (the collocated mass, Sec. 5.1)
 };
 
 // FP64 tables (the operator path) and their FP32 rounding (the inner solver of
