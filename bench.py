@@ -49,9 +49,10 @@ HBM_GBS = 6518.0  # measured copy bandwidth of the B300s
 # FP64 peak of the B300: 2 DFMA per clock per SM (a throughput probe measured
 # 565 G DFMA/s at ~1.94 GHz: 1.97 per clock per SM) x 148 SMs x 2032 MHz x 2 flops.
 FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
-# dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch from
-# an ncu capture, keyed by (p, N, geom); None until a capture of the current kernel exists.
-NCU_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch, keyed by
+# (p, N, geom): the 32^3 capture of the current kernel (497.8 MB read + 28.4 MB written)
+# scaled by the element count (27x at 96^3); traffic grows in proportion to the elements.
+NCU_TRAFFIC = {(4, 96, "stored"): (497.797120e6 + 28.446464e6) * 27}
 
 
 def alg_flops_per_element(p: int, q: int) -> int:

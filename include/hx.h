@@ -260,10 +260,27 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
  *                            Gauss-Lobatto rule at the nodes of the nodal basis, which is
  *                            diagonal and spectrally equivalent to M independently of h and
  *                            p (Sec. 5.1): the preconditioner of mass-dominated solves
- * Dirichlet rows use z = r in both.
+ *   HX_PREC_LOR              z = P_k(D^-1 A_LOR) D^-1 r: `degree` = k steps of the Chebyshev
+ *                            iteration for A_LOR z = r with Jacobi scaling D = diag(A_LOR),
+ *                            on the interval [b / k^2, b], b the Gershgorin bound of
+ *                            D^-1 A_LOR.  A_LOR = alpha M_LOR + nu K_LOR is the low-order
+ *                            (Q1, 2 Gauss points per direction) discretization on the mesh
+ *                            that cuts every element along its Gauss-Lobatto points, assembled
+ *                            and stored as a sparse matrix (Sec. 5.2).  The paper solves
+ *                            A_LOR with multigrid and Schwarz methods; here a fixed
+ *                            polynomial keeps the preconditioner symmetric and linear for CG.
+ *                            Constant nu only.
+ *   HX_PREC_LOR_MC           as HX_PREC_LOR with A_LOR = alpha Mc + nu K_LOR: the collocated
+ *                            mass of Sec. 5.1 in place of the Q1 mass.  Not in the paper:
+ *                            the Q1 mass is a poor match of M when alpha dominates (iteration
+ *                            counts double against Jacobi at alpha = 1000, nu = 1e-2), Mc is a
+ *                            good one, and the stiffness part is unchanged.
+ * Jacobi and collocated mass use z = r in Dirichlet rows; A_LOR has identity rows there.
  */
 #define HX_PREC_JACOBI 0
 #define HX_PREC_COLLOCATED_MASS 1
+#define HX_PREC_LOR 2
+#define HX_PREC_LOR_MC 3
 
 /*
  * alpha Mc as a vector (Sec. 5.1): diag[i] = alpha sum over elements K and local nodes
@@ -275,11 +292,29 @@ HX_API hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream);
 
 /*
  * Select the preconditioner of hx_solve_pcg, hx_solve_pcg_host, hx_solve_pcg_mixed and
- * batched solves of this operator (kind: HX_PREC_*).  HX_PREC_COLLOCATED_MASS needs
- * alpha > 0 (HX_ERR_ARG otherwise, also from a later hx_op_set_coefficients with
- * alpha <= 0).  It follows later hx_op_set_coefficients calls.  Stream-ordered.
+ * batched solves of this operator (kind: HX_PREC_*; degree: Chebyshev steps of
+ * HX_PREC_LOR, 1..64, ignored otherwise).  The choice follows later
+ * hx_op_set_coefficients calls; a batch keeps the preconditioners its operators had
+ * when it was created.
+ * Errors: HX_ERR_ARG (unknown kind, degree out of range, HX_PREC_COLLOCATED_MASS with
+ * alpha <= 0, also from a later hx_op_set_coefficients with alpha <= 0);
+ * HX_ERR_UNSUPPORTED (HX_PREC_LOR on an operator with a nu field, or a LOR row with
+ * more than 64 distinct columns; mixed-precision solves reject HX_PREC_LOR).
+ * The first HX_PREC_LOR selection allocates and builds the sparsity pattern (one
+ * synchronization of `stream`); later calls are stream-ordered.
  */
-HX_API hx_status hx_op_set_preconditioner(hx_op* op, int kind, void* stream);
+HX_API hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream);
+
+/*
+ * The assembled low-order refined matrix A_LOR of the operator's alpha, nu (Sec. 5.2; the
+ * HX_PREC_LOR_MC form when that preconditioner is selected) in
+ * CSR form with the Dirichlet rows and columns eliminated (unit diagonal in Dirichlet
+ * rows), columns sorted within each row.  *nnz receives the number of stored entries;
+ * row_off (device, n_dof + 1 int64), col (device, nnz int32) and val (device, nnz
+ * doubles) receive copies when not NULL (call with NULLs first to size them).
+ * Builds the matrix when no HX_PREC_LOR was selected (errors as hx_op_set_preconditioner).
+ */
+HX_API hx_status hx_op_lor_csr(hx_op* op, int64_t* nnz, int64_t* row_off, int* col, double* val, void* stream);
 
 /*
  * z = the current preconditioner applied to r (as one PCG step applies it).

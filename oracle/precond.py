@@ -73,3 +73,59 @@ def lor_mesh(mesh: Mesh) -> Mesh:
 def lor_operator(mesh: Mesh, alpha: float, nu: float) -> Operator:
     """A_LOR = alpha M_LOR + nu K_LOR (Sec. 5.2) as the oracle operator of the refined p = 1 mesh."""
     return Operator(lor_mesh(mesh), alpha, nu)
+
+
+def lor_matrix(mesh: Mesh, alpha: float, nu: float, mass: str = "consistent", constrained: bool = True):
+    """Dense A_LOR.  mass = "consistent": alpha M_LOR + nu K_LOR (Sec. 5.2 as written);
+    mass = "collocated": alpha Mc + nu K_LOR, the LOR stiffness with the collocated
+    Gauss-Lobatto mass of Sec. 5.1 (diagonal) in place of the Q1 mass."""
+    if mass == "consistent":
+        return lor_operator(mesh, alpha, nu).assembled(constrained=constrained)
+    if mass != "collocated":
+        raise ValueError(mass)
+    A = lor_operator(mesh, 0.0, nu).assembled(constrained=False)
+    A[np.diag_indices_from(A)] += collocated_mass_diagonal(mesh, alpha)
+    if constrained:
+        d = mesh.dirichlet
+        A[d, :] = 0.0
+        A[:, d] = 0.0
+        A[d, d] = 1.0
+    return A
+
+
+def gershgorin_bound(A) -> float:
+    """max_i sum_j |a_ij| / a_ii: an upper bound of the spectrum of D^-1 A (D = diag A)."""
+    A = np.asarray(A, dtype=np.float64)
+    return float(np.max(np.abs(A).sum(axis=1) / np.diag(A)))
+
+
+def chebyshev_apply(A, r, degree: int) -> np.ndarray:
+    """z after `degree` steps of the Chebyshev iteration for A z = r with Jacobi scaling, z_0 = 0.
+
+    The iteration follows Saad, Iterative Methods for Sparse Linear Systems (2nd ed.), Sec. 12.3
+    (Algorithm 12.1) on the system D^-1 A z = D^-1 r over the interval [b / k^2, b], b the
+    Gershgorin bound of D^-1 A and k the degree:
+      theta = (b + a) / 2, delta = (b - a) / 2, sigma = theta / delta, rho_0 = 1 / sigma,
+      res_0 = D^-1 r, d_0 = res_0 / theta, z_1 = d_0, and for j = 1 .. k-1:
+      res_j = res_{j-1} - D^-1 A d_{j-1},  rho_j = 1 / (2 sigma - rho_{j-1}),
+      d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) res_j,  z_{j+1} = z_j + d_j.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    dinv = 1.0 / np.diag(A)
+    b = gershgorin_bound(A)
+    a = b / degree ** 2
+    theta, delta = (b + a) / 2, (b - a) / 2
+    res = dinv * r
+    d = res / theta
+    z = d.copy()
+    if degree < 2:
+        return z
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    for _ in range(1, degree):
+        res = res - dinv * (A @ d)
+        rn = 1.0 / (2 * sigma - rho)
+        d = rn * rho * d + (2 * rn / delta) * res
+        z = z + d
+        rho = rn
+    return z

@@ -30,6 +30,8 @@ HX_GEOM_STORED = 0
 HX_GEOM_ONTHEFLY = 1
 HX_PREC_JACOBI = 0
 HX_PREC_COLLOCATED_MASS = 1
+HX_PREC_LOR = 2
+HX_PREC_LOR_MC = 3
 
 _NAMES = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_CUDA", -3: "HX_ERR_OOM", -4: "HX_ERR_INVALID_MESH",
           -5: "HX_ERR_NOT_CONVERGED", -6: "HX_ERR_BREAKDOWN", -7: "HX_ERR_UNSUPPORTED"}
@@ -73,7 +75,8 @@ SIGNATURES = {
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
     "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
     "hx_op_collocated_mass": (_I, [_P, _P, _P]),
-    "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, _P]),
+    "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "hx_op_lor_csr": (_I, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "hx_op_precond_apply": (_I, [_P, _P, _P, _P]),
     "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, ctypes.POINTER(_P)]),
     "hx_batch_solve": (_I, [_P, _P, _P]),
@@ -322,8 +325,21 @@ def hx_op_collocated_mass(op, diag, stream=None):
     _check(_lib.hx_op_collocated_mass(op, _dptr(diag, n, "diag"), _stream(stream)))
 
 
-def hx_op_set_preconditioner(op, kind, stream=None):
-    _check(_lib.hx_op_set_preconditioner(op, int(kind), _stream(stream)))
+def hx_op_set_preconditioner(op, kind, degree=8, stream=None):
+    _check(_lib.hx_op_set_preconditioner(op, int(kind), int(degree), _stream(stream)))
+
+
+def hx_op_lor_csr(op, row_off=None, col=None, val=None, stream=None):
+    """Number of stored entries of A_LOR; copies the CSR arrays into the given device tensors."""
+    nnz = ctypes.c_int64(0)
+    _check(_lib.hx_op_lor_csr(op, ctypes.byref(nnz), None, None, None, _stream(stream)))
+    n = hx_op_info(op)[1]
+    k = nnz.value
+    if row_off is not None or col is not None or val is not None:
+        _check(_lib.hx_op_lor_csr(op, ctypes.byref(nnz), _lptr(row_off, n + 1, "row_off") if row_off is not None else None,
+                                  _iptr(col, k, "col") if col is not None else None,
+                                  _dptr(val, k, "val") if val is not None else None, _stream(stream)))
+    return k
 
 
 def hx_op_precond_apply(op, r, z, stream=None):
@@ -371,6 +387,15 @@ class Batch:
         h, self.handle = getattr(self, "handle", None), None
         if h is not None and _lib is not None:
             _lib.hx_batch_destroy(h)
+
+
+def _lptr(t, n, name):
+    """Device pointer of a contiguous int64 CUDA tensor with n elements."""
+    if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.int64" or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _iptr(t, n, name):
@@ -483,8 +508,18 @@ class Operator:
         hx_op_collocated_mass(self.handle, d, stream)
         return d
 
-    def set_preconditioner(self, kind, stream=None):
-        hx_op_set_preconditioner(self.handle, kind, stream)
+    def set_preconditioner(self, kind, degree=8, stream=None):
+        hx_op_set_preconditioner(self.handle, kind, degree, stream)
+
+    def lor_csr(self, stream=None):
+        """(row_off, col, val) of the assembled low-order refined matrix (Sec. 5.2), device tensors."""
+        import torch
+        k = hx_op_lor_csr(self.handle, stream=stream)
+        row_off = torch.empty(self.n_dof + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(k, dtype=torch.int32, device="cuda")
+        val = torch.empty(k, dtype=torch.float64, device="cuda")
+        hx_op_lor_csr(self.handle, row_off, col, val, stream)
+        return row_off, col, val
 
     def precond_apply(self, r, stream=None):
         import torch
@@ -514,4 +549,5 @@ class Operator:
 
 
 __all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
-                              "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS"]
+                              "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS",
+                              "HX_PREC_LOR", "HX_PREC_LOR_MC"]

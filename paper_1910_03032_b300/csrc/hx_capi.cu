@@ -116,6 +116,15 @@ struct hx_op {
   // preconditioner: HX_PREC_JACOBI (dinv = 1 / diag A) or HX_PREC_COLLOCATED_MASS (1 / (alpha Mc))
   int prec = HX_PREC_JACOBI;
   double* pdiag = nullptr;      // [n_dof] alpha Mc (collocated mass)
+  bool has_field = false;       // the coefficients include a per-point nu field
+  // low-order refined operator (Sec. 5.2) and its Chebyshev-Jacobi inverse (HX_PREC_LOR)
+  HxLorMatrix lor = {0, nullptr, nullptr, nullptr, nullptr};
+  long long lor_nnz = 0;
+  bool lor_values_set = false;        // values of the current alpha, nu assembled
+  int lor_collocated = 0;             // 1: alpha Mc + nu K_LOR (HX_PREC_LOR_MC)
+  unsigned long long* lor_bound = nullptr;
+  HxChebWork cheb = {0, nullptr, nullptr, nullptr, nullptr};
+  double* zl = nullptr;               // [n_dof] preconditioned residual
 };
 
 namespace {
@@ -379,6 +388,16 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->m1);
   dfree(op->vol);
   dfree(op->pdiag);
+  dfree(op->lor.off);
+  dfree(op->lor.col);
+  dfree(op->lor.val);
+  dfree(op->lor.dinv);
+  dfree(op->lor_bound);
+  dfree(op->cheb.res);
+  dfree(op->cheb.d0);
+  dfree(op->cheb.d1);
+  dfree(op->cheb.coef);
+  dfree(op->zl);
   delete op;
 }
 
@@ -404,6 +423,95 @@ hx_status refresh_dinv(hx_op* op, cudaStream_t s, int* nl) {
   return HX_OK;
 }
 
+HxLorBuild lor_build_args(const hx_op* op) {
+  const hx_mesh* m = op->mesh;
+  HxLorBuild b;
+  b.p = m->p;
+  b.n = m->n_dof;
+  b.toff = m->off;
+  b.tidx = m->idx;
+  b.R = m->R;
+  b.dir = m->dir;
+  return b;
+}
+
+// Values of A_LOR for the current alpha, nu (the pattern exists), its inverse diagonal, the
+// Gershgorin bound of D^-1 A_LOR and the Chebyshev coefficients.  Stream-ordered.
+hx_status lor_assemble(hx_op* op, cudaStream_t s, int* nl) {
+  if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
+  if (!op->lor.val) return HX_OK;  // pattern not built yet: assembled when the preconditioner is selected
+  const hx_mesh* m = op->mesh;
+  HX_TRY(hx_lor_values(m->T, lor_build_args(op), m->X8, op->alpha, op->nu, op->lor_collocated, op->lor, op->lor_bound,
+                       s),
+         "LOR values");
+  HX_TRY(hx_lor_coefficients(op->lor_bound, op->cheb.degree, op->cheb.coef, s), "Chebyshev coefficients");
+  *nl += 3;
+  op->lor_values_set = true;
+  return HX_OK;
+}
+
+// The LOR pattern (CSR, built once per operator) and the Chebyshev workspace for `degree`
+// steps.  Synchronizes `s` once to size the column array.
+hx_status lor_setup(hx_op* op, int degree, cudaStream_t s) {
+  const hx_mesh* m = op->mesh;
+  const long long n = m->n_dof;
+  hx_status st = HX_OK;
+  if (!op->lor.val) {
+    long long* count = nullptr;
+    long long* sums = nullptr;
+    int* bad = nullptr;
+    int nbad = 0;
+    long long nnz = 0;
+    do {
+      if ((st = dalloc(&count, (size_t)n, "LOR counts")) || (st = dalloc(&sums, (size_t)hx_lor_scan_blocks(n) + 1, "scan")) ||
+          (st = dalloc(&bad, 1, "flag")) || (st = dalloc(&op->lor.off, (size_t)n + 1, "LOR offsets")) ||
+          (st = dalloc(&op->lor.dinv, (size_t)n, "LOR inverse diagonal")) ||
+          (st = dalloc(&op->lor_bound, 1, "LOR bound")))
+        break;
+      cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+      const HxLorBuild b = lor_build_args(op);
+      if (e == cudaSuccess) e = hx_lor_count(b, count, bad, s);
+      if (e == cudaSuccess) e = hx_lor_scan(n, count, sums, op->lor.off, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&nnz, op->lor.off + n, sizeof(long long), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "LOR pattern");
+        break;
+      }
+      if (nbad > 0) {
+        st = fail(HX_ERR_UNSUPPORTED, "%d LOR rows have more than %d columns", nbad, HX_LOR_MAX_NB);
+        break;
+      }
+      if ((st = dalloc(&op->lor.col, (size_t)nnz, "LOR columns")) || (st = dalloc(&op->lor.val, (size_t)nnz, "LOR values")))
+        break;
+      e = hx_lor_fill(b, op->lor.off, op->lor.col, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "LOR pattern fill");
+      op->launches += 6;
+    } while (0);
+    dfree(count);
+    dfree(sums);
+    dfree(bad);
+    if (st) {
+      dfree(op->lor.col);
+      dfree(op->lor.val);
+      op->lor.col = nullptr;
+      op->lor.val = nullptr;
+      return st;
+    }
+    op->lor.n = n;
+    op->lor_nnz = nnz;
+  }
+  if (!op->zl) {
+    if ((st = dalloc(&op->zl, (size_t)n, "preconditioned residual")) || (st = dalloc(&op->cheb.res, (size_t)n, "cheb res")) ||
+        (st = dalloc(&op->cheb.d0, (size_t)n, "cheb d0")) || (st = dalloc(&op->cheb.d1, (size_t)n, "cheb d1")) ||
+        (st = dalloc(&op->cheb.coef, 2 * HX_LOR_MAX_DEGREE, "cheb coefficients")))
+      return st;
+  }
+  op->cheb.degree = degree;
+  return HX_OK;
+}
+
 // Coefficient-dependent setup, stream-ordered and allocation-free: stored
 // factors (alpha, nu) and the assembled diagonal (and its inverse once the
 // solver workspace exists).  `bad` (nullable) counts detJ <= 0 points.
@@ -415,6 +523,8 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
   cudaError_t e;
   op->alpha = alpha;
   op->nu = nu;
+  op->has_field = nu_q != nullptr;
+  op->lor_values_set = false;
   // alpha = 0 with nothing fixed on the boundary: K alone, singular on the constants
   op->singular = (alpha == 0.0 && m->n_dirichlet == 0);
   if (op->geom == HX_GEOM_STORED) {
@@ -442,6 +552,11 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
   if (launches) *launches = nl;
   if (op->dinv) {
     hx_status st = refresh_dinv(op, s, &nl);
+    if (launches) *launches = nl;
+    if (st) return st;
+  }
+  if (op->prec == HX_PREC_LOR) {
+    hx_status st = lor_assemble(op, s, &nl);
     if (launches) *launches = nl;
     if (st) return st;
   }
@@ -523,6 +638,8 @@ hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const doubl
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
   if (op->geom == HX_GEOM_ONTHEFLY && nu_q && !op->nu_q)
     return fail(HX_ERR_ARG, "on-the-fly operator created without a nu field cannot take one");
+  if (op->prec == HX_PREC_LOR && nu_q)
+    return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
   int nl = 0;
   hx_status st = setup_coefficients(op, alpha, nu, nu_q, nullptr, (cudaStream_t)stream, &nl);
   if (st == HX_OK) op->launches += nl;
@@ -604,6 +721,7 @@ HxCgBuffers cg_buffers(const hx_op* op) {
   b.yE = op->yE;
   b.partial = op->partial;
   b.st = op->st;
+  b.z = (op->prec == HX_PREC_LOR) ? op->zl : nullptr;
   b.cond = 0ull;
   b.nullspace = op->singular ? 1 : 0;
   return b;
@@ -638,8 +756,21 @@ cudaError_t cg_iteration(const hx_op* op, cudaStream_t s, unsigned long long con
   cudaError_t e = element_apply(op, op->p, 1, &op->st->done, s);
   if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
   if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
+  if (e == cudaSuccess && b.z) {
+    e = hx_lor_precondition(op->lor, op->cheb, op->r, op->zl, &op->st->done, s);
+    if (e == cudaSuccess) e = hx_launch_cg_rz(b, s);
+  }
   if (e == cudaSuccess) e = hx_launch_cg_direction(b, s);
   return e;
+}
+
+// kernels one CG iteration launches
+int iteration_launches(const hx_op* op) { return op->prec == HX_PREC_LOR ? 4 + op->cheb.degree + 1 : 4; }
+
+// z = M^-1 r before the first direction (LOR preconditioner only; Jacobi is fused into cg_start)
+cudaError_t precondition_start(const hx_op* op, cudaStream_t s) {
+  if (op->prec != HX_PREC_LOR) return cudaSuccess;
+  return hx_lor_precondition(op->lor, op->cheb, op->r, op->zl, &op->st->done, s);
 }
 
 constexpr int kChunk = 16;  // CG iterations per launch of the fallback (non-conditional) path
@@ -713,8 +844,9 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
     HX_TRY(hx_launch_cg_residual(buf, st), "cg residual");
     op->launches += 3;
   }
+  HX_TRY(precondition_start(op, st), "first preconditioner");
   HX_TRY(hx_launch_cg_start(buf, st), "cg start");
-  op->launches += 2;
+  op->launches += 2 + (op->prec == HX_PREC_LOR ? op->cheb.degree : 0);
   if (op->singular) {
     HX_TRY(hx_launch_cg_direction(buf, st), "cg first direction");  // p = z - mean z
     op->launches += 1;
@@ -724,7 +856,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
     HX_TRY(cudaGraphLaunch(op->graph, st), "graph launch");
     HX_TRY(cudaMemcpyAsync(op->st_host, op->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
     HX_TRY(cudaStreamSynchronize(st), "solver sync");
-    op->launches += 4 * (long long)op->st_host->loops;
+    op->launches += iteration_launches(op) * (long long)op->st_host->loops;
     if (!op->st_host->done) return fail(HX_ERR_CUDA, "CG graph loop ended before the solver finished");
   } else {
     for (;;) {
@@ -732,7 +864,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
       HX_TRY(cudaStreamSynchronize(st), "solver sync");
       if (op->st_host->done) break;
       for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration(op, st), "cg iteration");
-      op->launches += 4 * kChunk;
+      op->launches += iteration_launches(op) * kChunk;
     }
   }
   const HxCgState cs = *op->st_host;
@@ -853,6 +985,7 @@ HxCgBuffersF cg_buffers32(const hx_op* op) {
   b.yE = op->yE32;
   b.partial = op->partial;
   b.st = op->st32;
+  b.z = nullptr;
   b.cond = 0ull;
   b.nullspace = op->singular ? 1 : 0;
   return b;
@@ -923,6 +1056,8 @@ hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_
 hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
                       cudaStream_t user, hx_solve_info* info) {
   const hx_mesh* m = op->mesh;
+  if (op->prec == HX_PREC_LOR)
+    return fail(HX_ERR_UNSUPPORTED, "mixed-precision solves take the Jacobi or collocated mass preconditioner");
   hx_status s = ensure_solver(op);
   if (s) return s;
   cudaStream_t st = op->stream;
@@ -1111,6 +1246,7 @@ hx_status build_batch_graph(hx_batch* B, double rtol, int max_it) {
       cudaError_t e = cudaSuccess;
       if (op->singular) e = hx_launch_cg_mean(buf, bi, cs);
       if (e == cudaSuccess) e = hx_launch_cg_init(buf, bi, (const double*)nullptr, rtol, max_it, cs);
+      if (e == cudaSuccess) e = precondition_start(op, cs);
       if (e == cudaSuccess) e = hx_launch_cg_start(buf, cs);
       if (e == cudaSuccess && op->singular) e = hx_launch_cg_direction(buf, cs);
       return e;
@@ -1290,21 +1426,38 @@ hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream) {
   return HX_OK;
 }
 
-hx_status hx_op_set_preconditioner(hx_op* op, int kind, void* stream) {
+hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream) {
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
-  if (kind != HX_PREC_JACOBI && kind != HX_PREC_COLLOCATED_MASS) return fail(HX_ERR_ARG, "unknown preconditioner");
+  if (kind != HX_PREC_JACOBI && kind != HX_PREC_COLLOCATED_MASS && kind != HX_PREC_LOR && kind != HX_PREC_LOR_MC)
+    return fail(HX_ERR_ARG, "unknown preconditioner");
+  const bool lor = kind == HX_PREC_LOR || kind == HX_PREC_LOR_MC;
+  cudaStream_t s = (cudaStream_t)stream;
+  hx_status st = HX_OK;
   if (kind == HX_PREC_COLLOCATED_MASS) {
     if (!(op->alpha > 0.0)) return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
-    if (!op->pdiag) {
-      hx_status st = dalloc(&op->pdiag, (size_t)op->mesh->n_dof, "preconditioner diagonal");
-      if (st) return st;
-    }
+    if (!op->pdiag && (st = dalloc(&op->pdiag, (size_t)op->mesh->n_dof, "preconditioner diagonal"))) return st;
   }
-  op->prec = kind;
+  if (lor) {
+    if (degree < 1 || degree > HX_LOR_MAX_DEGREE) return fail(HX_ERR_ARG, "degree must be in [1, %d]", HX_LOR_MAX_DEGREE);
+    if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
+    if ((st = lor_setup(op, degree, s))) return st;
+  }
+  // the captured CG iterations differ between the preconditioners: capture again at the next solve
+  if (op->graph) {
+    cudaGraphExecDestroy(op->graph);
+    op->graph = nullptr;
+  }
+  op->graph_failed = false;
+  op->prec = lor ? HX_PREC_LOR : kind;  // one solver path for both LOR forms
   op->mixed_stale = true;  // the FP32 inverse diagonal follows at the next mixed solve
-  if (!op->dinv) return HX_OK;  // applied when the solver workspace is set up
   int nl = 0;
-  hx_status st = refresh_dinv(op, (cudaStream_t)stream, &nl);
+  if (lor) {
+    op->cheb.degree = degree;
+    op->lor_collocated = kind == HX_PREC_LOR_MC ? 1 : 0;
+    st = lor_assemble(op, s, &nl);
+  } else if (op->dinv) {
+    st = refresh_dinv(op, s, &nl);
+  }
   op->launches += nl;
   return st;
 }
@@ -1317,8 +1470,38 @@ hx_status hx_op_precond_apply(hx_op* op, const double* r, double* z, void* strea
   // the solver workspace is set up on the solver stream: order after it
   HX_TRY(cudaEventRecord(op->ev, op->stream), "event record");
   HX_TRY(cudaStreamWaitEvent(s, op->ev, 0), "stream wait");
-  HX_TRY(hx_launch_scale(op->mesh->n_dof, op->dinv, r, z, s), "preconditioner apply");
-  op->launches += 1;
+  if (op->prec == HX_PREC_LOR) {
+    HX_TRY(hx_lor_precondition(op->lor, op->cheb, r, z, nullptr, s), "LOR preconditioner");
+    op->launches += op->cheb.degree;
+  } else {
+    HX_TRY(hx_launch_scale(op->mesh->n_dof, op->dinv, r, z, s), "preconditioner apply");
+    op->launches += 1;
+  }
+  return HX_OK;
+}
+
+hx_status hx_op_lor_csr(hx_op* op, int64_t* nnz, int64_t* row_off, int* col, double* val, void* stream) {
+  if (!op || !nnz) return fail(HX_ERR_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  hx_status st = HX_OK;
+  if (!op->lor.val) {
+    if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR operator takes a constant nu only");
+    if ((st = lor_setup(op, op->cheb.degree > 0 ? op->cheb.degree : 1, s))) return st;
+  }
+  if (!op->lor_values_set) {
+    if (op->cheb.degree == 0) op->cheb.degree = 1;
+    int nl = 0;
+    st = lor_assemble(op, s, &nl);
+    op->launches += nl;
+    if (st) return st;
+  }
+  *nnz = op->lor_nnz;
+  const long long n = op->mesh->n_dof;
+  if (row_off)
+    HX_TRY(cudaMemcpyAsync(row_off, op->lor.off, sizeof(long long) * (n + 1), cudaMemcpyDeviceToDevice, s), "copy");
+  if (col) HX_TRY(cudaMemcpyAsync(col, op->lor.col, sizeof(int) * op->lor_nnz, cudaMemcpyDeviceToDevice, s), "copy");
+  if (val)
+    HX_TRY(cudaMemcpyAsync(val, op->lor.val, sizeof(double) * op->lor_nnz, cudaMemcpyDeviceToDevice, s), "copy");
   return HX_OK;
 }
 

@@ -128,6 +128,7 @@ struct HxCgBuffersT {
   Real* yE;
   double* partial;  // [HX_RED_VALUES * HX_RED_BLOCKS]
   HxCgState* st;
+  const Real* z;            // preconditioned residual computed outside the CG kernels, or NULL (Jacobi: dinv r)
   unsigned long long cond;  // CUDA graph conditional handle of the enclosing while loop, or 0
   int nullspace;            // 1: singular operator with the constants as null space (pure Neumann Poisson)
 };
@@ -153,6 +154,45 @@ template <typename Real>
 cudaError_t hx_launch_cg_update(const HxCgBuffersT<Real>& b, cudaStream_t s);
 template <typename Real>
 cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s);
+template <typename Real>
+cudaError_t hx_launch_cg_rz(const HxCgBuffersT<Real>& b, cudaStream_t s);
+
+// ---- low-order refined operator (Sec. 5.2) and its Chebyshev-Jacobi inverse ----
+#define HX_LOR_MAX_NB 64  // distinct columns per LOR row at most (27 on structured meshes)
+#define HX_LOR_MAX_DEGREE 64
+struct HxLorBuild {
+  int p;
+  long long n;
+  const int* toff;  // transpose map of the restriction
+  const int* tidx;
+  const int* R;
+  const unsigned char* dir;
+};
+struct HxLorMatrix {
+  long long n;
+  long long* off;  // [n + 1]
+  int* col;        // [nnz], sorted per row
+  double* val;     // [nnz], Dirichlet rows and columns eliminated (identity rows)
+  double* dinv;    // [n]
+};
+struct HxChebWork {
+  int degree;      // Chebyshev steps (1: plain LOR-Jacobi)
+  double* res;     // [n]
+  double* d0;      // [n]
+  double* d1;      // [n]
+  double* coef;    // [2 degree]
+};
+cudaError_t hx_lor_count(const HxLorBuild& b, long long* count, int* bad, cudaStream_t s);
+long long hx_lor_scan_blocks(long long n);
+cudaError_t hx_lor_scan(long long n, const long long* count, long long* sums, long long* off, cudaStream_t s);
+cudaError_t hx_lor_fill(const HxLorBuild& b, const long long* off, int* col, cudaStream_t s);
+// collocated = 0: alpha M_LOR + nu K_LOR; 1: alpha Mc + nu K_LOR (collocated Gauss-Lobatto mass)
+cudaError_t hx_lor_values(const HxTables& T, const HxLorBuild& b, const double* X8, double alpha, double nu,
+                          int collocated, const HxLorMatrix& A, unsigned long long* bound, cudaStream_t s);
+cudaError_t hx_lor_coefficients(const unsigned long long* bound, int degree, double* coef, cudaStream_t s);
+cudaError_t hx_lor_precondition(const HxLorMatrix& A, const HxChebWork& w, const double* r, double* z,
+                                const int* done, cudaStream_t s);
+cudaError_t hx_lor_spmv(const HxLorMatrix& A, const double* x, double* y, cudaStream_t s);
 // mixed-precision refinement helpers
 cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s);

@@ -249,7 +249,7 @@ template <typename Real>
 __global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffersT<Real> B) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   HX_GRID_STRIDE(g, B.n) {
-    const Real r = B.r[g], z = B.dinv[g] * r;
+    const Real r = B.r[g], z = B.z ? B.z[g] : B.dinv[g] * r;
     B.p[g] = z;
     acc[0] += (double)r * (double)z;
     acc[1] += (double)r * (double)r;
@@ -320,11 +320,13 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<
     B.x[g] += a * pg;
     const Real r = B.r[g] - a * B.Ap[g];
     B.r[g] = r;
-    const Real z = B.dinv[g] * r;
     acc[0] += (double)r * (double)r;
-    acc[1] += (double)r * (double)z;
-    acc[2] += (double)z;
-    acc[3] += (double)r;
+    if (!B.z) {
+      const Real z = B.dinv[g] * r;
+      acc[1] += (double)r * (double)z;
+      acc[2] += (double)z;
+      acc[3] += (double)r;
+    }
   }
   double out[4];
   if (last_block_reduce<4>(acc, B.partial, &B.st->count[3], out) && threadIdx.x == 0) {
@@ -343,6 +345,36 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<
       s->done = 1;
     } else if (s->iter >= s->max_it) {
       s->status = -5;  // HX_ERR_NOT_CONVERGED
+      s->done = 1;
+    } else if (!B.z) {
+      s->beta = rz / s->rz;
+      s->rz = rz;
+    }
+  }
+}
+
+// Preconditioner given as a vector z = M^-1 r (computed between the update and the direction
+// passes): rz' = (r, z) (null-space mode: (r, z - mean z)), beta = rz' / rz.
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_rz_kernel(HxCgBuffersT<Real> B) {
+  if (*(volatile int*)&B.st->done) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  HX_GRID_STRIDE(g, B.n) {
+    const Real r = B.r[g], z = B.z[g];
+    acc[0] += (double)r * (double)z;
+    acc[1] += (double)z;
+    acc[2] += (double)r;
+  }
+  double out[3];
+  if (last_block_reduce<3>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
+    HxCgState* s = B.st;
+    double rz = out[0];
+    if (B.nullspace) {
+      s->zmean = out[1] / (double)B.n;
+      rz -= s->zmean * out[2];
+    }
+    if (!isfinite(rz)) {
+      s->status = -6;
       s->done = 1;
     } else {
       s->beta = rz / s->rz;
@@ -364,7 +396,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffer
   }
   if (*(volatile int*)&B.st->done) return;
   const Real beta = Real(B.st->beta), zm = Real(B.st->zmean);
-  HX_GRID_STRIDE(g, B.n) { B.p[g] = (B.dinv[g] * B.r[g] - zm) + beta * B.p[g]; }
+  HX_GRID_STRIDE(g, B.n) { B.p[g] = ((B.z ? B.z[g] : B.dinv[g] * B.r[g]) - zm) + beta * B.p[g]; }
 }
 
 // ---------------------------------------------------------------------------
@@ -549,6 +581,11 @@ cudaError_t hx_launch_cg_update(const HxCgBuffersT<Real>& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 template <typename Real>
+cudaError_t hx_launch_cg_rz(const HxCgBuffersT<Real>& b, cudaStream_t s) {
+  cg_rz_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  return cudaGetLastError();
+}
+template <typename Real>
 cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s) {
   cg_direction_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
@@ -574,6 +611,7 @@ cudaError_t hx_launch_shift(long long n, double* x, const double* num, const dou
   template cudaError_t hx_launch_cg_assemble_pap<R>(const HxCgBuffersT<R>&, cudaStream_t);             \
   template cudaError_t hx_launch_cg_update<R>(const HxCgBuffersT<R>&, cudaStream_t);                   \
   template cudaError_t hx_launch_cg_direction<R>(const HxCgBuffersT<R>&, cudaStream_t);                \
+  template cudaError_t hx_launch_cg_rz<R>(const HxCgBuffersT<R>&, cudaStream_t);                       \
   template cudaError_t hx_launch_cg_mean<R>(const HxCgBuffersT<R>&, const R*, cudaStream_t);
 HX_CG_INSTANTIATE(double)
 HX_CG_INSTANTIATE(float)

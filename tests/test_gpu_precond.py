@@ -105,3 +105,157 @@ def test_collocated_mass_needs_positive_alpha(hx):
     op.solve(to_dev(S.uniform_pm1(3, om.n_dof)))
     with pytest.raises(hx.HxError):
         op.set_coefficients(0.0, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# low-order refined preconditioner (Sec. 5.2)
+# ---------------------------------------------------------------------------
+def _dense(row_off, col, val, n):
+    ro, c, v = row_off.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
+    A = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(ro))
+    A[rows, c] = v
+    for g in range(n):
+        assert np.all(np.diff(c[ro[g]:ro[g + 1]]) > 0)    # sorted, distinct
+    return A
+
+
+@pytest.mark.parametrize("p,dirichlet", [(1, True), (2, True), (3, True), (3, False), (5, True), (8, True)])
+def test_lor_matrix_matches_oracle(hx, p, dirichlet):
+    from oracle import precond
+    shape = (3, 2, 2) if p <= 3 else (2, 2, 1)
+    V, EV, om = case(shape, p, perturb=0.15, seed=400 + p, dirichlet=dirichlet)
+    mesh = hx.Mesh.box(*shape, p, p + 2, V, dirichlet_faces=63 if dirichlet else 0)
+    op = hx.Operator(mesh, 2.5, 0.7)
+    A = _dense(*op.lor_csr(), om.n_dof)
+    Ao = precond.lor_operator(om, 2.5, 0.7).assembled(constrained=True)
+    assert np.abs(A - Ao).max() <= 1e-13 * np.abs(Ao).max()
+    # pattern: exactly the structural non-zeros of the oracle matrix (27 per interior row)
+    assert np.array_equal(A != 0, Ao != 0) or np.all(np.abs(Ao[(A != 0) != (Ao != 0)]) <= 1e-14 * np.abs(Ao).max())
+
+
+def test_lor_matrix_follows_coefficients(hx):
+    from oracle import precond
+    p, shape = 3, (2, 2, 2)
+    V, EV, om = case(shape, p)
+    mesh = hx.Mesh.structured(*shape, p, p + 2, V)
+    op = hx.Operator(mesh, 1.0, 1.0)
+    op.set_preconditioner(hx.HX_PREC_LOR, 4)
+    op.set_coefficients(30.0, 0.2)
+    A = _dense(*op.lor_csr(), om.n_dof)
+    Ao = precond.lor_operator(om, 30.0, 0.2).assembled(constrained=True)
+    assert np.abs(A - Ao).max() <= 1e-13 * np.abs(Ao).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_lor_precond_apply_matches_oracle(hx, k):
+    from oracle import precond
+    p, shape = 4, (3, 2, 2)
+    V, EV, om = case(shape, p)
+    mesh = hx.Mesh.structured(*shape, p, p + 2, V)
+    op = hx.Operator(mesh, 10.0, 0.5)
+    op.set_preconditioner(hx.HX_PREC_LOR, k)
+    r = np.where(om.dirichlet, 0.0, S.uniform_pm1(31, om.n_dof))
+    z = op.precond_apply(to_dev(r)).cpu().numpy()
+    zo = precond.chebyshev_apply(precond.lor_operator(om, 10.0, 0.5).assembled(constrained=True), r, k)
+    assert rel_err(z, zo) <= 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_lor_mc_matrix_matches_oracle(hx, p):
+    from oracle import precond
+    shape = (3, 2, 2)
+    V, EV, om = case(shape, p, perturb=0.15, seed=450 + p)
+    mesh = hx.Mesh.structured(*shape, p, p + 2, V)
+    op = hx.Operator(mesh, 40.0, 0.3)
+    op.set_preconditioner(hx.HX_PREC_LOR_MC, 3)
+    A = _dense(*op.lor_csr(), om.n_dof)
+    Ao = precond.lor_matrix(om, 40.0, 0.3, "collocated")
+    assert np.abs(A - Ao).max() <= 1e-13 * np.abs(Ao).max()
+    r = np.where(om.dirichlet, 0.0, S.uniform_pm1(33, om.n_dof))
+    assert rel_err(op.precond_apply(to_dev(r)).cpu().numpy(), precond.chebyshev_apply(Ao, r, 3)) <= 1e-12
+
+
+@pytest.mark.parametrize("kind,alpha", [("LOR", 0.0), ("LOR_MC", 0.0), ("LOR_MC", 1000.0), ("LOR", 1000.0)])
+def test_lor_pcg_matches_oracle(hx, kind, alpha):
+    """Iterations: the LOR forms need well under half of Jacobi's on Poisson; with alpha = 1000 the
+    collocated-mass form stays at Jacobi's count, while the Q1-mass form needs more (its mass
+    is a poor match of M), which is why HX_PREC_LOR_MC exists."""
+    from oracle import fem
+    from oracle.solve import jacobi_pcg
+    p, shape = 4, (4, 4, 4)
+    V, EV, om = case(shape, p)
+    mesh = hx.Mesh.structured(*shape, p, p + 2, V)
+    nu = 1.0 if alpha == 0.0 else 1e-2
+    op = hx.Operator(mesh, alpha, nu)
+    b = S.random_vector(om.n_dof, 37)
+    x_j, info_j = op.solve(to_dev(b), rtol=1e-10)
+    op.set_preconditioner(getattr(hx, "HX_PREC_" + kind), 8)
+    x_l, info_l = op.solve(to_dev(b), rtol=1e-10)
+    assert info_l["status"] == 0 and info_l["true_rel_residual"] <= 1.01e-10
+    xo, _, _, _ = jacobi_pcg(fem.Operator(om, alpha, nu), b, 1e-12)
+    assert rel_err(x_l.cpu().numpy(), xo) <= 1e-8
+    if alpha == 0.0:
+        assert 2 * info_l["iterations"] < info_j["iterations"]
+    elif kind == "LOR_MC":
+        assert info_l["iterations"] <= info_j["iterations"] + 3
+
+
+def test_lor_neumann_poisson(hx):
+    from oracle import fem
+    from oracle.solve import jacobi_pcg_nullspace
+    p, shape = 3, (3, 3, 3)
+    V, EV, om = case(shape, p, dirichlet=False)
+    mesh = hx.Mesh.box(*shape, p, p + 2, V, dirichlet_faces=0)
+    op = hx.Operator(mesh, 0.0, 1.0)
+    op.set_preconditioner(hx.HX_PREC_LOR, 6)
+    b = S.random_vector(om.n_dof, 41)
+    x, info = op.solve(to_dev(b), rtol=1e-10)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    xo, _, _, _ = jacobi_pcg_nullspace(fem.Operator(om, 0.0, 1.0), b, 1e-12)
+    assert rel_err(x.cpu().numpy(), xo) <= 1e-8
+    m1 = fem.Operator(om, 1.0, 0.0).apply(np.ones(om.n_dof))
+    xs = x.cpu().numpy()
+    assert abs(m1 @ xs) <= 1e-12 * np.abs(xs).max()
+
+
+def test_lor_in_a_batch(hx):
+    ops, bs, xs, refs = [], [], [], []
+    for k, (N, p, prec) in enumerate([(4, 3, hx.HX_PREC_LOR), (3, 5, hx.HX_PREC_JACOBI), (5, 2, hx.HX_PREC_LOR)]):
+        V = S.structured_vertices(N, N, N, 0.1, 500 + k)
+        mesh = hx.Mesh.structured(N, N, N, p, p + 2, V)
+        op = hx.Operator(mesh, 0.0, 1.0)
+        op.set_preconditioner(prec, 6)
+        b = to_dev(S.uniform_pm1(600 + k, mesh.n_dof))
+        refs.append(op.solve(b, rtol=1e-10))
+        ops.append(op)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    batch = hx.Batch(ops, bs, xs, rtol=1e-10)
+    infos = batch.solve()
+    for (xr, ir), x, i in zip(refs, xs, infos):
+        assert i["status"] == 0 and i["iterations"] == ir["iterations"]
+        assert torch.equal(x, xr)
+
+
+def test_lor_errors(hx):
+    p, shape = 2, (2, 2, 2)
+    V, EV, om = case(shape, p)
+    mesh = hx.Mesh.structured(*shape, p, p + 2, V)
+    E, Q = om.n_elem, (p + 2) ** 3
+    op = hx.Operator(mesh, 1.0, 0.0, to_dev(np.full((E, Q), 0.3)))
+    with pytest.raises(hx.HxError) as ei:
+        op.set_preconditioner(hx.HX_PREC_LOR, 4)
+    assert ei.value.status == -7
+    op2 = hx.Operator(mesh, 1.0, 1.0)
+    for bad in (0, 65):
+        with pytest.raises(hx.HxError) as ei:
+            op2.set_preconditioner(hx.HX_PREC_LOR, bad)
+        assert ei.value.status == -1
+    op2.set_preconditioner(hx.HX_PREC_LOR, 4)
+    with pytest.raises(hx.HxError) as ei:
+        op2.solve_mixed(to_dev(S.uniform_pm1(3, om.n_dof)))
+    assert ei.value.status == -7
+    with pytest.raises(hx.HxError) as ei:
+        op2.set_coefficients(1.0, 1.0, to_dev(np.full((E, Q), 0.3)))
+    assert ei.value.status == -7

@@ -124,3 +124,51 @@ def test_lor_condition_bounded_in_p():
         kj.append(ej.max() / ej.min())
     assert max(kl) <= 12.0
     assert kj[-1] > 5 * kl[-1] and kj[-1] > 2 * kj[0]
+
+
+def _cheb_T(k, x):
+    x = np.asarray(x, dtype=float)
+    out = np.empty_like(x)
+    inside = np.abs(x) <= 1
+    out[inside] = np.cos(k * np.arccos(x[inside]))
+    xo = x[~inside]
+    out[~inside] = np.sign(xo) ** k * np.cosh(k * np.arccosh(np.abs(xo)))
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 8])
+def test_chebyshev_is_the_residual_polynomial(k):
+    """After k steps from z = 0 the error is R_k(D^-1 A) times the initial error, with
+    R_k(l) = T_k((theta - l) / delta) / T_k(theta / delta) on [a, b] = [b / k^2, b]; so
+    z = D^-1/2 f(S) D^-1/2 r, f(l) = (1 - R_k(l)) / l, S = D^-1/2 A D^-1/2 (eigendecomposition)."""
+    shape, p = (2, 2, 2), 3
+    V = S.structured_vertices(*shape, 0.1, 11)
+    mesh = fem.StructuredMesh(*shape, p, p + 2, V, S.structured_elem_vert(*shape))
+    A = precond.lor_operator(mesh, 2.0, 1.0).assembled(constrained=True)
+    r = S.uniform_pm1(12, mesh.n_dof)
+    z = precond.chebyshev_apply(A, r, k)
+    d = np.diag(A)
+    Sm = A / np.sqrt(np.outer(d, d))
+    lam, Vv = np.linalg.eigh(Sm)
+    b = precond.gershgorin_bound(A)
+    assert lam.max() <= b * (1 + 1e-12)          # the Gershgorin bound is an upper bound
+    a = b / k ** 2
+    theta, delta = (b + a) / 2, (b - a) / 2
+    if k == 1:
+        f = np.full_like(lam, 1.0 / theta)
+    else:
+        R = _cheb_T(k, (theta - lam) / delta) / _cheb_T(k, np.array([theta / delta]))[0]
+        f = (1 - R) / lam
+    z_ref = (Vv @ (f * (Vv.T @ (r / np.sqrt(d))))) / np.sqrt(d)
+    assert np.abs(z - z_ref).max() <= 1e-11 * np.abs(z_ref).max()
+
+
+def test_lor_collocated_mass_variant_is_the_sum_of_its_parts():
+    shape, p = (2, 2, 1), 3
+    V = S.structured_vertices(*shape, 0.1, 13)
+    mesh = fem.StructuredMesh(*shape, p, p + 2, V, S.structured_elem_vert(*shape))
+    A = precond.lor_matrix(mesh, 4.0, 0.3, "collocated")
+    K = precond.lor_operator(mesh, 0.0, 0.3).assembled(constrained=True)
+    d = np.where(mesh.dirichlet, 0.0, precond.collocated_mass_diagonal(mesh, 4.0))
+    assert np.abs(A - K - np.diag(d)).max() <= 1e-15 * np.abs(A).max()
+    assert np.array_equal(precond.lor_matrix(mesh, 4.0, 0.3), precond.lor_operator(mesh, 4.0, 0.3).assembled(True))
