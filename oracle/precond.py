@@ -20,6 +20,7 @@ the Q1 mass exactly on affine sub-elements.
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 from .basis import gll_nodes, legendre
 from .fem import Mesh, Operator, trilinear_map
@@ -129,3 +130,103 @@ def chebyshev_apply(A, r, degree: int) -> np.ndarray:
         z = z + d
         rho = rn
     return z
+
+
+# --------------------------------------------------------------------------
+# geometric multigrid V-cycle on the LOR matrix of a structured mesh (the paper solves
+# A_LOR with a structured geometric multigrid V-cycle, Sec. 5.2; here the smoother is a
+# Chebyshev-Jacobi polynomial instead of ordered ILU, and the coarse operators are Galerkin
+# products of the logical-grid trilinear interpolation)
+# --------------------------------------------------------------------------
+MG_SMOOTH_DEGREE = 3      # Chebyshev steps of each pre- and post-smoothing
+MG_SMOOTH_RATIO = 10.0    # smoothing interval [b / 10, b]
+MG_COARSE_DEGREE = 16     # Chebyshev steps on the coarsest grid, interval [b / 16^2, b]
+MG_MIN_DIM = 5            # a grid is coarsened while every dimension is odd and >= 5
+MG_MAX_LEVELS = 16
+
+
+def chebyshev_ratio_apply(A, r, degree: int, ratio: float) -> np.ndarray:
+    """`degree` Chebyshev-Jacobi steps for A z = r from z = 0 on [b / ratio, b] (b the Gershgorin
+    bound); the recurrence of ``chebyshev_apply``."""
+    A = np.asarray(A, dtype=np.float64)
+    dinv = 1.0 / np.diag(A)
+    b = gershgorin_bound(A)
+    a = b / ratio
+    theta, delta = (b + a) / 2, (b - a) / 2
+    res = dinv * r
+    d = res / theta
+    z = d.copy()
+    if degree < 2:
+        return z
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    for _ in range(1, degree):
+        res = res - dinv * (A @ d)
+        rn = 1.0 / (2 * sigma - rho)
+        d = rn * rho * d + (2 * rn / delta) * res
+        z = z + d
+        rho = rn
+    return z
+
+
+def interpolation(dims, dirichlet):
+    """Trilinear interpolation P (n_fine x n_coarse) from the vertex-centred coarse grid (every other
+    node, dims (m + 1) / 2) of a logical grid with odd dims, lexicographic order (x fastest).
+    Rows of Dirichlet fine nodes and columns of Dirichlet coarse nodes are zero.
+    Returns (P, coarse dims, coarse Dirichlet mask)."""
+    mx, my, mz = dims
+    cx, cy, cz = (mx + 1) // 2, (my + 1) // 2, (mz + 1) // 2
+    nf = mx * my * mz
+    gi = np.arange(nf)
+    ix, iy, iz = gi % mx, (gi // mx) % my, gi // (mx * my)
+    cdir = dirichlet.reshape(mz, my, mx)[::2, ::2, ::2].ravel()
+    rows, cols, vals = [], [], []
+    for ox in (0, 1):
+        for oy in (0, 1):
+            for oz in (0, 1):
+                # coarse index along each axis: i / 2 for even i (once), (i -+ 1) / 2 for odd i
+                Jx = np.where(ix % 2 == 0, ix // 2, (ix - 1) // 2 + ox)
+                Jy = np.where(iy % 2 == 0, iy // 2, (iy - 1) // 2 + oy)
+                Jz = np.where(iz % 2 == 0, iz // 2, (iz - 1) // 2 + oz)
+                w = (np.where(ix % 2 == 0, 1.0 - ox, 0.5) * np.where(iy % 2 == 0, 1.0 - oy, 0.5) *
+                     np.where(iz % 2 == 0, 1.0 - oz, 0.5))
+                J = Jx + cx * (Jy + cy * Jz)
+                keep = (w > 0) & ~dirichlet
+                keep[keep] &= ~cdir[J[keep]]
+                rows.append(gi[keep])
+                cols.append(J[keep])
+                vals.append(w[keep])
+    P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nf, cx * cy * cz))
+    return P, (cx, cy, cz), cdir
+
+
+def mg_hierarchy(A, dims, dirichlet):
+    """[(A_l, P_l)] from the fine matrix down: A_{l+1} = P_l^T A_l P_l with identity rows at the
+    Dirichlet coarse nodes; the last entry has P = None (the coarsest grid)."""
+    levels = []
+    A = np.asarray(A, dtype=np.float64)
+    dims = tuple(int(d) for d in dims)
+    dirichlet = np.asarray(dirichlet, dtype=bool)
+    while (len(levels) < MG_MAX_LEVELS - 1 and all(d % 2 == 1 and d >= MG_MIN_DIM for d in dims)):
+        P, cdims, cdir = interpolation(dims, dirichlet)
+        Ac = np.asarray((P.T @ sp.csr_matrix(A) @ P).todense())
+        Ac[cdir, :] = 0.0
+        Ac[:, cdir] = 0.0
+        Ac[cdir, cdir] = 1.0
+        levels.append((A, P))
+        A, dims, dirichlet = Ac, cdims, cdir
+    levels.append((A, None))
+    return levels
+
+
+def vcycle(levels, b, level=0):
+    """One symmetric V-cycle for A_0 x = b from x = 0: Chebyshev pre-smoothing, residual,
+    restriction P^T, the V-cycle of the next grid, prolongation P, residual and Chebyshev
+    post-smoothing (the same polynomial, so the cycle is a symmetric linear operator);
+    Chebyshev with MG_COARSE_DEGREE steps on the coarsest grid."""
+    A, P = levels[level]
+    if P is None:
+        return chebyshev_ratio_apply(A, b, MG_COARSE_DEGREE, float(MG_COARSE_DEGREE ** 2))
+    x = chebyshev_ratio_apply(A, b, MG_SMOOTH_DEGREE, MG_SMOOTH_RATIO)
+    x = x + P @ vcycle(levels, P.T @ (b - A @ x), level + 1)
+    return x + chebyshev_ratio_apply(A, b - A @ x, MG_SMOOTH_DEGREE, MG_SMOOTH_RATIO)
