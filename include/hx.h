@@ -275,12 +275,23 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
  *                            the Q1 mass is a poor match of M when alpha dominates (iteration
  *                            counts double against Jacobi at alpha = 1000, nu = 1e-2), Mc is a
  *                            good one, and the stiffness part is unchanged.
+ *   HX_PREC_LOR_MG           z = one symmetric V-cycle for A_LOR z = r, A_LOR = alpha Mc +
+ *                            nu K_LOR, on meshes from hx_mesh_create_box/structured (the
+ *                            paper's structured geometric multigrid on the LOR matrix,
+ *                            Sec. 5.2).  The (pN+1)^3 LOR grid is coarsened vertex-centred
+ *                            while every dimension is odd and >= 5; trilinear interpolation P
+ *                            of the logical grid, Galerkin coarse operators P^T A P (27-point
+ *                            stencils), `degree` Chebyshev-Jacobi smoothing steps on
+ *                            [b / 10, b] before and after the coarse correction (the paper
+ *                            smooths with ordered ILU), 16 Chebyshev steps on [b / 256, b] on
+ *                            the coarsest grid.  HX_ERR_UNSUPPORTED on other meshes.
  * Jacobi and collocated mass use z = r in Dirichlet rows; A_LOR has identity rows there.
  */
 #define HX_PREC_JACOBI 0
 #define HX_PREC_COLLOCATED_MASS 1
 #define HX_PREC_LOR 2
 #define HX_PREC_LOR_MC 3
+#define HX_PREC_LOR_MG 4
 
 /*
  * alpha Mc as a vector (Sec. 5.1): diag[i] = alpha sum over elements K and local nodes
@@ -293,7 +304,8 @@ HX_API hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream);
 /*
  * Select the preconditioner of hx_solve_pcg, hx_solve_pcg_host, hx_solve_pcg_mixed and
  * batched solves of this operator (kind: HX_PREC_*; degree: Chebyshev steps of
- * HX_PREC_LOR, 1..64, ignored otherwise).  The choice follows later
+ * HX_PREC_LOR / HX_PREC_LOR_MC, smoothing steps of HX_PREC_LOR_MG, 1..64, ignored
+ * otherwise).  The choice follows later
  * hx_op_set_coefficients calls; a batch keeps the preconditioners its operators had
  * when it was created.
  * Errors: HX_ERR_ARG (unknown kind, degree out of range, HX_PREC_COLLOCATED_MASS with

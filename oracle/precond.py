@@ -219,7 +219,7 @@ def mg_hierarchy(A, dims, dirichlet):
     return levels
 
 
-def vcycle(levels, b, level=0):
+def vcycle(levels, b, level=0, smooth_degree=MG_SMOOTH_DEGREE):
     """One symmetric V-cycle for A_0 x = b from x = 0: Chebyshev pre-smoothing, residual,
     restriction P^T, the V-cycle of the next grid, prolongation P, residual and Chebyshev
     post-smoothing (the same polynomial, so the cycle is a symmetric linear operator);
@@ -227,6 +227,6 @@ def vcycle(levels, b, level=0):
     A, P = levels[level]
     if P is None:
         return chebyshev_ratio_apply(A, b, MG_COARSE_DEGREE, float(MG_COARSE_DEGREE ** 2))
-    x = chebyshev_ratio_apply(A, b, MG_SMOOTH_DEGREE, MG_SMOOTH_RATIO)
-    x = x + P @ vcycle(levels, P.T @ (b - A @ x), level + 1)
-    return x + chebyshev_ratio_apply(A, b - A @ x, MG_SMOOTH_DEGREE, MG_SMOOTH_RATIO)
+    x = chebyshev_ratio_apply(A, b, smooth_degree, MG_SMOOTH_RATIO)
+    x = x + P @ vcycle(levels, P.T @ (b - A @ x), level + 1, smooth_degree)
+    return x + chebyshev_ratio_apply(A, b - A @ x, smooth_degree, MG_SMOOTH_RATIO)

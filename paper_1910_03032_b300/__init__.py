@@ -32,6 +32,7 @@ HX_PREC_JACOBI = 0
 HX_PREC_COLLOCATED_MASS = 1
 HX_PREC_LOR = 2
 HX_PREC_LOR_MC = 3
+HX_PREC_LOR_MG = 4
 
 _NAMES = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_CUDA", -3: "HX_ERR_OOM", -4: "HX_ERR_INVALID_MESH",
           -5: "HX_ERR_NOT_CONVERGED", -6: "HX_ERR_BREAKDOWN", -7: "HX_ERR_UNSUPPORTED"}
@@ -550,4 +551,4 @@ class Operator:
 
 __all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
                               "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS",
-                              "HX_PREC_LOR", "HX_PREC_LOR_MC"]
+                              "HX_PREC_LOR", "HX_PREC_LOR_MC", "HX_PREC_LOR_MG"]

@@ -78,6 +78,7 @@ struct hx_mesh {
   unsigned char* dir = nullptr;  // [n_dof]
   double* X8 = nullptr;          // [E][8][3]
   long long n_dirichlet = 0;     // Dirichlet DoFs (0: no boundary condition fixes the constants)
+  long long grid[3] = {0, 0, 0}; // structured meshes: the logical (pN+1)-node grid of the DoFs
 };
 
 struct hx_op {
@@ -125,6 +126,9 @@ struct hx_op {
   unsigned long long* lor_bound = nullptr;
   HxChebWork cheb = {0, nullptr, nullptr, nullptr, nullptr};
   double* zl = nullptr;               // [n_dof] preconditioned residual
+  // geometric multigrid on the LOR matrix (HX_PREC_LOR_MG, structured meshes)
+  HxMg mg = {};
+  bool mg_built = false;
 };
 
 namespace {
@@ -283,7 +287,13 @@ hx_status hx_mesh_create_box(int nx, int ny, int nz, int p, int q, const double*
                   ((dirichlet_faces & 16) && K == 0) || ((dirichlet_faces & 32) && K == gz - 1))
                      ? 1
                      : 0;
-  return build_mesh(p, q, n_vert, vert_xyz, E, ev.data(), n_dof, R.data(), dir.data(), out);
+  s = build_mesh(p, q, n_vert, vert_xyz, E, ev.data(), n_dof, R.data(), dir.data(), out);
+  if (s == HX_OK) {
+    (*out)->grid[0] = gx;
+    (*out)->grid[1] = gy;
+    (*out)->grid[2] = gz;
+  }
+  return s;
 }
 
 hx_status hx_mesh_create_structured(int nx, int ny, int nz, int p, int q, const double* vert_xyz, hx_mesh** out) {
@@ -398,6 +408,22 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->cheb.d1);
   dfree(op->cheb.coef);
   dfree(op->zl);
+  for (int l = 0; l < op->mg.n_levels; ++l) {
+    HxMgLevel& L = op->mg.levels[l];
+    dfree(L.r);
+    dfree(L.coef);
+    if (l > 0) {
+      dfree(L.dir_own);
+      dfree(L.val);
+      dfree(L.dinv);
+      dfree(L.b);
+      dfree(L.x);
+      dfree(L.res);
+      dfree(L.d0);
+      dfree(L.d1);
+      dfree(L.bound);
+    }
+  }
   delete op;
 }
 
@@ -447,6 +473,50 @@ hx_status lor_assemble(hx_op* op, cudaStream_t s, int* nl) {
   HX_TRY(hx_lor_coefficients(op->lor_bound, op->cheb.degree, op->cheb.coef, s), "Chebyshev coefficients");
   *nl += 3;
   op->lor_values_set = true;
+  if (op->mg_built) {
+    HX_TRY(hx_mg_assemble(op->mg, op->lor, op->lor_bound, s), "multigrid hierarchy");
+    *nl += 3 * (op->mg.n_levels - 1) + op->mg.n_levels;
+  }
+  return HX_OK;
+}
+
+// The multigrid levels of a structured mesh (allocated once; values by hx_mg_assemble).
+hx_status mg_setup(hx_op* op, int smooth_degree, cudaStream_t s) {
+  const hx_mesh* m = op->mesh;
+  HxMg& M = op->mg;
+  M.smooth_degree = smooth_degree;
+  M.smooth_ratio = 10.0;
+  M.coarse_degree = 16;
+  if (op->mg_built) return HX_OK;
+  hx_status st = HX_OK;
+  HxMgLevel& F = M.levels[0];
+  F.g = HxGrid{(int)m->grid[0], (int)m->grid[1], (int)m->grid[2], m->n_dof};
+  F.dir = m->dir;
+  F.res = op->cheb.res;
+  F.d0 = op->cheb.d0;
+  F.d1 = op->cheb.d1;
+  M.n_levels = 1;
+  if ((st = dalloc(&F.r, (size_t)F.g.n, "MG residual")) || (st = dalloc(&F.coef, 2 * HX_LOR_MAX_DEGREE, "MG coefficients")))
+    return st;
+  while (M.n_levels < HX_MG_MAX_LEVELS) {
+    const HxGrid& g = M.levels[M.n_levels - 1].g;
+    if (!(g.mx % 2 == 1 && g.my % 2 == 1 && g.mz % 2 == 1 && g.mx >= 5 && g.my >= 5 && g.mz >= 5)) break;
+    HxMgLevel& C = M.levels[M.n_levels];
+    C.g = HxGrid{(g.mx + 1) / 2, (g.my + 1) / 2, (g.mz + 1) / 2, 0};
+    C.g.n = (long long)C.g.mx * C.g.my * C.g.mz;
+    const size_t n = (size_t)C.g.n;
+    ++M.n_levels;  // counted before the allocations so that destroy frees a partial level
+    if ((st = dalloc(&C.dir_own, n, "MG mask")) || (st = dalloc(&C.val, 27 * n, "MG stencil")) ||
+        (st = dalloc(&C.dinv, n, "MG dinv")) || (st = dalloc(&C.b, n, "MG b")) || (st = dalloc(&C.x, n, "MG x")) ||
+        (st = dalloc(&C.r, n, "MG r")) || (st = dalloc(&C.res, n, "MG res")) || (st = dalloc(&C.d0, n, "MG d0")) ||
+        (st = dalloc(&C.d1, n, "MG d1")) || (st = dalloc(&C.coef, 2 * HX_LOR_MAX_DEGREE, "MG coefficients")) ||
+        (st = dalloc(&C.bound, 1, "MG bound")))
+      return st;
+    C.dir = C.dir_own;
+    HX_TRY(hx_mg_coarse_dir(M.levels[M.n_levels - 2], C, s), "MG coarse mask");
+    op->launches += 1;
+  }
+  op->mg_built = true;
   return HX_OK;
 }
 
@@ -555,7 +625,7 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
     if (launches) *launches = nl;
     if (st) return st;
   }
-  if (op->prec == HX_PREC_LOR) {
+  if (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) {
     hx_status st = lor_assemble(op, s, &nl);
     if (launches) *launches = nl;
     if (st) return st;
@@ -638,7 +708,7 @@ hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const doubl
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
   if (op->geom == HX_GEOM_ONTHEFLY && nu_q && !op->nu_q)
     return fail(HX_ERR_ARG, "on-the-fly operator created without a nu field cannot take one");
-  if (op->prec == HX_PREC_LOR && nu_q)
+  if ((op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) && nu_q)
     return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
   int nl = 0;
   hx_status st = setup_coefficients(op, alpha, nu, nu_q, nullptr, (cudaStream_t)stream, &nl);
@@ -721,7 +791,7 @@ HxCgBuffers cg_buffers(const hx_op* op) {
   b.yE = op->yE;
   b.partial = op->partial;
   b.st = op->st;
-  b.z = (op->prec == HX_PREC_LOR) ? op->zl : nullptr;
+  b.z = (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) ? op->zl : nullptr;
   b.cond = 0ull;
   b.nullspace = op->singular ? 1 : 0;
   return b;
@@ -748,6 +818,17 @@ hx_status ensure_solver(hx_op* op) {
 }
 
 // One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
+// z = M^-1 r for the preconditioners that run outside the CG kernels (LOR forms)
+cudaError_t apply_z(const hx_op* op, const double* r, double* z, const int* done, cudaStream_t s) {
+  if (op->prec == HX_PREC_LOR_MG) return hx_mg_vcycle(op->mg, op->lor, r, z, done, s);
+  return hx_lor_precondition(op->lor, op->cheb, r, z, done, s);
+}
+int z_launches(const hx_op* op) {
+  if (op->prec == HX_PREC_LOR_MG) return hx_mg_vcycle_launches(op->mg);
+  if (op->prec == HX_PREC_LOR) return op->cheb.degree;
+  return 0;
+}
+
 // One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
 // cond: the conditional handle of an enclosing graph while loop (0 outside one).
 cudaError_t cg_iteration(const hx_op* op, cudaStream_t s, unsigned long long cond = 0ull) {
@@ -757,7 +838,7 @@ cudaError_t cg_iteration(const hx_op* op, cudaStream_t s, unsigned long long con
   if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
   if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
   if (e == cudaSuccess && b.z) {
-    e = hx_lor_precondition(op->lor, op->cheb, op->r, op->zl, &op->st->done, s);
+    e = apply_z(op, op->r, op->zl, &op->st->done, s);
     if (e == cudaSuccess) e = hx_launch_cg_rz(b, s);
   }
   if (e == cudaSuccess) e = hx_launch_cg_direction(b, s);
@@ -765,12 +846,12 @@ cudaError_t cg_iteration(const hx_op* op, cudaStream_t s, unsigned long long con
 }
 
 // kernels one CG iteration launches
-int iteration_launches(const hx_op* op) { return op->prec == HX_PREC_LOR ? 4 + op->cheb.degree + 1 : 4; }
+int iteration_launches(const hx_op* op) { return z_launches(op) > 0 ? 4 + z_launches(op) + 1 : 4; }
 
 // z = M^-1 r before the first direction (LOR preconditioner only; Jacobi is fused into cg_start)
 cudaError_t precondition_start(const hx_op* op, cudaStream_t s) {
-  if (op->prec != HX_PREC_LOR) return cudaSuccess;
-  return hx_lor_precondition(op->lor, op->cheb, op->r, op->zl, &op->st->done, s);
+  if (op->prec != HX_PREC_LOR && op->prec != HX_PREC_LOR_MG) return cudaSuccess;
+  return apply_z(op, op->r, op->zl, &op->st->done, s);
 }
 
 constexpr int kChunk = 16;  // CG iterations per launch of the fallback (non-conditional) path
@@ -846,7 +927,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   }
   HX_TRY(precondition_start(op, st), "first preconditioner");
   HX_TRY(hx_launch_cg_start(buf, st), "cg start");
-  op->launches += 2 + (op->prec == HX_PREC_LOR ? op->cheb.degree : 0);
+  op->launches += 2 + z_launches(op);
   if (op->singular) {
     HX_TRY(hx_launch_cg_direction(buf, st), "cg first direction");  // p = z - mean z
     op->launches += 1;
@@ -1056,7 +1137,7 @@ hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_
 hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
                       cudaStream_t user, hx_solve_info* info) {
   const hx_mesh* m = op->mesh;
-  if (op->prec == HX_PREC_LOR)
+  if (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG)
     return fail(HX_ERR_UNSUPPORTED, "mixed-precision solves take the Jacobi or collocated mass preconditioner");
   hx_status s = ensure_solver(op);
   if (s) return s;
@@ -1428,9 +1509,12 @@ hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream) {
 
 hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream) {
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
-  if (kind != HX_PREC_JACOBI && kind != HX_PREC_COLLOCATED_MASS && kind != HX_PREC_LOR && kind != HX_PREC_LOR_MC)
+  if (kind != HX_PREC_JACOBI && kind != HX_PREC_COLLOCATED_MASS && kind != HX_PREC_LOR && kind != HX_PREC_LOR_MC &&
+      kind != HX_PREC_LOR_MG)
     return fail(HX_ERR_ARG, "unknown preconditioner");
-  const bool lor = kind == HX_PREC_LOR || kind == HX_PREC_LOR_MC;
+  const bool lor = kind == HX_PREC_LOR || kind == HX_PREC_LOR_MC || kind == HX_PREC_LOR_MG;
+  if (kind == HX_PREC_LOR_MG && op->mesh->grid[0] == 0)
+    return fail(HX_ERR_UNSUPPORTED, "the multigrid preconditioner needs a structured mesh (hx_mesh_create_box)");
   cudaStream_t s = (cudaStream_t)stream;
   hx_status st = HX_OK;
   if (kind == HX_PREC_COLLOCATED_MASS) {
@@ -1441,6 +1525,7 @@ hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream
     if (degree < 1 || degree > HX_LOR_MAX_DEGREE) return fail(HX_ERR_ARG, "degree must be in [1, %d]", HX_LOR_MAX_DEGREE);
     if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
     if ((st = lor_setup(op, degree, s))) return st;
+    if (kind == HX_PREC_LOR_MG && (st = mg_setup(op, degree, s))) return st;
   }
   // the captured CG iterations differ between the preconditioners: capture again at the next solve
   if (op->graph) {
@@ -1448,12 +1533,12 @@ hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream
     op->graph = nullptr;
   }
   op->graph_failed = false;
-  op->prec = lor ? HX_PREC_LOR : kind;  // one solver path for both LOR forms
+  op->prec = (kind == HX_PREC_LOR_MC) ? HX_PREC_LOR : kind;  // one solver path for both Chebyshev forms
   op->mixed_stale = true;  // the FP32 inverse diagonal follows at the next mixed solve
   int nl = 0;
   if (lor) {
     op->cheb.degree = degree;
-    op->lor_collocated = kind == HX_PREC_LOR_MC ? 1 : 0;
+    op->lor_collocated = (kind == HX_PREC_LOR_MC || kind == HX_PREC_LOR_MG) ? 1 : 0;
     st = lor_assemble(op, s, &nl);
   } else if (op->dinv) {
     st = refresh_dinv(op, s, &nl);
@@ -1470,9 +1555,9 @@ hx_status hx_op_precond_apply(hx_op* op, const double* r, double* z, void* strea
   // the solver workspace is set up on the solver stream: order after it
   HX_TRY(cudaEventRecord(op->ev, op->stream), "event record");
   HX_TRY(cudaStreamWaitEvent(s, op->ev, 0), "stream wait");
-  if (op->prec == HX_PREC_LOR) {
-    HX_TRY(hx_lor_precondition(op->lor, op->cheb, r, z, nullptr, s), "LOR preconditioner");
-    op->launches += op->cheb.degree;
+  if (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) {
+    HX_TRY(apply_z(op, r, z, nullptr, s), "LOR preconditioner");
+    op->launches += z_launches(op);
   } else {
     HX_TRY(hx_launch_scale(op->mesh->n_dof, op->dinv, r, z, s), "preconditioner apply");
     op->launches += 1;

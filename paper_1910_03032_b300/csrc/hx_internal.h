@@ -193,6 +193,36 @@ cudaError_t hx_lor_coefficients(const unsigned long long* bound, int degree, dou
 cudaError_t hx_lor_precondition(const HxLorMatrix& A, const HxChebWork& w, const double* r, double* z,
                                 const int* done, cudaStream_t s);
 cudaError_t hx_lor_spmv(const HxLorMatrix& A, const double* x, double* y, cudaStream_t s);
+
+// ---- geometric multigrid V-cycle on the LOR matrix of a structured mesh (hx_mg.cu) ----
+struct HxGrid {
+  int mx, my, mz;  // logical grid dimensions (x fastest)
+  long long n;
+};
+struct HxMgLevel {
+  HxGrid g;
+  const unsigned char* dir;  // Dirichlet mask (the mesh's on the fine level)
+  unsigned char* dir_own;    // coarse levels: owned mask
+  double* val;               // coarse levels: [27][n] Galerkin stencil
+  double* dinv;              // coarse levels: inverse diagonal
+  double *b, *x, *r;         // right-hand side, solution, residual (b, x: coarse levels)
+  double *res, *d0, *d1;     // Chebyshev work vectors
+  double* coef;              // Chebyshev coefficients of this level's smoother (coarse solver)
+  unsigned long long* bound; // coarse levels: Gershgorin bound of D^-1 A
+};
+#define HX_MG_MAX_LEVELS 16
+struct HxMg {
+  int n_levels;
+  int smooth_degree;     // Chebyshev steps before and after the coarse correction
+  double smooth_ratio;   // smoothing interval [b / ratio, b]
+  int coarse_degree;     // Chebyshev steps on the coarsest grid, interval [b / k^2, b]
+  HxMgLevel levels[HX_MG_MAX_LEVELS];
+};
+cudaError_t hx_mg_coarse_dir(const HxMgLevel& F, HxMgLevel& C, cudaStream_t s);
+cudaError_t hx_mg_assemble(const HxMg& M, const HxLorMatrix& A0, const unsigned long long* bound0, cudaStream_t s);
+cudaError_t hx_mg_vcycle(const HxMg& M, const HxLorMatrix& A0, const double* r, double* z, const int* done,
+                         cudaStream_t s);
+int hx_mg_vcycle_launches(const HxMg& M);
 // mixed-precision refinement helpers
 cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s);

@@ -259,3 +259,71 @@ def test_lor_errors(hx):
     with pytest.raises(hx.HxError) as ei:
         op2.set_coefficients(1.0, 1.0, to_dev(np.full((E, Q), 0.3)))
     assert ei.value.status == -7
+
+
+# ---------------------------------------------------------------------------
+# geometric multigrid V-cycle on the LOR matrix (Sec. 5.2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,p,dirichlet,alpha,deg", [(4, 2, True, 0.0, 3), (2, 4, True, 5.0, 2), (4, 2, False, 0.0, 3),
+                                                     (3, 3, True, 1.0, 3), (4, 4, True, 100.0, 4)])
+def test_mg_vcycle_matches_oracle(hx, N, p, dirichlet, alpha, deg):
+    from oracle import precond
+    shape = (N, N, N)
+    V, EV, om = case(shape, p, seed=700 + N + p, dirichlet=dirichlet)
+    mesh = hx.Mesh.box(*shape, p, p + 2, V, dirichlet_faces=63 if dirichlet else 0)
+    op = hx.Operator(mesh, alpha, 1.0)
+    op.set_preconditioner(hx.HX_PREC_LOR_MG, deg)
+    A = precond.lor_matrix(om, alpha, 1.0, "collocated")
+    levels = precond.mg_hierarchy(A, (p * N + 1,) * 3, om.dirichlet)
+    r = np.where(om.dirichlet, 0.0, S.uniform_pm1(800 + N, om.n_dof))
+    z = op.precond_apply(to_dev(r)).cpu().numpy()
+    zo = precond.vcycle(levels, r, smooth_degree=deg)
+    assert rel_err(z, zo) <= 1e-11, (len(levels), rel_err(z, zo))
+
+
+@pytest.mark.parametrize("alpha,dirichlet", [(0.0, True), (1000.0, True), (0.0, False)])
+def test_mg_pcg_matches_oracle(hx, alpha, dirichlet):
+    from oracle import fem
+    from oracle.solve import jacobi_pcg, jacobi_pcg_nullspace
+    p, shape = 4, (4, 4, 4)
+    V, EV, om = case(shape, p, dirichlet=dirichlet)
+    mesh = hx.Mesh.box(*shape, p, p + 2, V, dirichlet_faces=63 if dirichlet else 0)
+    nu = 1.0 if alpha == 0.0 else 1e-2
+    op = hx.Operator(mesh, alpha, nu)
+    b = S.random_vector(om.n_dof, 43)
+    x_j, info_j = op.solve(to_dev(b), rtol=1e-10)
+    op.set_preconditioner(hx.HX_PREC_LOR_MG, 3)
+    x, info = op.solve(to_dev(b), rtol=1e-10)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    oop = fem.Operator(om, alpha, nu)
+    xo = (jacobi_pcg(oop, b, 1e-12) if dirichlet else jacobi_pcg_nullspace(oop, b, 1e-12))[0]
+    assert rel_err(x.cpu().numpy(), xo) <= 1e-8
+    if alpha == 0.0:
+        assert 2 * info["iterations"] < info_j["iterations"], (info["iterations"], info_j["iterations"])
+    else:
+        assert info["iterations"] <= info_j["iterations"] + 3
+
+
+def test_mg_iterations_flat_under_refinement(hx):
+    its = []
+    for N in (4, 8, 16):
+        V = S.structured_vertices(N, N, N, 0.1, 900 + N)
+        mesh = hx.Mesh.structured(N, N, N, 4, 6, V)
+        op = hx.Operator(mesh, 0.0, 1.0)
+        op.set_preconditioner(hx.HX_PREC_LOR_MG, 3)
+        x, info = op.solve(to_dev(S.uniform_pm1(901, mesh.n_dof)), rtol=1e-10)
+        assert info["status"] == 0
+        its.append(info["iterations"])
+    assert its[-1] <= its[0] + 10, its
+
+
+def test_mg_needs_a_structured_mesh(hx):
+    from oracle import fem
+    p, shape = 2, (2, 2, 2)
+    V, EV, om = case(shape, p)
+    mesh = hx.Mesh.general(p, p + 2, V, EV.astype(np.int64), om.n_dof, om.restriction.astype(np.int32),
+                           om.dirichlet.astype(np.uint8))
+    op = hx.Operator(mesh, 1.0, 1.0)
+    with pytest.raises(hx.HxError) as ei:
+        op.set_preconditioner(hx.HX_PREC_LOR_MG, 3)
+    assert ei.value.status == -7
