@@ -371,6 +371,8 @@ def run_hx(args, world, rank, local):
         line["sweep"] = run_sweep(hx, torch)
     if rank == 0 and args.grad:
         line["grad"] = run_grad(hx, torch, args)
+    if rank == 0 and args.precond:
+        line["precond"] = run_precond(hx, torch, args)
     if rank == 0 and args.batch:
         line["batch"] = run_batch(hx, torch, args)
     if rank == 0:
@@ -559,6 +561,47 @@ def run_grad(hx, torch, args):
             "timing": f"{reps} steps after 2 warm-up; kernel: 20 launches after 3"}
 
 
+def run_precond(hx, torch, args):
+    """Preconditioners on two solves: the projection step's pure-Neumann pressure Poisson (64^3,
+    p = 5) and the headline Helmholtz (96^3, p = 4, alpha = 1000, nu = 1e-2), both to 1e-10.
+    Per preconditioner: set-up time (selection: LOR pattern + values), solve time, iterations."""
+    cases = [("poisson_neumann_64_p5", 64, 5, 0.0, 1.0, 0), ("helmholtz_96_p4", 96, 4, 1000.0, 1e-2, 63)]
+    precs = [("jacobi", hx.HX_PREC_JACOBI, 0), ("lor_mc_k8", hx.HX_PREC_LOR_MC, 8),
+             ("lor_mc_k16", hx.HX_PREC_LOR_MC, 16), ("lor_mg_s2", hx.HX_PREC_LOR_MG, 2),
+             ("lor_mg_s3", hx.HX_PREC_LOR_MG, 3)]
+    out = {}
+    s = torch.cuda.current_stream()
+    for name, N, p, alpha, nu, faces in cases:
+        V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED)
+        mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=faces)
+        op = hx.Operator(mesh, alpha, nu)
+        xq = mesh.qpoint_coords()
+        f = torch.sin(math.pi * xq[..., 0]) * torch.sin(math.pi * xq[..., 1]) * torch.cos(math.pi * xq[..., 2])
+        b = op.load_vector(f.contiguous())
+        del xq, f
+        res = {"n_dof": mesh.n_dof}
+        for pname, kind, k in precs:
+            if alpha > 0 and pname == "lor_mc_k16":
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op.set_preconditioner(kind, max(k, 1))
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            x, info = op.solve(b, rtol=RTOL, max_it=20000)  # warm-up (graph capture)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            x, info = op.solve(b, rtol=RTOL, max_it=20000)
+            e1.record(s)
+            torch.cuda.synchronize()
+            res[pname] = {"setup_s": t_setup, "solve_s": e0.elapsed_time(e1) / 1e3, "iterations": info["iterations"],
+                          "true_rel_residual": info["true_rel_residual"], "status": info["status"]}
+        out[name] = res
+        del op, mesh, b, x
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_sweep(hx, torch):
     """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
     out = []
@@ -599,6 +642,7 @@ def main():
     ap.add_argument("--geom", default="stored", choices=["stored", "onthefly"])
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--batch", action="store_true", help="add the batched-solve measurement (64 instances; projection-step set)")
+    ap.add_argument("--precond", action="store_true", help="add the preconditioner comparison (Jacobi vs LOR)")
     ap.add_argument("--grad", action="store_true", help="add the adjoint-gradient measurement (32^3, p = 4)")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
