@@ -138,8 +138,11 @@ def dist_init():
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:  # host-only runs (the reference arm, CPU tests of this plumbing)
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -154,7 +157,8 @@ def reduce_max(v: float, world: int) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -446,14 +450,16 @@ def batch_specs(seed=4444, n=64):
 
 
 def run_batch(hx, torch, args):
-    """64 independent instances (8^3..40^3, p = 2..8) in one graph launch vs one solve after another, plus the
-    projection-step set (3 velocity Helmholtz + 1 pure-Neumann pressure Poisson, 64^3, p = 5)."""
-    def build(specs, faces_of):
+    """64 independent instances (8^3..32^3, p = 2..8) in one graph launch vs one solve after another, plus the
+    projection-step set (3 velocity Helmholtz + 1 pure-Neumann pressure Poisson, 64^3, p = 5; the
+    Poisson instance with the LOR multigrid preconditioner)."""
+    def build(specs, faces_of, prec_of=lambda k: (hx.HX_PREC_JACOBI, 0)):
         ops, bs, xs = [], [], []
         for k, (N, p, a, nu) in enumerate(specs):
             V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED + k)
             mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=faces_of(k))
             op = hx.Operator(mesh, a, nu)
+            op.set_preconditioner(*prec_of(k))
             xq = mesh.qpoint_coords()
             f = torch.sin(math.pi * xq[..., 0]) * torch.sin(math.pi * xq[..., 1]) * torch.cos(math.pi * xq[..., 2])
             ops.append(op)
@@ -474,10 +480,15 @@ def run_batch(hx, torch, args):
         return e0.elapsed_time(e1) / 1e3 / reps, out
 
     res = {}
-    for name, specs, faces_of in [
-            ("batch64", batch_specs(), lambda k: 63),
-            ("projection_step", [(64, 5, 1000.0, 1e-2)] * 3 + [(64, 5, 0.0, 1.0)], lambda k: 63 if k < 3 else 0)]:
-        ops, bs, xs = build(specs, faces_of)
+    # the projection step: 3 velocity Helmholtz solves (Jacobi) and the pure-Neumann pressure
+    # Poisson, whose Jacobi-PCG needs ~2800 iterations, with the LOR multigrid preconditioner
+    for name, specs, faces_of, prec_of in [
+            ("batch64", batch_specs(), lambda k: 63, lambda k: (hx.HX_PREC_JACOBI, 0)),
+            ("batch64_mg", batch_specs(), lambda k: 63,
+             lambda k: (hx.HX_PREC_LOR_MG, 2) if batch_specs()[k][2] == 0.0 else (hx.HX_PREC_JACOBI, 0)),
+            ("projection_step", [(64, 5, 1000.0, 1e-2)] * 3 + [(64, 5, 0.0, 1.0)], lambda k: 63 if k < 3 else 0,
+             lambda k: (hx.HX_PREC_JACOBI, 0) if k < 3 else (hx.HX_PREC_LOR_MG, 2))]:
+        ops, bs, xs = build(specs, faces_of, prec_of)
         batch = hx.Batch(ops, bs, xs, rtol=RTOL, max_it=20000)
         seq = lambda: [hx.hx_solve_pcg(o.handle, b, x, RTOL, 20000, False) for o, b, x in zip(ops, bs, xs)]
         seq()
