@@ -363,12 +363,18 @@ HX_API hx_status hx_op_gradient(hx_op* op, const double* u, const double* lam, d
  *   b, x      host arrays of n device pointers (n_dof_i doubles each), bound at
  *             creation: the graph reads b_i and writes x_i on every solve
  *   rtol, max_it  stopping rule of every instance (as hx_solve_pcg, x0 = 0)
- * The graph captures the operators' coefficients: after hx_op_set_coefficients on
- * an HX_GEOM_ONTHEFLY operator, create the batch again.  Synchronous create.
+ *   lanes     number of chains the instances are spread over: instance i starts
+ *             after instance i - lanes has finished, so at most `lanes` solves run
+ *             side by side (0 or >= n: all instances concurrently).  Small
+ *             instances gain from overlap; the many short kernels of multigrid
+ *             V-cycles run better in few lanes.
+ * The graph captures the operators' coefficients and preconditioners: after
+ * hx_op_set_coefficients on an HX_GEOM_ONTHEFLY operator, or hx_op_set_preconditioner,
+ * create the batch again.  Synchronous create.
  */
 typedef struct hx_batch hx_batch;
 HX_API hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, double* const* x, double rtol,
-                                 int max_it, hx_batch** out);
+                                 int max_it, int lanes, hx_batch** out);
 
 /* Solve every instance (after the caller's prior work on `stream`); infos: host array of n
  * results or NULL.  Returns HX_OK when all converged, else the first failing status.

@@ -79,7 +79,7 @@ SIGNATURES = {
     "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, ctypes.c_int, _P]),
     "hx_op_lor_csr": (_I, [_P, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "hx_op_precond_apply": (_I, [_P, _P, _P, _P]),
-    "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, ctypes.POINTER(_P)]),
+    "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, _I, ctypes.POINTER(_P)]),
     "hx_batch_solve": (_I, [_P, _P, _P]),
     "hx_batch_destroy": (None, [_P]),
     "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
@@ -348,8 +348,9 @@ def hx_op_precond_apply(op, r, z, stream=None):
     _check(_lib.hx_op_precond_apply(op, _dptr(r, n, "r"), _dptr(z, n, "z"), _stream(stream)))
 
 
-def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000):
-    """ops: operator handles; b, x: CUDA float64 tensors (n_dof_i each), bound to the batch."""
+def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000, lanes=0):
+    """ops: operator handles; b, x: CUDA float64 tensors (n_dof_i each), bound to the batch;
+    lanes: concurrent chains of solves (0: all instances at once)."""
     n = len(ops)
     if not (len(b) == len(x) == n) or n < 1:
         raise ValueError("ops, b and x must have the same positive length")
@@ -358,7 +359,8 @@ def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000):
     Xp = (ctypes.c_void_p * n)(*[_dptr(xi, hx_op_info(o)[1], f"x[{i}]").value for i, (o, xi) in enumerate(zip(ops, x))])
     out = ctypes.c_void_p()
     _check(_lib.hx_batch_create(n, ctypes.cast(H, ctypes.c_void_p), ctypes.cast(Bp, ctypes.c_void_p),
-                                ctypes.cast(Xp, ctypes.c_void_p), float(rtol), int(max_it), ctypes.byref(out)))
+                                ctypes.cast(Xp, ctypes.c_void_p), float(rtol), int(max_it), int(lanes),
+                                ctypes.byref(out)))
     return out
 
 
@@ -377,9 +379,9 @@ def hx_batch_destroy(batch):
 class Batch:
     """Owning handle of a batch; keeps its operators and vectors alive."""
 
-    def __init__(self, ops, b, x, rtol=1e-10, max_it=10000):
+    def __init__(self, ops, b, x, rtol=1e-10, max_it=10000, lanes=0):
         self.ops, self.b, self.x = list(ops), list(b), list(x)
-        self.handle = hx_batch_create([o.handle for o in self.ops], self.b, self.x, rtol, max_it)
+        self.handle = hx_batch_create([o.handle for o in self.ops], self.b, self.x, rtol, max_it, lanes)
 
     def solve(self, stream=None, raise_on_fail=True):
         return hx_batch_solve(self.handle, len(self.ops), stream, raise_on_fail)

@@ -412,9 +412,9 @@ void hx_op_destroy(hx_op* op) {
     HxMgLevel& L = op->mg.levels[l];
     dfree(L.r);
     dfree(L.coef);
+    dfree(L.val);
     if (l > 0) {
       dfree(L.dir_own);
-      dfree(L.val);
       dfree(L.dinv);
       dfree(L.b);
       dfree(L.x);
@@ -496,8 +496,10 @@ hx_status mg_setup(hx_op* op, int smooth_degree, cudaStream_t s) {
   F.d0 = op->cheb.d0;
   F.d1 = op->cheb.d1;
   M.n_levels = 1;
-  if ((st = dalloc(&F.r, (size_t)F.g.n, "MG residual")) || (st = dalloc(&F.coef, 2 * HX_LOR_MAX_DEGREE, "MG coefficients")))
+  if ((st = dalloc(&F.r, (size_t)F.g.n, "MG residual")) || (st = dalloc(&F.coef, 2 * HX_LOR_MAX_DEGREE, "MG coefficients")) ||
+      (st = dalloc(&F.val, 27 * (size_t)F.g.n, "MG fine stencil")))
     return st;
+  F.dinv = op->lor.dinv;
   while (M.n_levels < HX_MG_MAX_LEVELS) {
     const HxGrid& g = M.levels[M.n_levels - 1].g;
     if (!(g.mx % 2 == 1 && g.my % 2 == 1 && g.mz % 2 == 1 && g.mx >= 5 && g.my >= 5 && g.mz >= 5)) break;
@@ -1310,11 +1312,13 @@ hx_status add_captured_child(cudaGraph_t G, cudaStream_t s, const cudaGraphNode_
   return HX_OK;
 }
 
-hx_status build_batch_graph(hx_batch* B, double rtol, int max_it) {
+hx_status build_batch_graph(hx_batch* B, double rtol, int max_it, int lanes) {
   cudaGraph_t G = nullptr;
   HX_TRY(cudaGraphCreate(&G, 0), "batch graph");
   hx_status s = HX_OK;
   cudaStream_t cs = B->stream;
+  // instance i runs after instance i - lanes: `lanes` chains of solves run side by side
+  std::vector<cudaGraphNode_t> tails((size_t)B->n, nullptr);
   for (int i = 0; i < B->n && s == HX_OK; ++i) {
     hx_op* op = B->ops[i];
     const hx_mesh* m = op->mesh;
@@ -1323,7 +1327,8 @@ hx_status build_batch_graph(hx_batch* B, double rtol, int max_it) {
     const HxCgBuffers buf = cg_buffers(op);
     cudaGraphNode_t init = nullptr, loop = nullptr, tail = nullptr;
     // 1. initialization: r = P b (mean removed for pure Neumann), z = D^-1 r, p
-    s = add_captured_child(G, cs, nullptr, 0, [&]() {
+    const cudaGraphNode_t* dep = (i >= lanes) ? &tails[(size_t)(i - lanes)] : nullptr;
+    s = add_captured_child(G, cs, dep, dep ? 1 : 0, [&]() {
       cudaError_t e = cudaSuccess;
       if (op->singular) e = hx_launch_cg_mean(buf, bi, cs);
       if (e == cudaSuccess) e = hx_launch_cg_init(buf, bi, (const double*)nullptr, rtol, max_it, cs);
@@ -1375,6 +1380,7 @@ hx_status build_batch_graph(hx_batch* B, double rtol, int max_it) {
         e3 = cudaMemcpyAsync(xi, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, cs);
       return e3;
     }, &tail);
+    tails[(size_t)i] = tail;
   }
   if (s == HX_OK) {
     cudaError_t e = cudaGraphInstantiate(&B->exec, G, 0);
@@ -1389,10 +1395,11 @@ hx_status build_batch_graph(hx_batch* B, double rtol, int max_it) {
 extern "C" {
 
 hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, double* const* x, double rtol, int max_it,
-                          hx_batch** out) {
+                          int lanes, hx_batch** out) {
   if (!out) return fail(HX_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || !ops || !b || !x) return fail(HX_ERR_ARG, "need n >= 1 and non-NULL arrays");
+  if (lanes < 0) return fail(HX_ERR_ARG, "lanes must be >= 0");
   if (!(rtol >= 0.0) || max_it < 0) return fail(HX_ERR_ARG, "rtol must be >= 0 and max_it >= 0");
   for (int i = 0; i < n; ++i)
     if (!ops[i] || !b[i] || !x[i]) return fail(HX_ERR_ARG, "instance %d: NULL operator or vector", i);
@@ -1413,7 +1420,7 @@ hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, doub
   if (e == cudaSuccess && s == HX_OK) e = cudaMallocHost((void**)&B->st_host, sizeof(HxCgState) * n);
   if (e == cudaSuccess && s == HX_OK) e = cudaMallocHost((void**)&B->rn2_host, sizeof(double) * n);
   if (e != cudaSuccess && s == HX_OK) s = cuda_fail(e, "batch resources");
-  if (s == HX_OK) s = build_batch_graph(B, rtol, max_it);
+  if (s == HX_OK) s = build_batch_graph(B, rtol, max_it, (lanes == 0 || lanes > n) ? n : lanes);
   if (s != HX_OK) {
     hx_batch_destroy(B);
     return s;

@@ -200,12 +200,19 @@ __device__ __forceinline__ Real point_factors(const Real (&j0)[3], const Real (&
 // SY (q rounded up to odd, so x-line tasks of consecutive threads fall in
 // different banks) and plane stride SZ = q SY
 // ---------------------------------------------------------------------------
-template <int Q>
+//
+// FP32 (4-byte banks, shared-memory-bound kernel): rows are not padded (SY = q), so the
+// column stages of consecutive threads read consecutive words; the plane stride is odd
+// for the line stages; and the element stride is padded so that the columns of the next
+// element continue the bank sequence (R3 = q^2 mod 32) for warps that straddle elements.
+template <int Q, typename Real = double>
 struct Layout {
-  static constexpr int SY = (Q % 2 == 0) ? Q + 1 : Q;
-  static constexpr int SZ = Q * SY;
+  static constexpr bool F32 = sizeof(Real) == 4;
+  static constexpr int SY = F32 ? Q : ((Q % 2 == 0) ? Q + 1 : Q);
+  static constexpr int SZ = F32 ? ((Q * Q) | 1) : Q * SY;
   static constexpr int RG = Q * SZ;  // one region
-  static constexpr int R3 = 3 * RG;  // the three regions D, X, Y of one element
+  // the three regions D, X, Y of one element (element stride)
+  static constexpr int R3 = F32 ? 3 * RG + (((Q * Q - 3 * RG) % 32) + 32) % 32 : 3 * RG;
 };
 
 // ---------------------------------------------------------------------------
@@ -216,7 +223,7 @@ struct Layout {
 template <int N, int Q, int NE, int NT, typename Real>
 __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Real* smem, long long e0, long long E,
                                                     Real* __restrict__ yE) {
-  using Lt = Layout<Q>;
+  using Lt = Layout<Q, Real>;
   constexpr int N3 = N * N * N, SY = Lt::SY, SZ = Lt::SZ, R3 = Lt::R3;
   for (int t = threadIdx.x; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
@@ -245,7 +252,7 @@ __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Re
 template <typename Real, int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
 __global__ void __launch_bounds__(NT, MINB)
     apply_kernel(const __grid_constant__ HxTablesT<Real> T, const HxApplyArgsT<Real> A) {
-  using Lt = Layout<Q>;
+  using Lt = Layout<Q, Real>;
   constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q;
   constexpr int SY = Lt::SY, SZ = Lt::SZ, RG = Lt::RG, R3 = Lt::R3;
   constexpr int CQ = (Q + 1) / 2, CN = (N + 1) / 2;
@@ -712,7 +719,7 @@ template <typename Real, int P, int Q, int GEOM, bool NUF>
 cudaError_t launch_apply_impl(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, cudaStream_t s) {
   using C = Config<P, Q, Real>;
   constexpr int NE = C::NE, NT = C::NT, MINB = C::MINB;
-  const size_t shmem = sizeof(Real) * (size_t)(NE * Layout<Q>::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+  const size_t shmem = sizeof(Real) * (size_t)(NE * Layout<Q, Real>::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
   auto k = apply_kernel<Real, P, Q, NE, NT, MINB, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;

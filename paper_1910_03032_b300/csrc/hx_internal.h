@@ -203,7 +203,7 @@ struct HxMgLevel {
   HxGrid g;
   const unsigned char* dir;  // Dirichlet mask (the mesh's on the fine level)
   unsigned char* dir_own;    // coarse levels: owned mask
-  double* val;               // coarse levels: [27][n] Galerkin stencil
+  double* val;               // [27][n] stencil (fine level: the LOR matrix; coarse: Galerkin)
   double* dinv;              // coarse levels: inverse diagonal
   double *b, *x, *r;         // right-hand side, solution, residual (b, x: coarse levels)
   double *res, *d0, *d1;     // Chebyshev work vectors

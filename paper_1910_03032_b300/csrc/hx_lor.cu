@@ -136,6 +136,22 @@ __global__ void __launch_bounds__(kT) lor_values_kernel(const __grid_constant__ 
   const int p = T.p;
   const double am = collocated ? 0.0 : alpha;  // the Q1 mass enters only in the consistent form
   const double g2 = 0.57735026918962576451;  // 2-point Gauss nodes +-1/sqrt(3), weights 1
+  // Q1 shape functions on the sub-element's cube, prod_d (1 + s_d eta_d) / 2, and their
+  // gradients, at the 8 points: q1[qp][c] = (phi, dphi/deta_1, dphi/deta_2, dphi/deta_3)
+  __shared__ double q1[8][8][4];
+  if (threadIdx.x < 64) {
+    const int qp = threadIdx.x >> 3, c = threadIdx.x & 7;
+    double f[3], sg[3];
+    for (int d = 0; d < 3; ++d) {
+      sg[d] = ((c >> d) & 1) ? 1.0 : -1.0;
+      f[d] = 0.5 * (1.0 + sg[d] * (((qp >> d) & 1) ? g2 : -g2));
+    }
+    q1[qp][c][0] = f[0] * f[1] * f[2];
+    q1[qp][c][1] = 0.5 * sg[0] * f[1] * f[2];
+    q1[qp][c][2] = 0.5 * sg[1] * f[0] * f[2];
+    q1[qp][c][3] = 0.5 * sg[2] * f[0] * f[1];
+  }
+  __syncthreads();
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
     const long long o0 = off[g], o1 = off[g + 1];
     if (dir[g]) {
@@ -155,34 +171,25 @@ __global__ void __launch_bounds__(kT) lor_values_kernel(const __grid_constant__ 
       for_sub_elements(p, v, [&](int e_, int s, int t, int u, int c) {
         const double hs = T.xn[s + 1] - T.xn[s], ht = T.xn[t + 1] - T.xn[t], hu = T.xn[u + 1] - T.xn[u];
         double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const double sc[3] = {(c & 1) ? 1.0 : -1.0, (c & 2) ? 1.0 : -1.0, (c & 4) ? 1.0 : -1.0};
         for (int qp = 0; qp < 8; ++qp) {
-          const double eta[3] = {(qp & 1) ? g2 : -g2, (qp & 2) ? g2 : -g2, (qp & 4) ? g2 : -g2};
           double j0[3], j1[3], j2[3], f[7];
-          hx::trilinear_jacobian(cf, T.xn[s] + 0.5 * (eta[0] + 1.0) * hs, T.xn[t] + 0.5 * (eta[1] + 1.0) * ht,
-                                 T.xn[u] + 0.5 * (eta[2] + 1.0) * hu, j0, j1, j2);
+          hx::trilinear_jacobian(cf, T.xn[s] + 0.5 * (((qp & 1) ? g2 : -g2) + 1.0) * hs,
+                                 T.xn[t] + 0.5 * (((qp & 2) ? g2 : -g2) + 1.0) * ht,
+                                 T.xn[u] + 0.5 * (((qp & 4) ? g2 : -g2) + 1.0) * hu, j0, j1, j2);
           for (int d = 0; d < 3; ++d) {
             j0[d] *= 0.5 * hs;
             j1[d] *= 0.5 * ht;
             j2[d] *= 0.5 * hu;
           }
           hx::point_factors(j0, j1, j2, am, nu, f);
-          // Q1 shape functions on the sub-element's cube: prod_d (1 + s_d eta_d) / 2
-          const double fc[3] = {0.5 * (1.0 + sc[0] * eta[0]), 0.5 * (1.0 + sc[1] * eta[1]),
-                                0.5 * (1.0 + sc[2] * eta[2])};
-          const double phic = fc[0] * fc[1] * fc[2];
-          const double gc[3] = {0.5 * sc[0] * fc[1] * fc[2], 0.5 * sc[1] * fc[0] * fc[2],
-                                0.5 * sc[2] * fc[0] * fc[1]};
-          const double Gg[3] = {f[1] * gc[0] + f[2] * gc[1] + f[3] * gc[2], f[2] * gc[0] + f[4] * gc[1] + f[5] * gc[2],
-                                f[3] * gc[0] + f[5] * gc[1] + f[6] * gc[2]};
-          for (int c2 = 0; c2 < 8; ++c2) {
-            const double s2[3] = {(c2 & 1) ? 1.0 : -1.0, (c2 & 2) ? 1.0 : -1.0, (c2 & 4) ? 1.0 : -1.0};
-            const double f2[3] = {0.5 * (1.0 + s2[0] * eta[0]), 0.5 * (1.0 + s2[1] * eta[1]),
-                                  0.5 * (1.0 + s2[2] * eta[2])};
-            const double g2v[3] = {0.5 * s2[0] * f2[1] * f2[2], 0.5 * s2[1] * f2[0] * f2[2],
-                                   0.5 * s2[2] * f2[0] * f2[1]};
-            a[c2] += f[0] * phic * (f2[0] * f2[1] * f2[2]) + Gg[0] * g2v[0] + Gg[1] * g2v[1] + Gg[2] * g2v[2];
-          }
+          const double mc = f[0] * q1[qp][c][0];
+          const double gx = q1[qp][c][1], gy = q1[qp][c][2], gz = q1[qp][c][3];
+          const double G0 = f[1] * gx + f[2] * gy + f[3] * gz;
+          const double G1 = f[2] * gx + f[4] * gy + f[5] * gz;
+          const double G2 = f[3] * gx + f[5] * gy + f[6] * gz;
+#pragma unroll
+          for (int c2 = 0; c2 < 8; ++c2)
+            a[c2] += mc * q1[qp][c2][0] + G0 * q1[qp][c2][1] + G1 * q1[qp][c2][2] + G2 * q1[qp][c2][3];
         }
         for (int c2 = 0; c2 < 8; ++c2) {
           const int h = corner_dof(R, p, e_, s, t, u, c2);

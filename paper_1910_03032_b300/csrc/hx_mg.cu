@@ -7,7 +7,8 @@
 // Interpolation P is trilinear in the logical indices; its rows at Dirichlet fine nodes and
 // its columns at Dirichlet coarse nodes are zero.  Coarse operators are Galerkin products
 // P^T A P, stored as 27-point stencils ([27][n], neighbour k = (dz+1) 9 + (dy+1) 3 + (dx+1)),
-// with identity rows at Dirichlet coarse nodes.  Smoothing: Chebyshev-Jacobi polynomials
+// with identity rows at Dirichlet coarse nodes; the fine LOR matrix is copied into the same
+// structure-of-arrays form, so every smoother pass reads coalesced.  Smoothing: Chebyshev-Jacobi polynomials
 // (the paper uses ordered ILU, a sequential method); the same polynomial before and after the
 // coarse correction keeps the cycle a symmetric linear operator, as CG needs.
 #include <cuda_runtime.h>
@@ -44,7 +45,7 @@ __device__ __forceinline__ long long index(const HxGrid& g, int x, int y, int z)
   return (long long)x + (long long)g.mx * ((long long)y + (long long)g.my * z);
 }
 
-// The fine level: the assembled LOR matrix in CSR.
+// The assembled LOR matrix in CSR (read once per assembly, into the fine stencil).
 struct CsrRows {
   const long long* off;
   const int* col;
@@ -60,7 +61,7 @@ struct CsrRows {
   }
 };
 
-// Coarse levels: 27-point stencils on the logical grid.
+// Every level: 27-point stencils on the logical grid.
 struct StencilRows {
   HxGrid g;
   const double* val;  // [27][n]
@@ -239,6 +240,23 @@ __global__ void __launch_bounds__(kT) mg_galerkin_kernel(Rows A, HxGrid fg, cons
   }
 }
 
+// The fine LOR matrix (CSR, rows of the logical grid) as a 27-point stencil [27][n]: the
+// structure-of-arrays form the smoothers read with coalesced loads.
+__global__ void __launch_bounds__(kT) mg_csr_to_stencil_kernel(CsrRows A, HxGrid g, double* __restrict__ v27) {
+  MG_STRIDE(i, g.n) {
+    for (int k = 0; k < 27; ++k) v27[(long long)k * g.n + i] = 0.0;
+    int ix, iy, iz;
+    coords(g, i, ix, iy, iz);
+    A.each(i, [&](long long j, double a) {
+      int jx, jy, jz;
+      coords(g, j, jx, jy, jz);
+      const int dx = jx - ix, dy = jy - iy, dz = jz - iz;
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
+        v27[(long long)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * g.n + i] = a;
+    });
+  }
+}
+
 // dinv and the Gershgorin bound of D^-1 A of a stencil level
 __global__ void __launch_bounds__(kT) mg_diag_kernel(StencilRows A, double* __restrict__ dinv,
                                                      unsigned long long* bound) {
@@ -331,15 +349,14 @@ cudaError_t hx_mg_coarse_dir(const HxMgLevel& F, HxMgLevel& C, cudaStream_t s) {
 // Galerkin operators, inverse diagonals, bounds and Chebyshev coefficients of every level
 // (the fine level's matrix, inverse diagonal and bound come from the LOR assembly).
 cudaError_t hx_mg_assemble(const HxMg& M, const HxLorMatrix& A0, const unsigned long long* bound0, cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
+  // the fine level as a stencil (every LOR row couples only logical neighbours)
+  mg_csr_to_stencil_kernel<<<grid_of(M.levels[0].g.n), kT, 0, s>>>(csr_rows(A0), M.levels[0].g, M.levels[0].val);
+  cudaError_t e = cudaGetLastError();
   for (int l = 1; l < M.n_levels && e == cudaSuccess; ++l) {
     const HxMgLevel& F = M.levels[l - 1];
     const HxMgLevel& C = M.levels[l];
     const unsigned g = grid_of(C.g.n);
-    if (l == 1)
-      mg_galerkin_kernel<CsrRows><<<g, kT, 0, s>>>(csr_rows(A0), F.g, F.dir, C.g, C.dir, C.val);
-    else
-      mg_galerkin_kernel<StencilRows><<<g, kT, 0, s>>>(stencil_rows(F), F.g, F.dir, C.g, C.dir, C.val);
+    mg_galerkin_kernel<StencilRows><<<g, kT, 0, s>>>(stencil_rows(F), F.g, F.dir, C.g, C.dir, C.val);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(C.bound, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
@@ -360,7 +377,7 @@ cudaError_t hx_mg_assemble(const HxMg& M, const HxLorMatrix& A0, const unsigned 
 
 cudaError_t hx_mg_vcycle(const HxMg& M, const HxLorMatrix& A0, const double* r, double* z, const int* done,
                          cudaStream_t s) {
-  return level_cycle(M, 0, csr_rows(A0), A0.dinv, r, z, done, s);
+  return level_cycle(M, 0, stencil_rows(M.levels[0]), A0.dinv, r, z, done, s);
 }
 
 int hx_mg_vcycle_launches(const HxMg& M) {

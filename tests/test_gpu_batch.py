@@ -27,13 +27,17 @@ def test_batch_matches_individual_solves():
         bs.append(b)
         xs.append(torch.full_like(b, float("nan")))
         refs.append((x_ref, info))
-    batch = hx.Batch(ops, bs, xs, rtol=1e-10)
-    for rep in range(2):  # the bound graph is reusable
-        infos = batch.solve()
-        for (x_ref, info), x, bi in zip(refs, xs, infos):
-            assert bi["status"] == 0 and bi["iterations"] == info["iterations"]
-            assert bi["true_rel_residual"] <= 1.01e-10
-            assert rel_err(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-14
+    for lanes in (0, 1, 2, 4):  # all concurrent, one chain, and chains of several solves
+        batch = hx.Batch(ops, bs, xs, rtol=1e-10, lanes=lanes)
+        for rep in range(2):  # the bound graph is reusable
+            for x in xs:
+                x.fill_(float("nan"))
+            infos = batch.solve()
+            for (x_ref, info), x, bi in zip(refs, xs, infos):
+                assert bi["status"] == 0 and bi["iterations"] == info["iterations"]
+                assert bi["true_rel_residual"] <= 1.01e-10
+                assert rel_err(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-14
+        del batch
 
 
 def test_batch_reports_failures():
