@@ -30,11 +30,13 @@ unsigned grid_of(long long n) {
 #define MG_STRIDE(i, n) \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
+// grids hold fewer than 2^31 nodes (the element vectors are int32-indexed): 32-bit index math
 __device__ __forceinline__ void coords(const HxGrid& g, long long i, int& x, int& y, int& z) {
-  x = (int)(i % g.mx);
-  const long long r = i / g.mx;
-  y = (int)(r % g.my);
-  z = (int)(r / g.my);
+  const unsigned u = (unsigned)i, mx = (unsigned)g.mx, my = (unsigned)g.my;
+  const unsigned r = u / mx;
+  x = (int)(u - r * mx);
+  z = (int)(r / my);
+  y = (int)(r - (unsigned)z * my);
 }
 
 __device__ __forceinline__ bool inside(const HxGrid& g, int x, int y, int z) {
@@ -68,10 +70,21 @@ struct StencilRows {
   __device__ __forceinline__ double dot(long long i, const double* __restrict__ x) const {
     int ix, iy, iz;
     coords(g, i, ix, iy, iz);
+    const long long sy = g.mx, sz = (long long)g.mx * g.my;
     double s = 0.0;
-    for (int k = 0; k < 27; ++k) {
-      const int jx = ix + k % 3 - 1, jy = iy + (k / 3) % 3 - 1, jz = iz + k / 9 - 1;
-      if (inside(g, jx, jy, jz)) s += __ldg(val + (long long)k * g.n + i) * __ldg(x + index(g, jx, jy, jz));
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      if (iz + dz < 0 || iz + dz >= g.mz) continue;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        if (iy + dy < 0 || iy + dy >= g.my) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (ix + dx < 0 || ix + dx >= g.mx) continue;
+          const int k = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+          s += __ldg(val + (long long)k * g.n + i) * __ldg(x + i + dx + dy * sy + dz * sz);
+        }
+      }
     }
     return s;
   }
