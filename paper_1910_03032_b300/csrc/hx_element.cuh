@@ -706,12 +706,13 @@ struct Config {
   // elements per block of the operator kernel (3 q^3 values each: ~40-75 KB per block);
   // FP32 blocks take twice the elements while the block stays within 1024 threads
   static constexpr int NE_D = P == 1 ? 64 : P == 2 ? 32 : P == 3 ? 16 : P == 4 ? 8 : P == 5 ? 6 : P == 6 ? 4 : P == 7 ? 3 : 2;
-  static constexpr int NE = (sizeof(Real) == 4 && 2 * NE_D * Q * Q <= 1024) ? 2 * NE_D : NE_D;
+  static constexpr int NE = (sizeof(Real) == 4) ? (NE_D > 1 ? NE_D / 2 : 1) : NE_D;
   // one thread per z-column, rounded up to whole warps
   static constexpr int NT = ((NE * Q * Q + 31) / 32) * 32;
   static_assert(NT <= 1024, "block too large");
   // resident blocks per SM the register budget is sized for (shared memory allows at least this)
-  static constexpr int MINB = (sizeof(Real) == 8 && P >= 7) ? 3 : NT >= 512 ? 2 : NT >= 384 ? 3 : 4;
+  static constexpr int MINB_F = 65536 / (NT * 64) < 2 ? 2 : 65536 / (NT * 64) > 16 ? 16 : 65536 / (NT * 64);
+  static constexpr int MINB = (sizeof(Real) == 4) ? MINB_F : (P >= 7) ? 3 : NT >= 512 ? 2 : NT >= 384 ? 3 : 4;
   static constexpr int NE_DIAG = P <= 2 ? 8 : P <= 4 ? 2 : 1;
 };
 
