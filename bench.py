@@ -620,6 +620,39 @@ def run_precond(hx, torch, args):
     return out
 
 
+def run_vcycle(args):
+    """The LOR multigrid preconditioner alone: one V-cycle (smoothing degree 2) against one
+    high-order apply on the pure-Neumann Poisson of an N^3, Q_p mesh (the projection step's
+    pressure solve); CUDA events, 3 warm-up calls, 10 timed."""
+    import torch
+    import paper_1910_03032_b300 as hx
+    N, p = args.n, args.p
+    V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED)
+    mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=0)
+    op = hx.Operator(mesh, 0.0, 1.0)
+    r = torch.as_tensor(S.uniform_pm1(5, mesh.n_dof), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op.set_preconditioner(hx.HX_PREC_LOR_MG, 2)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, fn in (("vcycle_ms", lambda: op.precond_apply(r)), ("apply_ms", lambda: op.apply(r, constrained=True))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(10):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / 10
+    print(json.dumps({"probe": "lor_multigrid_vcycle", "mesh": f"{N}^3", "p": p, "n_dof": mesh.n_dof,
+                      "setup_s": t_setup, **out}), flush=True)
+
+
 def run_sweep(hx, torch):
     """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
     out = []
@@ -661,6 +694,8 @@ def main():
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--batch", action="store_true", help="add the batched-solve measurement (64 instances; projection-step set)")
     ap.add_argument("--precond", action="store_true", help="add the preconditioner comparison (Jacobi vs LOR)")
+    ap.add_argument("--vcycle", action="store_true",
+                    help="time one LOR multigrid V-cycle against one apply (pure-Neumann Poisson, --p, --n) and exit")
     ap.add_argument("--grad", action="store_true", help="add the adjoint-gradient measurement (32^3, p = 4)")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
@@ -672,6 +707,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
+    if args.vcycle:
+        run_vcycle(args)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)

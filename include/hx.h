@@ -310,10 +310,12 @@ HX_API hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream);
  * when it was created.
  * Errors: HX_ERR_ARG (unknown kind, degree out of range, HX_PREC_COLLOCATED_MASS with
  * alpha <= 0, also from a later hx_op_set_coefficients with alpha <= 0);
- * HX_ERR_UNSUPPORTED (HX_PREC_LOR on an operator with a nu field, or a LOR row with
- * more than 64 distinct columns; mixed-precision solves reject HX_PREC_LOR).
- * The first HX_PREC_LOR selection allocates and builds the sparsity pattern (one
- * synchronization of `stream`); later calls are stream-ordered.
+ * HX_ERR_UNSUPPORTED (a LOR form on an operator with a nu field, a LOR row with more
+ * than 64 distinct columns, HX_PREC_LOR_MG on a mesh without a logical grid;
+ * mixed-precision solves reject the LOR forms).
+ * The first selection of a LOR form allocates and builds the sparsity pattern (one
+ * synchronization of `stream`) and, for HX_PREC_LOR_MG, the grid hierarchy; later calls
+ * are stream-ordered.
  */
 HX_API hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream);
 

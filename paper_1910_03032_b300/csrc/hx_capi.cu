@@ -103,7 +103,9 @@ struct hx_op {
   bool graph_failed = false;
   long long launches = 0;  // kernels enqueued by this operator so far (graph replays included)
   // FP32 inner solver of the mixed-precision refinement (allocated at the first mixed solve)
-  float* factors32 = nullptr;  // [E][7][Q3] FP32 rounding of the stored factors
+  float* factors32 = nullptr;  // [E][7][Q3] FP32 rounding of the stored factors (+16 bytes: the bulk
+                               // copies of the element kernel round their end up to 16 bytes)
+  int* kerr = nullptr;         // device flag: a kernel's bounded wait gave up
   float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
   double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual
   HxCgState* st32 = nullptr;
@@ -117,6 +119,10 @@ struct hx_op {
   // preconditioner: HX_PREC_JACOBI (dinv = 1 / diag A) or HX_PREC_COLLOCATED_MASS (1 / (alpha Mc))
   int prec = HX_PREC_JACOBI;
   double* pdiag = nullptr;      // [n_dof] alpha Mc (collocated mass)
+  // the FP64 diagonal and the inverse preconditioner diagonal follow the coefficients lazily:
+  // computed when a call needs them (a mixed-precision solve needs neither)
+  bool diag_stale = true;
+  bool dinv_stale = true;
   bool has_field = false;       // the coefficients include a per-point nu field
   // low-order refined operator (Sec. 5.2) and its Chebyshev-Jacobi inverse (HX_PREC_LOR)
   HxLorMatrix lor = {0, nullptr, nullptr, nullptr, nullptr};
@@ -352,6 +358,7 @@ HxApplyArgs apply_args(const hx_op* op, const double* x, int constrained, const 
   a.nu = op->nu;
   a.constrained = constrained;
   a.done = done;
+  a.err = op->kerr;
   return a;
 }
 
@@ -398,6 +405,7 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->m1);
   dfree(op->vol);
   dfree(op->pdiag);
+  dfree(op->kerr);
   dfree(op->lor.off);
   dfree(op->lor.col);
   dfree(op->lor.val);
@@ -431,11 +439,47 @@ void hx_op_destroy(hx_op* op) {
 
 namespace {
 
+// HX_ERR_CUDA when a kernel of this operator gave up a bounded wait since the last check
+// (the flag is cleared).  Synchronizes s.
+hx_status check_kernel_flag(hx_op* op, cudaStream_t s) {
+  int flag = 0;
+  HX_TRY(cudaMemcpyAsync(&flag, op->kerr, sizeof(int), cudaMemcpyDeviceToHost, s), "flag read");
+  HX_TRY(cudaStreamSynchronize(s), "flag sync");
+  if (flag) {
+    HX_TRY(cudaMemsetAsync(op->kerr, 0, sizeof(int), s), "flag reset");
+    return fail(HX_ERR_CUDA, "an element kernel's wait for its staged factors timed out");
+  }
+  return HX_OK;
+}
+
 // dinv = the inverse of the preconditioner's diagonal (Dirichlet rows 1): diag(A) for
 // Jacobi, alpha Mc for the collocated mass (Sec. 5.1).  Counts its launches in *nl.
+hx_status ensure_diag(hx_op* op, cudaStream_t s, int* nl) {
+  if (!op->diag_stale) return HX_OK;
+  const hx_mesh* m = op->mesh;
+  HxDiagArgs d;
+  d.E = m->E;
+  d.factors = op->factors;
+  d.X8 = m->X8;
+  d.nu_q = op->use_field ? op->nu_q : nullptr;
+  d.alpha = op->alpha;
+  d.nu = op->nu;
+  d.dE = op->yE;
+  HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
+         "diagonal assembly");
+  *nl += 2;
+  op->diag_stale = false;
+  return HX_OK;
+}
+
 hx_status refresh_dinv(hx_op* op, cudaStream_t s, int* nl) {
   const hx_mesh* m = op->mesh;
   const double* d = op->diag;
+  if (op->prec != HX_PREC_COLLOCATED_MASS) {
+    hx_status st = ensure_diag(op, s, nl);
+    if (st) return st;
+  }
   if (op->prec == HX_PREC_COLLOCATED_MASS) {
     if (!(op->alpha > 0.0)) return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
     HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
@@ -446,7 +490,17 @@ hx_status refresh_dinv(hx_op* op, cudaStream_t s, int* nl) {
   }
   HX_TRY(hx_launch_dinv(m->n_dof, d, m->dir, op->dinv, s), "dinv");
   *nl += 1;
+  op->dinv_stale = false;
   return HX_OK;
+}
+
+// the inverse preconditioner diagonal of the current coefficients (once the solver workspace exists)
+hx_status ensure_dinv(hx_op* op, cudaStream_t s) {
+  if (!op->dinv || !op->dinv_stale) return HX_OK;
+  int nl = 0;
+  hx_status st = refresh_dinv(op, s, &nl);
+  op->launches += nl;
+  return st;
 }
 
 HxLorBuild lor_build_args(const hx_op* op) {
@@ -609,24 +663,9 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
       if (e != cudaSuccess) return cuda_fail(e, "nu copy");
     }
   }
-  HxDiagArgs d;
-  d.E = m->E;
-  d.factors = op->factors;
-  d.X8 = m->X8;
-  d.nu_q = op->use_field ? op->nu_q : nullptr;
-  d.alpha = alpha;
-  d.nu = nu;
-  d.dE = op->yE;
-  HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
-  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
-         "diagonal assembly");
-  nl += 2;
+  op->diag_stale = true;
+  op->dinv_stale = true;
   if (launches) *launches = nl;
-  if (op->dinv) {
-    hx_status st = refresh_dinv(op, s, &nl);
-    if (launches) *launches = nl;
-    if (st) return st;
-  }
   if (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) {
     hx_status st = lor_assemble(op, s, &nl);
     if (launches) *launches = nl;
@@ -659,6 +698,8 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
   do {
     if ((st = dalloc(&op->yE, (size_t)m->E * m->N3, "E-vector"))) break;
     if ((st = dalloc(&op->diag, (size_t)m->n_dof, "diagonal"))) break;
+    if ((st = dalloc(&op->kerr, 1, "kernel error flag"))) break;
+    if ((e = cudaMemsetAsync(op->kerr, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
     if ((st = dalloc(&bad, 1, "flag"))) break;
     if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
     if (geom_mode == HX_GEOM_STORED) {
@@ -712,6 +753,8 @@ hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const doubl
     return fail(HX_ERR_ARG, "on-the-fly operator created without a nu field cannot take one");
   if ((op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) && nu_q)
     return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
+  if (op->prec == HX_PREC_COLLOCATED_MASS && !(alpha > 0.0))
+    return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
   int nl = 0;
   hx_status st = setup_coefficients(op, alpha, nu, nu_q, nullptr, (cudaStream_t)stream, &nl);
   if (st == HX_OK) op->launches += nl;
@@ -749,6 +792,10 @@ hx_status hx_op_apply(hx_op* op, const double* x, double* y, int constrained, vo
 
 hx_status hx_op_diagonal(hx_op* op, double* diag, int constrained, void* stream) {
   if (!op || !diag) return fail(HX_ERR_ARG, "NULL argument");
+  int nl = 0;
+  hx_status st = ensure_diag(op, (cudaStream_t)stream, &nl);
+  op->launches += nl;
+  if (st) return st;
   HX_TRY(hx_launch_masked_copy(op->mesh->n_dof, op->diag, op->mesh->dir, constrained, 1.0, diag,
                                (cudaStream_t)stream),
          "diagonal copy");
@@ -813,10 +860,8 @@ hx_status ensure_solver(hx_op* op) {
   HX_TRY(cudaEventCreateWithFlags(&op->ev, cudaEventDisableTiming), "solver event");
   HX_TRY(cudaMemsetAsync(op->st, 0, sizeof(HxCgState), op->stream), "state init");
   HX_TRY(cudaMemsetAsync(op->counters, 0, 2 * sizeof(unsigned int), op->stream), "counter init");
-  int nl = 0;
-  s = refresh_dinv(op, op->stream, &nl);
-  op->launches += nl;
-  return s;
+  op->dinv_stale = true;  // computed by the first call that needs it
+  return HX_OK;
 }
 
 // One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
@@ -913,6 +958,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   // order after the caller's prior work on `user`
   HX_TRY(cudaEventRecord(op->ev, user), "event record");
   HX_TRY(cudaStreamWaitEvent(st, op->ev, 0), "stream wait");
+  if ((s = ensure_dinv(op, st))) return s;
   const HxCgBuffers buf = cg_buffers(op);
   const long long launches0 = op->launches;
   if (op->singular) {
@@ -1042,6 +1088,7 @@ HxApplyArgsF apply_args32(const hx_op* op, const float* x, const int* done) {
   a.nu = op->nu;
   a.constrained = 1;
   a.done = done;
+  a.err = op->kerr;
   return a;
 }
 
@@ -1086,7 +1133,7 @@ hx_status ensure_mixed(hx_op* op) {
         (s = dalloc(&op->rn2, 1, "residual norm")) || (s = dalloc(&op->st32, 1, "FP32 state")))
       return s;
     if (op->geom == HX_GEOM_STORED &&
-        (s = dalloc(&op->factors32, (size_t)m->E * 7 * m->q * m->q * m->q, "FP32 factors")))
+        (s = dalloc(&op->factors32, (size_t)m->E * 7 * m->q * m->q * m->q + 4, "FP32 factors")))
       return s;
     HX_TRY(cudaMemsetAsync(op->st32, 0, sizeof(HxCgState), op->stream), "FP32 state init");
   }
@@ -1094,8 +1141,30 @@ hx_status ensure_mixed(hx_op* op) {
     if (op->geom == HX_GEOM_STORED)
       HX_TRY(hx_launch_to_float((long long)m->E * 7 * m->q * m->q * m->q, op->factors, op->factors32, op->stream),
              "FP32 factors");
-    HX_TRY(hx_launch_to_float(n, op->dinv, op->dinv32, op->stream), "FP32 dinv");
-    op->launches += (op->geom == HX_GEOM_STORED) ? 2 : 1;
+    if (op->prec == HX_PREC_JACOBI) {
+      // the inner solver's Jacobi diagonal: the diagonal of the FP32 operator, computed in FP32
+      static const hx_diag32_launcher t[] = {nullptr, hx_launch_diag32_p1, hx_launch_diag32_p2, hx_launch_diag32_p3,
+                                             hx_launch_diag32_p4, hx_launch_diag32_p5, hx_launch_diag32_p6,
+                                             hx_launch_diag32_p7, hx_launch_diag32_p8};
+      HxDiagArgsF d;
+      d.E = m->E;
+      d.factors = op->factors32;
+      d.X8 = m->X8;
+      d.nu_q = op->use_field ? op->nu_q : nullptr;
+      d.alpha = op->alpha;
+      d.nu = op->nu;
+      d.dE = op->yE32;
+      HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
+      HX_TRY(hx_launch_assemble32(n, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
+             "FP32 diagonal assembly");
+      HX_TRY(hx_launch_dinv32(n, op->Ap32, m->dir, op->dinv32, op->stream), "FP32 dinv");
+      op->launches += 3;
+    } else {
+      if ((s = ensure_dinv(op, op->stream))) return s;
+      HX_TRY(hx_launch_to_float(n, op->dinv, op->dinv32, op->stream), "FP32 dinv");
+      op->launches += 1;
+    }
+    op->launches += (op->geom == HX_GEOM_STORED) ? 1 : 0;
     op->mixed_stale = false;
   }
   return HX_OK;
@@ -1230,6 +1299,7 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
   }
   HX_TRY(cudaMemcpyAsync(x, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, st), "solution copy");
   HX_TRY(cudaStreamSynchronize(st), "solver sync");
+  if ((s = check_kernel_flag(op, st))) return s;
   hx_solve_info inf;
   inf.iterations = inner_total;
   inf.status = status;
@@ -1433,6 +1503,10 @@ hx_status hx_batch_solve(hx_batch* B, void* stream, hx_solve_info* infos) {
   if (!B) return fail(HX_ERR_ARG, "batch is NULL");
   HX_TRY(cudaEventRecord(B->ev, (cudaStream_t)stream), "event record");
   HX_TRY(cudaStreamWaitEvent(B->stream, B->ev, 0), "stream wait");
+  for (int i = 0; i < B->n; ++i) {  // inverse diagonals of the operators' current coefficients
+    hx_status st = ensure_dinv(B->ops[i], B->stream);
+    if (st) return st;
+  }
   HX_TRY(cudaGraphLaunch(B->exec, B->stream), "batch graph launch");
   for (int i = 0; i < B->n; ++i) {
     HX_TRY(cudaMemcpyAsync(B->st_host + i, B->ops[i]->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, B->stream),
@@ -1547,8 +1621,8 @@ hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream
     op->cheb.degree = degree;
     op->lor_collocated = (kind == HX_PREC_LOR_MC || kind == HX_PREC_LOR_MG) ? 1 : 0;
     st = lor_assemble(op, s, &nl);
-  } else if (op->dinv) {
-    st = refresh_dinv(op, s, &nl);
+  } else {
+    op->dinv_stale = true;
   }
   op->launches += nl;
   return st;
@@ -1559,6 +1633,7 @@ hx_status hx_op_precond_apply(hx_op* op, const double* r, double* z, void* strea
   hx_status st = ensure_solver(op);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((st = ensure_dinv(op, op->stream))) return st;
   // the solver workspace is set up on the solver stream: order after it
   HX_TRY(cudaEventRecord(op->ev, op->stream), "event record");
   HX_TRY(cudaStreamWaitEvent(s, op->ev, 0), "stream wait");

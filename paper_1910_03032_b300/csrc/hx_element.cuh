@@ -196,6 +196,47 @@ __device__ __forceinline__ Real point_factors(const Real (&j0)[3], const Real (&
 }
 
 // ---------------------------------------------------------------------------
+// bulk asynchronous copies (TMA engine) into shared memory, completed on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  // make the initialized barrier visible to the asynchronous (bulk-copy) proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase 0 of `bar` with a bound on the attempts (each try_wait itself suspends
+// for a while); false when the bound was reached.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, 0u)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // shared-memory layout of one element's q^3 region: [z][y][x] with row stride
 // SY (q rounded up to odd, so x-line tasks of consecutive threads fall in
 // different banks) and plane stride SZ = q SY
@@ -256,15 +297,33 @@ __global__ void __launch_bounds__(NT, MINB)
   constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q;
   constexpr int SY = Lt::SY, SZ = Lt::SZ, RG = Lt::RG, R3 = Lt::R3;
   constexpr int CQ = (Q + 1) / 2, CN = (N + 1) / 2;
+  // FP32 stored factors are staged in shared memory by one bulk copy (TMA) per block, issued
+  // before the forward contractions and waited for in the pointwise stage.  For p > 4 the
+  // staging buffer would cut the resident blocks per SM, which costs more than it saves.
+  constexpr bool STAGE = Lt::F32 && GEOM == HX_KGEOM_STORED && P <= 4;
+  constexpr int FE = 7 * Q3;  // factors per element
   static_assert(NT >= NE * Q2, "one thread per z-column");
   if (A.done != nullptr && *(volatile const int*)A.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long fbar;  // completion barrier of the factor copy
   Real* smem = reinterpret_cast<Real*>(smem_raw);
   Real* geo = smem + NE * R3;  // on-the-fly: NE x 24 map coefficients
+  Real* sf = smem + ((NE * R3 + 3) & ~3);  // staged factors (16-byte aligned)
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
+  // the copy starts at the 16-byte boundary at or below element e0's first factor
+  const int foff = STAGE ? (int)(((e0 * FE * (long long)sizeof(Real)) & 15) / (long long)sizeof(Real)) : 0;
 
-  if (GEOM == HX_KGEOM_STORED) {
+  if (STAGE) {
+    if (tid == 0) {
+      const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
+      const long long b0 = e0 * FE * (long long)sizeof(Real), b1 = (e0 + nel) * FE * (long long)sizeof(Real);
+      const long long a0 = b0 & ~15LL, a1 = (b1 + 15) & ~15LL;  // the factor array has 16 bytes of slack
+      mbar_init(&fbar, 1);
+      mbar_expect_tx(&fbar, (unsigned)(a1 - a0));
+      bulk_load(sf, reinterpret_cast<const char*>(A.factors) + a0, (unsigned)(a1 - a0), &fbar);
+    }
+  } else if (GEOM == HX_KGEOM_STORED) {
     // pull this block's factors toward L2 while the forward contractions run
     const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
     const char* base = reinterpret_cast<const char*>(A.factors + e0 * 7 * Q3);
@@ -347,6 +406,7 @@ __global__ void __launch_bounds__(NT, MINB)
   // 5. columns: pointwise v = m u (into D, over u), w = G grad u; then Dh^T along z of
   //    w_3 (folded parts kept in registers)
   Real Et[CQ], Ot[CQ];
+  if (STAGE && owner && !mbar_wait_bounded(&fbar) && A.err) atomicExch(A.err, 1);
   if (owner) {
     const long long e = e0 + cel;
     Real* Dc = smem + cel * R3 + cs;
@@ -357,7 +417,16 @@ __global__ void __launch_bounds__(NT, MINB)
     for (int kq = 0; kq < Q; ++kq) {
       const int pt = kq * Q2 + c;
       Real f[7];
-      if (GEOM == HX_KGEOM_STORED) {
+      if (STAGE) {
+        if (e < A.E) {
+          const Real* fe = sf + foff + cel * FE + pt;
+#pragma unroll
+          for (int m = 0; m < 7; ++m) f[m] = fe[m * Q3];
+        } else {
+#pragma unroll
+          for (int m = 0; m < 7; ++m) f[m] = Real(0);
+        }
+      } else if (GEOM == HX_KGEOM_STORED) {
         if (e < A.E) {
           const Real* fe = A.factors + e * 7 * Q3 + pt;
 #pragma unroll
@@ -422,6 +491,8 @@ __global__ void __launch_bounds__(NT, MINB)
   }
   __syncthreads();
   transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
+  // no copy may still be writing this block's shared memory when it exits
+  if (STAGE && tid == 0) mbar_wait_bounded(&fbar);
 }
 
 // Load vector: bE = (B x B x B)^T (w detJ f) per element.
@@ -586,15 +657,16 @@ __global__ void __launch_bounds__(NT) grad_kernel(const __grid_constant__ HxTabl
 // diag[k][j][i] = sum_{c,b,a} m (BB_ai BB_bj BB_ck) + G00 DD_ai BB_bj BB_ck + G11 BB_ai DD_bj BB_ck
 //   + G22 BB_ai BB_bj DD_ck + 2 G01 BD_ai BD_bj BB_ck + 2 G02 BD_ai BB_bj BD_ck + 2 G12 BB_ai BD_bj BD_ck
 // with BB = B.B, DD = D.D, BD = B.D (entrywise) and factors at point (a, b, c).
-template <int P, int Q, int NE, int NT, int GEOM, bool NUF>
-__global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTables T, const HxDiagArgs A) {
+template <typename Real, int P, int Q, int NE, int NT, int GEOM, bool NUF>
+__global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTablesT<Real> T, const HxDiagArgsT<Real> A) {
   constexpr int N = P + 1, N3 = N * N * N, Q3 = Q * Q * Q;
   constexpr int F1 = 7 * Q * Q * N, F2 = 7 * Q * N * N;
   constexpr int FA = (7 * Q3 > F2) ? 7 * Q3 : F2;  // factors, later reused by stage-2 output
   constexpr int PER = FA + F1;
-  extern __shared__ double smem[];
-  double* tab = smem + NE * PER;  // BB, DD, BD tables: 3 q n
-  double* geo = tab + 3 * Q * N;  // NE x 24
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* smem = reinterpret_cast<Real*>(smem_raw);
+  Real* tab = smem + NE * PER;  // BB, DD, BD tables: 3 q n
+  Real* geo = tab + 3 * Q * N;  // NE x 24
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
   for (int t = tid; t < Q * N; t += NT) {
@@ -615,36 +687,36 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
   for (int t = tid; t < NE * Q3; t += NT) {
     const int el = t / Q3, pt = t - el * Q3;
     const long long e = e0 + el;
-    double f[7] = {0, 0, 0, 0, 0, 0, 0};
+    Real f[7] = {0, 0, 0, 0, 0, 0, 0};
     if (e < A.E) {
       if (GEOM == HX_KGEOM_STORED) {
 #pragma unroll
         for (int c = 0; c < 7; ++c) f[c] = A.factors[(e * 7 + c) * Q3 + pt];
       } else {
         const int iq = pt % Q, jq = (pt / Q) % Q, kq = pt / (Q * Q);
-        double j0[3], j1[3], j2[3];
+        Real j0[3], j1[3], j2[3];
         trilinear_jacobian(geo + el * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
-        const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
-        const double nu = NUF ? A.nu_q[e * Q3 + pt] : A.nu;
-        point_factors(j0, j1, j2, A.alpha * w, nu * w, f);
+        const Real w = T.wq[iq] * T.wq[jq] * T.wq[kq];
+        const Real nu = Real(NUF ? A.nu_q[e * Q3 + pt] : A.nu);
+        point_factors(j0, j1, j2, Real(A.alpha) * w, nu * w, f);
       }
     }
 #pragma unroll
     for (int c = 0; c < 7; ++c) smem[el * PER + c * Q3 + pt] = f[c];
   }
   __syncthreads();
-  const double* BB = tab;
-  const double* DD = tab + Q * N;
-  const double* BD = tab + 2 * Q * N;
+  const Real* BB = tab;
+  const Real* DD = tab + Q * N;
+  const Real* BD = tab + 2 * Q * N;
   // stage 1: contract a -> T1[f][c][b][i]
   for (int t = tid; t < NE * Q * Q; t += NT) {
     const int el = t / (Q * Q), cb = t - el * (Q * Q);
-    const double* F = smem + el * PER + cb * Q;
-    double* T1 = smem + el * PER + FA + cb * N;
+    const Real* F = smem + el * PER + cb * Q;
+    Real* T1 = smem + el * PER + FA + cb * N;
     for (int i = 0; i < N; ++i) {
-      double s[7] = {0, 0, 0, 0, 0, 0, 0};
+      Real s[7] = {0, 0, 0, 0, 0, 0, 0};
       for (int a = 0; a < Q; ++a) {
-        const double bb = BB[a * N + i], dd = DD[a * N + i], bd = BD[a * N + i];
+        const Real bb = BB[a * N + i], dd = DD[a * N + i], bd = BD[a * N + i];
         s[0] += bb * F[0 * Q3 + a];
         s[1] += dd * F[1 * Q3 + a];
         s[2] += bd * F[2 * Q3 + a];
@@ -661,13 +733,13 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
   for (int t = tid; t < NE * Q * N; t += NT) {
     const int el = t / (Q * N), r = t - el * (Q * N);
     const int c = r / N, i = r - c * N;
-    const double* T1 = smem + el * PER + FA + c * Q * N + i;
-    double* T2 = smem + el * PER + c * N * N + i;
+    const Real* T1 = smem + el * PER + FA + c * Q * N + i;
+    Real* T2 = smem + el * PER + c * N * N + i;
     for (int j = 0; j < N; ++j) {
-      double s[7] = {0, 0, 0, 0, 0, 0, 0};
+      Real s[7] = {0, 0, 0, 0, 0, 0, 0};
       for (int b = 0; b < Q; ++b) {
-        const double bb = BB[b * N + j], dd = DD[b * N + j], bd = BD[b * N + j];
-        const double* src = T1 + b * N;
+        const Real bb = BB[b * N + j], dd = DD[b * N + j], bd = BD[b * N + j];
+        const Real* src = T1 + b * N;
         s[0] += bb * src[0 * Q * Q * N];
         s[1] += bb * src[1 * Q * Q * N];
         s[2] += bd * src[2 * Q * Q * N];
@@ -685,14 +757,14 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
     const int el = t / N3, l = t - el * N3;
     const int k = l / (N * N), ji = l - k * N * N;
     const long long e = e0 + el;
-    const double* T2 = smem + el * PER + ji;
-    double s = 0.0;
+    const Real* T2 = smem + el * PER + ji;
+    Real s = Real(0);
     for (int c = 0; c < Q; ++c) {
-      const double bb = BB[c * N + k], dd = DD[c * N + k], bd = BD[c * N + k];
-      const double* src = T2 + c * N * N;
+      const Real bb = BB[c * N + k], dd = DD[c * N + k], bd = BD[c * N + k];
+      const Real* src = T2 + c * N * N;
       const int st = Q * N * N;
-      s += bb * (src[0] + src[1 * st] + src[4 * st]) + dd * src[6 * st] + 2.0 * bd * (src[3 * st] + src[5 * st]) +
-           2.0 * bb * src[2 * st];
+      s += bb * (src[0] + src[1 * st] + src[4 * st]) + dd * src[6 * st] + Real(2) * bd * (src[3 * st] + src[5 * st]) +
+           Real(2) * bb * src[2 * st];
     }
     if (e < A.E) A.dE[e * N3 + l] = s;
   }
@@ -716,11 +788,27 @@ struct Config {
   static constexpr int NE_DIAG = P <= 2 ? 8 : P <= 4 ? 2 : 1;
 };
 
+// Block shape of the operator kernel.  FP32 with on-the-fly geometry keeps the larger blocks
+// (twice the FP64 element count): its per-element map set-up amortizes better over them.
+template <int P, int Q, typename Real, int GEOM>
+struct ApplyConfig {
+  using C = Config<P, Q, Real>;
+  static constexpr bool BIG = sizeof(Real) == 4 && GEOM == HX_KGEOM_ONTHEFLY && 2 * C::NE_D * Q * Q <= 1024;
+  static constexpr int NE = BIG ? 2 * C::NE_D : C::NE;
+  static constexpr int NT = BIG ? ((NE * Q * Q + 31) / 32) * 32 : C::NT;
+  static constexpr int MINB = BIG ? (NT >= 512 ? 2 : NT >= 384 ? 3 : 4) : C::MINB;
+};
+
 template <typename Real, int P, int Q, int GEOM, bool NUF>
 cudaError_t launch_apply_impl(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, cudaStream_t s) {
-  using C = Config<P, Q, Real>;
+  using C = ApplyConfig<P, Q, Real, GEOM>;
   constexpr int NE = C::NE, NT = C::NT, MINB = C::MINB;
-  const size_t shmem = sizeof(Real) * (size_t)(NE * Layout<Q, Real>::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+  using Lt = Layout<Q, Real>;
+  constexpr bool STAGE = Lt::F32 && GEOM == HX_KGEOM_STORED && P <= 4;  // the kernel stages the factors
+  // the copy rounds its start down and its end up to 16 bytes: up to 6 more words
+  const size_t words = STAGE ? (size_t)((NE * Lt::R3 + 3) & ~3) + (size_t)NE * 7 * Q * Q * Q + 8
+                             : (size_t)NE * Lt::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0);
+  const size_t shmem = sizeof(Real) * words;
   auto k = apply_kernel<Real, P, Q, NE, NT, MINB, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
@@ -737,13 +825,13 @@ cudaError_t launch_apply_q(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A
   return launch_apply_impl<Real, P, Q, HX_KGEOM_ONTHEFLY, false>(T, A, s);
 }
 
-template <int P, int Q, int GEOM, bool NUF>
-cudaError_t launch_diag_impl(const HxTables& T, const HxDiagArgs& A, cudaStream_t s) {
+template <typename Real, int P, int Q, int GEOM, bool NUF>
+cudaError_t launch_diag_impl(const HxTablesT<Real>& T, const HxDiagArgsT<Real>& A, cudaStream_t s) {
   constexpr int N = P + 1, NE = Config<P, Q>::NE_DIAG, NT = 128;
   constexpr int F1 = 7 * Q * Q * N, F2 = 7 * Q * N * N;
   constexpr int FA = (7 * Q * Q * Q > F2) ? 7 * Q * Q * Q : F2;
-  const size_t shmem = sizeof(double) * (size_t)(NE * (FA + F1) + 3 * Q * N + NE * 24);
-  auto k = diag_kernel<P, Q, NE, NT, GEOM, NUF>;
+  const size_t shmem = sizeof(Real) * (size_t)(NE * (FA + F1) + 3 * Q * N + NE * 24);
+  auto k = diag_kernel<Real, P, Q, NE, NT, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
   const long long blocks = (A.E + NE - 1) / NE;
@@ -752,11 +840,11 @@ cudaError_t launch_diag_impl(const HxTables& T, const HxDiagArgs& A, cudaStream_
   return cudaGetLastError();
 }
 
-template <int P, int Q>
-cudaError_t launch_diag_q(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {
-  if (geom == HX_KGEOM_STORED) return launch_diag_impl<P, Q, HX_KGEOM_STORED, false>(T, A, s);
-  if (A.nu_q) return launch_diag_impl<P, Q, HX_KGEOM_ONTHEFLY, true>(T, A, s);
-  return launch_diag_impl<P, Q, HX_KGEOM_ONTHEFLY, false>(T, A, s);
+template <typename Real, int P, int Q>
+cudaError_t launch_diag_q(const HxTablesT<Real>& T, const HxDiagArgsT<Real>& A, int geom, cudaStream_t s) {
+  if (geom == HX_KGEOM_STORED) return launch_diag_impl<Real, P, Q, HX_KGEOM_STORED, false>(T, A, s);
+  if (A.nu_q) return launch_diag_impl<Real, P, Q, HX_KGEOM_ONTHEFLY, true>(T, A, s);
+  return launch_diag_impl<Real, P, Q, HX_KGEOM_ONTHEFLY, false>(T, A, s);
 }
 
 template <int P, int Q>
@@ -800,8 +888,13 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_diag_p##P(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {     \
-    if (T.q == P + 1) return hx::launch_diag_q<P, P + 1>(T, A, geom, s);                                  \
-    if (T.q == P + 2) return hx::launch_diag_q<P, P + 2>(T, A, geom, s);                                  \
+    if (T.q == P + 1) return hx::launch_diag_q<double, P, P + 1>(T, A, geom, s);                                  \
+    if (T.q == P + 2) return hx::launch_diag_q<double, P, P + 2>(T, A, geom, s);                                  \
+    return cudaErrorInvalidValue;                                                                          \
+  }                                                                                                       \
+  cudaError_t hx_launch_diag32_p##P(const HxTablesF& T, const HxDiagArgsF& A, int geom, cudaStream_t s) {     \
+    if (T.q == P + 1) return hx::launch_diag_q<float, P, P + 1>(T, A, geom, s);                                  \
+    if (T.q == P + 2) return hx::launch_diag_q<float, P, P + 2>(T, A, geom, s);                                  \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_grad_p##P(const HxTables& T, const HxGradArgs& A, cudaStream_t s) {               \

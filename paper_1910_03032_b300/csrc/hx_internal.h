@@ -22,19 +22,23 @@ struct HxApplyArgsT {
   double alpha, nu;       // Helmholtz coefficients (on-the-fly geometry)
   int constrained;        // 1: Dirichlet DoFs of x read as zero
   const int* done;        // optional device flag: kernel returns at once when *done != 0
+  int* err;               // optional device flag, set to 1 when a bounded wait gives up
 };
 typedef HxApplyArgsT<double> HxApplyArgs;
 typedef HxApplyArgsT<float> HxApplyArgsF;
 
 // Arguments of the diagonal kernel (sum-factorized diag of the element matrices).
-struct HxDiagArgs {
+template <typename T>
+struct HxDiagArgsT {
   long long E;
-  const double* factors;  // stored geometry or null
+  const T* factors;       // stored geometry or null
   const double* X8;
   const double* nu_q;
   double alpha, nu;
-  double* dE;             // [E][n^3] element diagonals
+  T* dE;                  // [E][n^3] element diagonals
 };
+typedef HxDiagArgsT<double> HxDiagArgs;
+typedef HxDiagArgsT<float> HxDiagArgsF;
 
 // Arguments of the load-vector kernel: bE = B^T (w detJ f) per element.
 struct HxLoadArgs {
@@ -60,6 +64,7 @@ enum { HX_KGEOM_STORED = 0, HX_KGEOM_ONTHEFLY = 1 };
 // Per-order launchers (one translation unit per p; q in {p+1, p+2}).
 typedef cudaError_t (*hx_apply_launcher)(const HxTables&, const HxApplyArgs&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_diag_launcher)(const HxTables&, const HxDiagArgs&, int geom, cudaStream_t);
+typedef cudaError_t (*hx_diag32_launcher)(const HxTablesF&, const HxDiagArgsF&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cudaStream_t);
 typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cudaStream_t);
@@ -67,6 +72,7 @@ typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cuda
 #define HX_DECLARE_ORDER(P)                                                                        \
   cudaError_t hx_launch_apply_p##P(const HxTables&, const HxApplyArgs&, int, cudaStream_t);       \
   cudaError_t hx_launch_diag_p##P(const HxTables&, const HxDiagArgs&, int, cudaStream_t);         \
+  cudaError_t hx_launch_diag32_p##P(const HxTablesF&, const HxDiagArgsF&, int, cudaStream_t);     \
   cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);              \
   cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, cudaStream_t);  \
   cudaError_t hx_launch_grad_p##P(const HxTables&, const HxGradArgs&, cudaStream_t);
@@ -139,6 +145,7 @@ cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, do
                             cudaStream_t s);
 cudaError_t hx_launch_scale(long long n, const double* d, const double* r, double* z, cudaStream_t s);
 cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s);
+cudaError_t hx_launch_dinv32(long long n, const float* diag, const unsigned char* dir, float* dinv, cudaStream_t s);
 cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
                                   double value, double* dst, cudaStream_t s);
 template <typename Real>

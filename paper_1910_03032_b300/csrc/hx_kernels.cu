@@ -543,6 +543,16 @@ cudaError_t hx_launch_scale(long long n, const double* d, const double* r, doubl
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(kThreads) dinv32_kernel(long long n, const float* __restrict__ diag,
+                                                           const unsigned char* __restrict__ dir, float* __restrict__ dinv) {
+  HX_GRID_STRIDE(g, n) { dinv[g] = dir[g] ? 1.0f : 1.0f / diag[g]; }
+}
+
+cudaError_t hx_launch_dinv32(long long n, const float* diag, const unsigned char* dir, float* dinv, cudaStream_t s) {
+  dinv32_kernel<<<grid_for(n), kThreads, 0, s>>>(n, diag, dir, dinv);
+  return cudaGetLastError();
+}
+
 cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s) {
   dinv_kernel<<<grid_for(n), kThreads, 0, s>>>(n, diag, dir, dinv);
   return cudaGetLastError();
