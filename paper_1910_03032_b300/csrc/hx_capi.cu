@@ -135,6 +135,7 @@ struct hx_op {
   // geometric multigrid on the LOR matrix (HX_PREC_LOR_MG, structured meshes)
   HxMg mg = {};
   bool mg_built = false;
+  double* mg_mc = nullptr;  // [n_dof] alpha Mc for the multigrid's fine stencil
 };
 
 namespace {
@@ -421,17 +422,18 @@ void hx_op_destroy(hx_op* op) {
     dfree(L.r);
     dfree(L.coef);
     dfree(L.val);
+    dfree(L.dinv);
+    dfree(L.bound);
     if (l > 0) {
       dfree(L.dir_own);
-      dfree(L.dinv);
       dfree(L.b);
       dfree(L.x);
       dfree(L.res);
       dfree(L.d0);
       dfree(L.d1);
-      dfree(L.bound);
     }
   }
+  dfree(op->mg_mc);
   delete op;
 }
 
@@ -517,7 +519,8 @@ HxLorBuild lor_build_args(const hx_op* op) {
 
 // Values of A_LOR for the current alpha, nu (the pattern exists), its inverse diagonal, the
 // Gershgorin bound of D^-1 A_LOR and the Chebyshev coefficients.  Stream-ordered.
-hx_status lor_assemble(hx_op* op, cudaStream_t s, int* nl) {
+// CSR values of A_LOR (the Chebyshev forms and hx_op_lor_csr)
+hx_status lor_csr_values(hx_op* op, cudaStream_t s, int* nl) {
   if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
   if (!op->lor.val) return HX_OK;  // pattern not built yet: assembled when the preconditioner is selected
   const hx_mesh* m = op->mesh;
@@ -527,11 +530,27 @@ hx_status lor_assemble(hx_op* op, cudaStream_t s, int* nl) {
   HX_TRY(hx_lor_coefficients(op->lor_bound, op->cheb.degree, op->cheb.coef, s), "Chebyshev coefficients");
   *nl += 3;
   op->lor_values_set = true;
-  if (op->mg_built) {
-    HX_TRY(hx_mg_assemble(op->mg, op->lor, op->lor_bound, s), "multigrid hierarchy");
-    *nl += 3 * (op->mg.n_levels - 1) + op->mg.n_levels;
-  }
   return HX_OK;
+}
+
+// The multigrid hierarchy of the current alpha, nu: alpha Mc, the fine stencil of alpha Mc + nu K_LOR
+// assembled cell by cell, then the Galerkin levels.
+hx_status mg_values(hx_op* op, cudaStream_t s, int* nl) {
+  if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
+  const hx_mesh* m = op->mesh;
+  const int nx = (int)((m->grid[0] - 1) / m->p), ny = (int)((m->grid[1] - 1) / m->p);
+  HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->mg_mc, s),
+         "collocated mass assembly");
+  HX_TRY(hx_mg_fine(m->T, nx, ny, m->X8, op->alpha, op->nu, 1, op->mg_mc, op->mg.levels[0], s), "fine LOR stencil");
+  HX_TRY(hx_mg_assemble(op->mg, s), "multigrid hierarchy");
+  *nl += 2 + 10 + 3 * op->mg.n_levels;
+  return HX_OK;
+}
+
+hx_status lor_assemble(hx_op* op, cudaStream_t s, int* nl) {
+  if (op->prec == HX_PREC_LOR_MG) return mg_values(op, s, nl);
+  return lor_csr_values(op, s, nl);
 }
 
 // The multigrid levels of a structured mesh (allocated once; values by hx_mg_assemble).
@@ -551,9 +570,9 @@ hx_status mg_setup(hx_op* op, int smooth_degree, cudaStream_t s) {
   F.d1 = op->cheb.d1;
   M.n_levels = 1;
   if ((st = dalloc(&F.r, (size_t)F.g.n, "MG residual")) || (st = dalloc(&F.coef, 2 * HX_LOR_MAX_DEGREE, "MG coefficients")) ||
-      (st = dalloc(&F.val, 27 * (size_t)F.g.n, "MG fine stencil")))
+      (st = dalloc(&F.val, 27 * (size_t)F.g.n, "MG fine stencil")) || (st = dalloc(&F.dinv, (size_t)F.g.n, "MG dinv")) ||
+      (st = dalloc(&F.bound, 1, "MG bound")) || (st = dalloc(&op->mg_mc, (size_t)F.g.n, "MG collocated mass")))
     return st;
-  F.dinv = op->lor.dinv;
   while (M.n_levels < HX_MG_MAX_LEVELS) {
     const HxGrid& g = M.levels[M.n_levels - 1].g;
     if (!(g.mx % 2 == 1 && g.my % 2 == 1 && g.mz % 2 == 1 && g.mx >= 5 && g.my >= 5 && g.mz >= 5)) break;
@@ -573,6 +592,20 @@ hx_status mg_setup(hx_op* op, int smooth_degree, cudaStream_t s) {
     op->launches += 1;
   }
   op->mg_built = true;
+  return HX_OK;
+}
+
+// The preconditioned-residual vector and the Chebyshev workspace for `degree` steps.
+hx_status lor_workspace(hx_op* op, int degree) {
+  const long long n = op->mesh->n_dof;
+  hx_status st = HX_OK;
+  if (!op->zl) {
+    if ((st = dalloc(&op->zl, (size_t)n, "preconditioned residual")) || (st = dalloc(&op->cheb.res, (size_t)n, "cheb res")) ||
+        (st = dalloc(&op->cheb.d0, (size_t)n, "cheb d0")) || (st = dalloc(&op->cheb.d1, (size_t)n, "cheb d1")) ||
+        (st = dalloc(&op->cheb.coef, 2 * HX_LOR_MAX_DEGREE, "cheb coefficients")))
+      return st;
+  }
+  op->cheb.degree = degree;
   return HX_OK;
 }
 
@@ -628,14 +661,7 @@ hx_status lor_setup(hx_op* op, int degree, cudaStream_t s) {
     op->lor.n = n;
     op->lor_nnz = nnz;
   }
-  if (!op->zl) {
-    if ((st = dalloc(&op->zl, (size_t)n, "preconditioned residual")) || (st = dalloc(&op->cheb.res, (size_t)n, "cheb res")) ||
-        (st = dalloc(&op->cheb.d0, (size_t)n, "cheb d0")) || (st = dalloc(&op->cheb.d1, (size_t)n, "cheb d1")) ||
-        (st = dalloc(&op->cheb.coef, 2 * HX_LOR_MAX_DEGREE, "cheb coefficients")))
-      return st;
-  }
-  op->cheb.degree = degree;
-  return HX_OK;
+  return lor_workspace(op, degree);
 }
 
 // Coefficient-dependent setup, stream-ordered and allocation-free: stored
@@ -867,7 +893,7 @@ hx_status ensure_solver(hx_op* op) {
 // One CG iteration: element kernel on p, fused assembly + (p, Ap), update, direction.
 // z = M^-1 r for the preconditioners that run outside the CG kernels (LOR forms)
 cudaError_t apply_z(const hx_op* op, const double* r, double* z, const int* done, cudaStream_t s) {
-  if (op->prec == HX_PREC_LOR_MG) return hx_mg_vcycle(op->mg, op->lor, r, z, done, s);
+  if (op->prec == HX_PREC_LOR_MG) return hx_mg_vcycle(op->mg, r, z, done, s);
   return hx_lor_precondition(op->lor, op->cheb, r, z, done, s);
 }
 int z_launches(const hx_op* op) {
@@ -1605,8 +1631,11 @@ hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream
   if (lor) {
     if (degree < 1 || degree > HX_LOR_MAX_DEGREE) return fail(HX_ERR_ARG, "degree must be in [1, %d]", HX_LOR_MAX_DEGREE);
     if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
-    if ((st = lor_setup(op, degree, s))) return st;
-    if (kind == HX_PREC_LOR_MG && (st = mg_setup(op, degree, s))) return st;
+    if (kind == HX_PREC_LOR_MG) {
+      if ((st = lor_workspace(op, degree)) || (st = mg_setup(op, degree, s))) return st;
+    } else if ((st = lor_setup(op, degree, s))) {
+      return st;
+    }
   }
   // the captured CG iterations differ between the preconditioners: capture again at the next solve
   if (op->graph) {
@@ -1658,7 +1687,7 @@ hx_status hx_op_lor_csr(hx_op* op, int64_t* nnz, int64_t* row_off, int* col, dou
   if (!op->lor_values_set) {
     if (op->cheb.degree == 0) op->cheb.degree = 1;
     int nl = 0;
-    st = lor_assemble(op, s, &nl);
+    st = lor_csr_values(op, s, &nl);
     op->launches += nl;
     if (st) return st;
   }

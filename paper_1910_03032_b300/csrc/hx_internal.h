@@ -211,11 +211,11 @@ struct HxMgLevel {
   const unsigned char* dir;  // Dirichlet mask (the mesh's on the fine level)
   unsigned char* dir_own;    // coarse levels: owned mask
   double* val;               // [27][n] stencil (fine level: the LOR matrix; coarse: Galerkin)
-  double* dinv;              // coarse levels: inverse diagonal
+  double* dinv;              // inverse diagonal
   double *b, *x, *r;         // right-hand side, solution, residual (b, x: coarse levels)
   double *res, *d0, *d1;     // Chebyshev work vectors
   double* coef;              // Chebyshev coefficients of this level's smoother (coarse solver)
-  unsigned long long* bound; // coarse levels: Gershgorin bound of D^-1 A
+  unsigned long long* bound; // Gershgorin bound of D^-1 A
 };
 #define HX_MG_MAX_LEVELS 16
 struct HxMg {
@@ -226,9 +226,12 @@ struct HxMg {
   HxMgLevel levels[HX_MG_MAX_LEVELS];
 };
 cudaError_t hx_mg_coarse_dir(const HxMgLevel& F, HxMgLevel& C, cudaStream_t s);
-cudaError_t hx_mg_assemble(const HxMg& M, const HxLorMatrix& A0, const unsigned long long* bound0, cudaStream_t s);
-cudaError_t hx_mg_vcycle(const HxMg& M, const HxLorMatrix& A0, const double* r, double* z, const int* done,
-                         cudaStream_t s);
+// fine stencil of the LOR matrix (collocated = 1: alpha Mc + nu K_LOR, mc = alpha Mc assembled)
+cudaError_t hx_mg_fine(const HxTables& T, int nx, int ny, const double* X8, double alpha, double nu, int collocated,
+                       const double* mc, const HxMgLevel& L0, cudaStream_t s);
+// inverse diagonals, bounds, Galerkin levels and Chebyshev coefficients from the fine stencil
+cudaError_t hx_mg_assemble(const HxMg& M, cudaStream_t s);
+cudaError_t hx_mg_vcycle(const HxMg& M, const double* r, double* z, const int* done, cudaStream_t s);
 int hx_mg_vcycle_launches(const HxMg& M);
 // mixed-precision refinement helpers
 cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,

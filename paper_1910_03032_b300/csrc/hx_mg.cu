@@ -7,12 +7,13 @@
 // Interpolation P is trilinear in the logical indices; its rows at Dirichlet fine nodes and
 // its columns at Dirichlet coarse nodes are zero.  Coarse operators are Galerkin products
 // P^T A P, stored as 27-point stencils ([27][n], neighbour k = (dz+1) 9 + (dy+1) 3 + (dx+1)),
-// with identity rows at Dirichlet coarse nodes; the fine LOR matrix is copied into the same
-// structure-of-arrays form, so every smoother pass reads coalesced.  Smoothing: Chebyshev-Jacobi polynomials
+// with identity rows at Dirichlet coarse nodes; the fine LOR matrix is assembled straight into
+// the same structure-of-arrays form, so every smoother pass reads coalesced.  Smoothing: Chebyshev-Jacobi polynomials
 // (the paper uses ordered ILU, a sequential method); the same polynomial before and after the
 // coarse correction keeps the cycle a symmetric linear operator, as CG needs.
 #include <cuda_runtime.h>
 
+#include "hx_element.cuh"
 #include "hx_internal.h"
 
 namespace {
@@ -46,22 +47,6 @@ __device__ __forceinline__ bool inside(const HxGrid& g, int x, int y, int z) {
 __device__ __forceinline__ long long index(const HxGrid& g, int x, int y, int z) {
   return (long long)x + (long long)g.mx * ((long long)y + (long long)g.my * z);
 }
-
-// The assembled LOR matrix in CSR (read once per assembly, into the fine stencil).
-struct CsrRows {
-  const long long* off;
-  const int* col;
-  const double* val;
-  __device__ __forceinline__ double dot(long long i, const double* __restrict__ x) const {
-    double s = 0.0;
-    for (long long o = off[i]; o < off[i + 1]; ++o) s += __ldg(val + o) * __ldg(x + __ldg(col + o));
-    return s;
-  }
-  template <typename F>
-  __device__ __forceinline__ void each(long long i, F&& f) const {
-    for (long long o = off[i]; o < off[i + 1]; ++o) f((long long)col[o], val[o]);
-  }
-};
 
 // Every level: 27-point stencils on the logical grid.
 struct StencilRows {
@@ -253,20 +238,97 @@ __global__ void __launch_bounds__(kT) mg_galerkin_kernel(Rows A, HxGrid fg, cons
   }
 }
 
-// The fine LOR matrix (CSR, rows of the logical grid) as a 27-point stencil [27][n]: the
-// structure-of-arrays form the smoothers read with coalesced loads.
-__global__ void __launch_bounds__(kT) mg_csr_to_stencil_kernel(CsrRows A, HxGrid g, double* __restrict__ v27) {
+// The fine LOR stencil of a structured mesh, cell by cell.  A cell (cx, cy, cz) of the logical
+// grid is sub-element (cx mod p, cy mod p, cz mod p) of element (cx / p, cy / p, cz / p); its Q1
+// matrix (2 Gauss points per direction, the sub-element's Jacobian J_K(xi(eta)) diag(h) / 2) is
+// computed once and added into the stencil rows of its 8 corners.  Cells of one parity class
+// (ox, oy, oz) share no node, so each of the 8 passes adds without atomics, in a fixed order.
+__global__ void __launch_bounds__(kT) mg_cell_kernel(const __grid_constant__ HxTables T, HxGrid g, int nx, int ny,
+                                                     const double* __restrict__ X8,
+                                                     const unsigned char* __restrict__ dir, double am, double nu,
+                                                     int ox, int oy, int oz, double* __restrict__ v27) {
+  const double g2 = 0.57735026918962576451;  // 2-point Gauss nodes +-1/sqrt(3), weights 1
+  __shared__ double q1[8][8][4];             // Q1 shape functions and gradients at the 8 points
+  if (threadIdx.x < 64) {
+    const int qp = threadIdx.x >> 3, c = threadIdx.x & 7;
+    double f[3], sg[3];
+    for (int d = 0; d < 3; ++d) {
+      sg[d] = ((c >> d) & 1) ? 1.0 : -1.0;
+      f[d] = 0.5 * (1.0 + sg[d] * (((qp >> d) & 1) ? g2 : -g2));
+    }
+    q1[qp][c][0] = f[0] * f[1] * f[2];
+    q1[qp][c][1] = 0.5 * sg[0] * f[1] * f[2];
+    q1[qp][c][2] = 0.5 * sg[1] * f[0] * f[2];
+    q1[qp][c][3] = 0.5 * sg[2] * f[0] * f[1];
+  }
+  __syncthreads();
+  const int p = T.p;
+  const int hxn = (g.mx - 1 - ox + 1) / 2, hyn = (g.my - 1 - oy + 1) / 2, hzn = (g.mz - 1 - oz + 1) / 2;
+  const long long nc = (long long)hxn * hyn * hzn;
+  const long long sy = g.mx, sz = (long long)g.mx * g.my;
+  MG_STRIDE(t, nc) {
+    const int ix = (int)(t % hxn), iy = (int)((t / hxn) % hyn), iz = (int)(t / ((long long)hxn * hyn));
+    const int cx = 2 * ix + ox, cy = 2 * iy + oy, cz = 2 * iz + oz;
+    const int ex = cx / p, ey = cy / p, ez = cz / p;
+    const int s0 = cx - ex * p, t0 = cy - ey * p, u0 = cz - ez * p;
+    const long long e = ex + (long long)nx * (ey + (long long)ny * ez);
+    double cf[24];
+    {
+      double x8[24];
+      for (int c = 0; c < 24; ++c) x8[c] = X8[e * 24 + c];
+      hx::trilinear_coeffs(x8, cf);
+    }
+    const double hs = T.xn[s0 + 1] - T.xn[s0], ht = T.xn[t0 + 1] - T.xn[t0], hu = T.xn[u0 + 1] - T.xn[u0];
+    double a[36];  // upper triangle of the symmetric 8 x 8 cell matrix
+    for (int k = 0; k < 36; ++k) a[k] = 0.0;
+    for (int qp = 0; qp < 8; ++qp) {
+      double j0[3], j1[3], j2[3], f[7];
+      hx::trilinear_jacobian(cf, T.xn[s0] + 0.5 * (((qp & 1) ? g2 : -g2) + 1.0) * hs,
+                             T.xn[t0] + 0.5 * (((qp & 2) ? g2 : -g2) + 1.0) * ht,
+                             T.xn[u0] + 0.5 * (((qp & 4) ? g2 : -g2) + 1.0) * hu, j0, j1, j2);
+      for (int d = 0; d < 3; ++d) {
+        j0[d] *= 0.5 * hs;
+        j1[d] *= 0.5 * ht;
+        j2[d] *= 0.5 * hu;
+      }
+      hx::point_factors(j0, j1, j2, am, nu, f);
+      int k = 0;
+      for (int c = 0; c < 8; ++c) {
+        const double mc = f[0] * q1[qp][c][0];
+        const double gx = q1[qp][c][1], gy = q1[qp][c][2], gz = q1[qp][c][3];
+        const double G0 = f[1] * gx + f[2] * gy + f[3] * gz;
+        const double G1 = f[2] * gx + f[4] * gy + f[5] * gz;
+        const double G2 = f[3] * gx + f[5] * gy + f[6] * gz;
+        for (int c2 = c; c2 < 8; ++c2, ++k)
+          a[k] += mc * q1[qp][c2][0] + G0 * q1[qp][c2][1] + G1 * q1[qp][c2][2] + G2 * q1[qp][c2][3];
+      }
+    }
+    const long long base = cx + sy * cy + sz * cz;
+    for (int c = 0; c < 8; ++c) {
+      const int dxc = c & 1, dyc = (c >> 1) & 1, dzc = (c >> 2) & 1;
+      const long long i = base + dxc + sy * dyc + sz * dzc;
+      if (dir[i]) continue;
+      for (int c2 = 0; c2 < 8; ++c2) {
+        const int dx = (c2 & 1) - dxc, dy = ((c2 >> 1) & 1) - dyc, dz = ((c2 >> 2) & 1) - dzc;
+        const long long j = i + dx + sy * dy + sz * dz;
+        if (dir[j]) continue;
+        const int lo = c < c2 ? c : c2, hi = c < c2 ? c2 : c;
+        const int k = lo * 8 - lo * (lo - 1) / 2 + (hi - lo);  // position of (lo, hi) in the upper triangle
+        v27[(long long)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * g.n + i] += a[k];
+      }
+    }
+  }
+}
+
+// Identity rows at Dirichlet nodes; the collocated mass (alpha Mc) added to the centre elsewhere.
+__global__ void __launch_bounds__(kT) mg_fine_finish_kernel(HxGrid g, const unsigned char* __restrict__ dir,
+                                                            const double* __restrict__ mc, double* __restrict__ v27) {
   MG_STRIDE(i, g.n) {
-    for (int k = 0; k < 27; ++k) v27[(long long)k * g.n + i] = 0.0;
-    int ix, iy, iz;
-    coords(g, i, ix, iy, iz);
-    A.each(i, [&](long long j, double a) {
-      int jx, jy, jz;
-      coords(g, j, jx, jy, jz);
-      const int dx = jx - ix, dy = jy - iy, dz = jz - iz;
-      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
-        v27[(long long)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * g.n + i] = a;
-    });
+    if (dir[i]) {
+      for (int k = 0; k < 27; ++k) v27[(long long)k * g.n + i] = (k == 13) ? 1.0 : 0.0;
+    } else if (mc) {
+      v27[13 * g.n + i] += mc[i];
+    }
   }
 }
 
@@ -303,7 +365,6 @@ __global__ void mg_coef_kernel(const unsigned long long* bound, int k, double ra
   }
 }
 
-CsrRows csr_rows(const HxLorMatrix& A) { return CsrRows{A.off, A.col, A.val}; }
 StencilRows stencil_rows(const HxMgLevel& L) { return StencilRows{L.g, L.val}; }
 
 // `degree` Chebyshev steps for A x = b on level L (x overwritten, or accumulated into)
@@ -361,10 +422,30 @@ cudaError_t hx_mg_coarse_dir(const HxMgLevel& F, HxMgLevel& C, cudaStream_t s) {
 
 // Galerkin operators, inverse diagonals, bounds and Chebyshev coefficients of every level
 // (the fine level's matrix, inverse diagonal and bound come from the LOR assembly).
-cudaError_t hx_mg_assemble(const HxMg& M, const HxLorMatrix& A0, const unsigned long long* bound0, cudaStream_t s) {
-  // the fine level as a stencil (every LOR row couples only logical neighbours)
-  mg_csr_to_stencil_kernel<<<grid_of(M.levels[0].g.n), kT, 0, s>>>(csr_rows(A0), M.levels[0].g, M.levels[0].val);
-  cudaError_t e = cudaGetLastError();
+cudaError_t hx_mg_fine(const HxTables& T, int nx, int ny, const double* X8, double alpha, double nu, int collocated,
+                       const double* mc, const HxMgLevel& L0, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(L0.val, 0, sizeof(double) * 27 * (size_t)L0.g.n, s);
+  const double am = collocated ? 0.0 : alpha;  // the Q1 mass enters only in the consistent form
+  const long long cells = (long long)(L0.g.mx - 1) * (L0.g.my - 1) * (L0.g.mz - 1);
+  for (int c = 0; c < 8 && e == cudaSuccess; ++c) {
+    mg_cell_kernel<<<grid_of(cells / 8 + 1), kT, 0, s>>>(T, L0.g, nx, ny, X8, L0.dir, am, nu, c & 1, (c >> 1) & 1,
+                                                         (c >> 2) & 1, L0.val);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    mg_fine_finish_kernel<<<grid_of(L0.g.n), kT, 0, s>>>(L0.g, L0.dir, collocated ? mc : nullptr, L0.val);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t hx_mg_assemble(const HxMg& M, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(M.levels[0].bound, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    mg_diag_kernel<<<grid_of(M.levels[0].g.n), kT, 0, s>>>(stencil_rows(M.levels[0]), M.levels[0].dinv,
+                                                           M.levels[0].bound);
+    e = cudaGetLastError();
+  }
   for (int l = 1; l < M.n_levels && e == cudaSuccess; ++l) {
     const HxMgLevel& F = M.levels[l - 1];
     const HxMgLevel& C = M.levels[l];
@@ -382,15 +463,14 @@ cudaError_t hx_mg_assemble(const HxMg& M, const HxLorMatrix& A0, const unsigned 
     const bool coarsest = l == M.n_levels - 1;
     const int k = coarsest ? M.coarse_degree : M.smooth_degree;
     const double ratio = coarsest ? (double)k * k : M.smooth_ratio;
-    mg_coef_kernel<<<1, 32, 0, s>>>(l == 0 ? bound0 : L.bound, k, ratio, L.coef);
+    mg_coef_kernel<<<1, 32, 0, s>>>(L.bound, k, ratio, L.coef);
     e = cudaGetLastError();
   }
   return e;
 }
 
-cudaError_t hx_mg_vcycle(const HxMg& M, const HxLorMatrix& A0, const double* r, double* z, const int* done,
-                         cudaStream_t s) {
-  return level_cycle(M, 0, stencil_rows(M.levels[0]), A0.dinv, r, z, done, s);
+cudaError_t hx_mg_vcycle(const HxMg& M, const double* r, double* z, const int* done, cudaStream_t s) {
+  return level_cycle(M, 0, stencil_rows(M.levels[0]), M.levels[0].dinv, r, z, done, s);
 }
 
 int hx_mg_vcycle_launches(const HxMg& M) {
