@@ -614,6 +614,16 @@ def run_precond(hx, torch, args):
             torch.cuda.synchronize()
             res[pname] = {"setup_s": t_setup, "solve_s": e0.elapsed_time(e1) / 1e3, "iterations": info["iterations"],
                           "true_rel_residual": info["true_rel_residual"], "status": info["status"]}
+            if pname in ("jacobi", "lor_mg_s2"):
+                # the same preconditioner inside the mixed-precision refinement (FP32 inner CG)
+                xm, infom = op.solve_mixed(b, rtol=RTOL)
+                e0.record(s)
+                xm, infom = op.solve_mixed(b, rtol=RTOL)
+                e1.record(s)
+                torch.cuda.synchronize()
+                res[pname + "_mixed"] = {"solve_s": e0.elapsed_time(e1) / 1e3, "inner_iterations": infom["iterations"],
+                                         "refinements": infom["refinements"], "rel_residual": infom["rel_residual"],
+                                         "status": infom["status"]}
         out[name] = res
         del op, mesh, b, x
         torch.cuda.empty_cache()

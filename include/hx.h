@@ -233,9 +233,12 @@ HX_API hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_ho
  * Mixed-precision solve of A_c x = P b to the FP64 relative residual rtol:
  * iterative refinement whose residual r = P b - A_c x, update x += |r| d and
  * solution accumulate in FP64, while each correction d solves A_c d = r / |r|
- * with an FP32 Jacobi-PCG (FP32 operator apply: the same sum-factorized
- * kernels in FP32 with the FP32 rounding of the stored factors, or FP32
- * on-the-fly geometry) to the relative residual inner_rtol (e.g. 1e-5).
+ * with an FP32 PCG (FP32 operator apply: the same sum-factorized kernels in
+ * FP32 with the FP32 rounding of the stored factors, or FP32 on-the-fly
+ * geometry) to the relative residual inner_rtol (e.g. 1e-5).  The inner
+ * preconditioner follows hx_op_set_preconditioner: Jacobi (the diagonal of the
+ * FP32 operator, computed in FP32), the collocated mass, or the LOR multigrid
+ * V-cycle run in FP32 on FP32 copies of its levels.
  * Not in the paper; it trades the B300's 1:64 FP64:FP32 rate for a few FP64
  * residual applies.  max_it caps the total inner iterations; the solve also
  * stops with HX_ERR_NOT_CONVERGED when two refinement steps in a row fail to
@@ -312,7 +315,7 @@ HX_API hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream);
  * alpha <= 0, also from a later hx_op_set_coefficients with alpha <= 0);
  * HX_ERR_UNSUPPORTED (a LOR form on an operator with a nu field, a LOR row with more
  * than 64 distinct columns, HX_PREC_LOR_MG on a mesh without a logical grid;
- * mixed-precision solves reject the LOR forms).
+ * mixed-precision solves reject HX_PREC_LOR and HX_PREC_LOR_MC).
  * The first selection of a LOR form allocates and builds the sparsity pattern (one
  * synchronization of `stream`) and, for HX_PREC_LOR_MG, the grid hierarchy; later calls
  * are stream-ordered.

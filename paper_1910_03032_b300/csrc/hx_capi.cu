@@ -136,6 +136,8 @@ struct hx_op {
   HxMg mg = {};
   bool mg_built = false;
   double* mg_mc = nullptr;  // [n_dof] alpha Mc for the multigrid's fine stencil
+  float* zl32 = nullptr;    // [n_dof] FP32 preconditioned residual (mixed solves with the multigrid)
+  bool mg32 = false;        // FP32 copies of the multigrid levels allocated
 };
 
 namespace {
@@ -432,8 +434,17 @@ void hx_op_destroy(hx_op* op) {
       dfree(L.d0);
       dfree(L.d1);
     }
+    dfree(L.val32);
+    dfree(L.dinv32);
+    dfree(L.b32);
+    dfree(L.x32);
+    dfree(L.r32);
+    dfree(L.res32);
+    dfree(L.d032);
+    dfree(L.d132);
   }
   dfree(op->mg_mc);
+  dfree(op->zl32);
   delete op;
 }
 
@@ -1141,7 +1152,7 @@ HxCgBuffersF cg_buffers32(const hx_op* op) {
   b.yE = op->yE32;
   b.partial = op->partial;
   b.st = op->st32;
-  b.z = nullptr;
+  b.z = (op->prec == HX_PREC_LOR_MG) ? op->zl32 : nullptr;
   b.cond = 0ull;
   b.nullspace = op->singular ? 1 : 0;
   return b;
@@ -1163,11 +1174,29 @@ hx_status ensure_mixed(hx_op* op) {
       return s;
     HX_TRY(cudaMemsetAsync(op->st32, 0, sizeof(HxCgState), op->stream), "FP32 state init");
   }
+  if (op->prec == HX_PREC_LOR_MG && !op->mg32) {
+    // FP32 copies of the multigrid levels: stencils, inverse diagonals, work vectors
+    for (int l = 0; l < op->mg.n_levels; ++l) {
+      HxMgLevel& L = op->mg.levels[l];
+      const size_t nl = (size_t)L.g.n;
+      if ((s = dalloc(&L.val32, 27 * nl, "FP32 MG stencil")) || (s = dalloc(&L.dinv32, nl, "FP32 MG dinv")) ||
+          (s = dalloc(&L.r32, nl, "FP32 MG r")) || (s = dalloc(&L.res32, nl, "FP32 MG res")) ||
+          (s = dalloc(&L.d032, nl, "FP32 MG d0")) || (s = dalloc(&L.d132, nl, "FP32 MG d1")))
+        return s;
+      if (l > 0 && ((s = dalloc(&L.b32, nl, "FP32 MG b")) || (s = dalloc(&L.x32, nl, "FP32 MG x")))) return s;
+    }
+    if ((s = dalloc(&op->zl32, (size_t)n, "FP32 preconditioned residual"))) return s;
+    op->mg32 = true;
+    op->mixed_stale = true;
+  }
   if (op->mixed_stale) {
     if (op->geom == HX_GEOM_STORED)
       HX_TRY(hx_launch_to_float((long long)m->E * 7 * m->q * m->q * m->q, op->factors, op->factors32, op->stream),
              "FP32 factors");
-    if (op->prec == HX_PREC_JACOBI) {
+    if (op->prec == HX_PREC_LOR_MG) {
+      HX_TRY(hx_mg_to_float(op->mg, op->stream), "FP32 multigrid levels");
+      op->launches += 2 * op->mg.n_levels;
+    } else if (op->prec == HX_PREC_JACOBI) {
       // the inner solver's Jacobi diagonal: the diagonal of the FP32 operator, computed in FP32
       static const hx_diag32_launcher t[] = {nullptr, hx_launch_diag32_p1, hx_launch_diag32_p2, hx_launch_diag32_p3,
                                              hx_launch_diag32_p4, hx_launch_diag32_p5, hx_launch_diag32_p6,
@@ -1202,6 +1231,10 @@ cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s, unsigned long long c
   cudaError_t e = element_apply32(op, op->p32, &op->st32->done, s);
   if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
   if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
+  if (e == cudaSuccess && b.z) {
+    e = hx_mg_vcycle32(op->mg, op->r32, op->zl32, &op->st32->done, s);
+    if (e == cudaSuccess) e = hx_launch_cg_rz(b, s);
+  }
   if (e == cudaSuccess) e = hx_launch_cg_direction(b, s);
   return e;
 }
@@ -1234,8 +1267,8 @@ hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_
 hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
                       cudaStream_t user, hx_solve_info* info) {
   const hx_mesh* m = op->mesh;
-  if (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG)
-    return fail(HX_ERR_UNSUPPORTED, "mixed-precision solves take the Jacobi or collocated mass preconditioner");
+  if (op->prec == HX_PREC_LOR)
+    return fail(HX_ERR_UNSUPPORTED, "mixed-precision solves take the Jacobi, collocated mass or multigrid preconditioner");
   hx_status s = ensure_solver(op);
   if (s) return s;
   cudaStream_t st = op->stream;
@@ -1270,6 +1303,10 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
     }
     HX_TRY(hx_launch_cg_init(buf, (const float*)op->r32, (const float*)nullptr, inner_rtol, max_it - inner_total, st),
            "inner init");
+    if (op->prec == HX_PREC_LOR_MG) {
+      HX_TRY(hx_mg_vcycle32(op->mg, op->r32, op->zl32, &op->st32->done, st), "inner first V-cycle");
+      op->launches += hx_mg_vcycle_launches(op->mg);
+    }
     HX_TRY(hx_launch_cg_start(buf, st), "inner start");
     op->launches += 3;
     if (op->singular) {
@@ -1280,7 +1317,7 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
       HX_TRY(cudaGraphLaunch(op->graph32, st), "graph launch");
       HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
       HX_TRY(cudaStreamSynchronize(st), "solver sync");
-      op->launches += 4 * (long long)op->st_host->loops;
+      op->launches += iteration_launches(op) * (long long)op->st_host->loops;
       if (!op->st_host->done) return fail(HX_ERR_CUDA, "inner CG graph loop ended before the solver finished");
     } else {
       for (;;) {
@@ -1288,7 +1325,7 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
         HX_TRY(cudaStreamSynchronize(st), "solver sync");
         if (op->st_host->done) break;
         for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration32(op, st), "inner iteration");
-        op->launches += 4 * kChunk;
+        op->launches += iteration_launches(op) * kChunk;
       }
     }
     const HxCgState cs = *op->st_host;
@@ -1642,7 +1679,12 @@ hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream
     cudaGraphExecDestroy(op->graph);
     op->graph = nullptr;
   }
+  if (op->graph32) {
+    cudaGraphExecDestroy(op->graph32);
+    op->graph32 = nullptr;
+  }
   op->graph_failed = false;
+  op->graph32_failed = false;
   op->prec = (kind == HX_PREC_LOR_MC) ? HX_PREC_LOR : kind;  // one solver path for both Chebyshev forms
   op->mixed_stale = true;  // the FP32 inverse diagonal follows at the next mixed solve
   int nl = 0;

@@ -216,6 +216,8 @@ struct HxMgLevel {
   double *res, *d0, *d1;     // Chebyshev work vectors
   double* coef;              // Chebyshev coefficients of this level's smoother (coarse solver)
   unsigned long long* bound; // Gershgorin bound of D^-1 A
+  // FP32 copies for the inner solver of mixed-precision solves (allocated on first use)
+  float *val32, *dinv32, *b32, *x32, *r32, *res32, *d032, *d132;
 };
 #define HX_MG_MAX_LEVELS 16
 struct HxMg {
@@ -232,6 +234,8 @@ cudaError_t hx_mg_fine(const HxTables& T, int nx, int ny, const double* X8, doub
 // inverse diagonals, bounds, Galerkin levels and Chebyshev coefficients from the fine stencil
 cudaError_t hx_mg_assemble(const HxMg& M, cudaStream_t s);
 cudaError_t hx_mg_vcycle(const HxMg& M, const double* r, double* z, const int* done, cudaStream_t s);
+cudaError_t hx_mg_vcycle32(const HxMg& M, const float* r, float* z, const int* done, cudaStream_t s);
+cudaError_t hx_mg_to_float(const HxMg& M, cudaStream_t s);
 int hx_mg_vcycle_launches(const HxMg& M);
 // mixed-precision refinement helpers
 cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,

@@ -48,15 +48,17 @@ __device__ __forceinline__ long long index(const HxGrid& g, int x, int y, int z)
   return (long long)x + (long long)g.mx * ((long long)y + (long long)g.my * z);
 }
 
-// Every level: 27-point stencils on the logical grid.
-struct StencilRows {
+// Every level: 27-point stencils on the logical grid (FP64; FP32 copies for the inner solver of
+// mixed-precision solves).
+template <typename Real>
+struct StencilRowsT {
   HxGrid g;
-  const double* val;  // [27][n]
-  __device__ __forceinline__ double dot(long long i, const double* __restrict__ x) const {
+  const Real* val;  // [27][n]
+  __device__ __forceinline__ Real dot(long long i, const Real* __restrict__ x) const {
     int ix, iy, iz;
     coords(g, i, ix, iy, iz);
     const long long sy = g.mx, sz = (long long)g.mx * g.my;
-    double s = 0.0;
+    Real s = Real(0);
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
       if (iz + dz < 0 || iz + dz >= g.mz) continue;
@@ -83,55 +85,58 @@ struct StencilRows {
     }
   }
 };
+typedef StencilRowsT<double> StencilRows;
 
 // ---- Chebyshev-Jacobi on one level (the recurrence of hx_lor.cu, accumulating into x) ----
-__global__ void __launch_bounds__(kT) mg_cheb_first_kernel(long long n, const double* __restrict__ dinv,
-                                                           const double* __restrict__ b, double* __restrict__ res,
-                                                           double* __restrict__ d, double* __restrict__ x,
+template <typename Real>
+__global__ void __launch_bounds__(kT) mg_cheb_first_kernel(long long n, const Real* __restrict__ dinv,
+                                                           const Real* __restrict__ b, Real* __restrict__ res,
+                                                           Real* __restrict__ d, Real* __restrict__ x,
                                                            const double* __restrict__ coef, int accumulate,
                                                            const int* done) {
   if (done && *(volatile const int*)done) return;
-  const double c0 = coef[0];
+  const Real c0 = Real(coef[0]);
   MG_STRIDE(i, n) {
-    const double s = dinv[i] * b[i];
+    const Real s = dinv[i] * b[i];
     res[i] = s;
     d[i] = c0 * s;
     x[i] = accumulate ? x[i] + c0 * s : c0 * s;
   }
 }
 
-template <typename Rows>
-__global__ void __launch_bounds__(kT) mg_cheb_step_kernel(Rows A, long long n, const double* __restrict__ dinv,
-                                                          const double* __restrict__ din, double* __restrict__ dout,
-                                                          double* __restrict__ res, double* __restrict__ x,
+template <typename Real, typename Rows>
+__global__ void __launch_bounds__(kT) mg_cheb_step_kernel(Rows A, long long n, const Real* __restrict__ dinv,
+                                                          const Real* __restrict__ din, Real* __restrict__ dout,
+                                                          Real* __restrict__ res, Real* __restrict__ x,
                                                           const double* __restrict__ coef, int j, const int* done) {
   if (done && *(volatile const int*)done) return;
-  const double c1 = coef[2 * j], c2 = coef[2 * j + 1];
+  const Real c1 = Real(coef[2 * j]), c2 = Real(coef[2 * j + 1]);
   MG_STRIDE(i, n) {
-    const double rs = res[i] - dinv[i] * A.dot(i, din);
+    const Real rs = res[i] - dinv[i] * A.dot(i, din);
     res[i] = rs;
-    const double dn = c1 * din[i] + c2 * rs;
+    const Real dn = c1 * din[i] + c2 * rs;
     dout[i] = dn;
     x[i] += dn;
   }
 }
 
-template <typename Rows>
-__global__ void __launch_bounds__(kT) mg_residual_kernel(Rows A, long long n, const double* __restrict__ b,
-                                                         const double* __restrict__ x, double* __restrict__ r,
+template <typename Real, typename Rows>
+__global__ void __launch_bounds__(kT) mg_residual_kernel(Rows A, long long n, const Real* __restrict__ b,
+                                                         const Real* __restrict__ x, Real* __restrict__ r,
                                                          const int* done) {
   if (done && *(volatile const int*)done) return;
   MG_STRIDE(i, n) { r[i] = b[i] - A.dot(i, x); }
 }
 
 // b_c = P^T r_f
+template <typename Real>
 __global__ void __launch_bounds__(kT) mg_restrict_kernel(HxGrid fg, const unsigned char* __restrict__ fdir,
-                                                         const double* __restrict__ rf, HxGrid cg,
+                                                         const Real* __restrict__ rf, HxGrid cg,
                                                          const unsigned char* __restrict__ cdir,
-                                                         double* __restrict__ bc, const int* done) {
+                                                         Real* __restrict__ bc, const int* done) {
   if (done && *(volatile const int*)done) return;
   MG_STRIDE(I, cg.n) {
-    double s = 0.0;
+    Real s = Real(0);
     if (!cdir[I]) {
       int X, Y, Z;
       coords(cg, I, X, Y, Z);
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(kT) mg_restrict_kernel(HxGrid fg, const unsign
         if (!inside(fg, ix, iy, iz)) continue;
         const long long i = index(fg, ix, iy, iz);
         if (fdir[i]) continue;
-        const double w = (dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0);
+        const Real w = Real((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
         s += w * rf[i];
       }
     }
@@ -150,16 +155,17 @@ __global__ void __launch_bounds__(kT) mg_restrict_kernel(HxGrid fg, const unsign
 }
 
 // x_f += P x_c
+template <typename Real>
 __global__ void __launch_bounds__(kT) mg_prolong_kernel(HxGrid cg, const unsigned char* __restrict__ cdir,
-                                                        const double* __restrict__ xc, HxGrid fg,
+                                                        const Real* __restrict__ xc, HxGrid fg,
                                                         const unsigned char* __restrict__ fdir,
-                                                        double* __restrict__ xf, const int* done) {
+                                                        Real* __restrict__ xf, const int* done) {
   if (done && *(volatile const int*)done) return;
   MG_STRIDE(i, fg.n) {
     if (fdir[i]) continue;
     int ix, iy, iz;
     coords(fg, i, ix, iy, iz);
-    double s = 0.0;
+    Real s = Real(0);
     for (int oz = 0; oz < 2; ++oz) {
       if ((iz & 1) == 0 && oz) break;
       const int Z = (iz & 1) ? (iz - 1) / 2 + oz : iz / 2;
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(kT) mg_prolong_kernel(HxGrid cg, const unsigne
           const int X = (ix & 1) ? (ix - 1) / 2 + ox : ix / 2;
           const double wx = (ix & 1) ? 0.5 : 1.0;
           const long long J = index(cg, X, Y, Z);
-          if (!cdir[J]) s += wx * wy * wz * xc[J];
+          if (!cdir[J]) s += Real(wx * wy * wz) * xc[J];
         }
       }
     }
@@ -367,50 +373,69 @@ __global__ void mg_coef_kernel(const unsigned long long* bound, int k, double ra
 
 StencilRows stencil_rows(const HxMgLevel& L) { return StencilRows{L.g, L.val}; }
 
+// What one V-cycle level works with, in the cycle's precision.
+template <typename Real>
+struct LevelView {
+  HxGrid g;
+  const unsigned char* dir;
+  const Real* val;
+  const Real* dinv;
+  Real *b, *x, *r, *res, *d0, *d1;
+  const double* coef;
+};
+LevelView<double> view(const HxMgLevel& L, double) {
+  return LevelView<double>{L.g, L.dir, L.val, L.dinv, L.b, L.x, L.r, L.res, L.d0, L.d1, L.coef};
+}
+LevelView<float> view(const HxMgLevel& L, float) {
+  return LevelView<float>{L.g, L.dir, L.val32, L.dinv32, L.b32, L.x32, L.r32, L.res32, L.d032, L.d132, L.coef};
+}
+
 // `degree` Chebyshev steps for A x = b on level L (x overwritten, or accumulated into)
-template <typename Rows>
-cudaError_t smooth(const Rows& A, const HxMgLevel& L, const double* dinv, const double* b, double* x, int degree,
-                   const double* coef, int accumulate, const int* done, cudaStream_t s) {
+template <typename Real>
+cudaError_t smooth(const LevelView<Real>& L, const Real* b, Real* x, int degree, int accumulate, const int* done,
+                   cudaStream_t s) {
+  const StencilRowsT<Real> A{L.g, L.val};
   const unsigned g = grid_of(L.g.n);
-  mg_cheb_first_kernel<<<g, kT, 0, s>>>(L.g.n, dinv, b, L.res, L.d0, x, coef, accumulate, done);
+  mg_cheb_first_kernel<Real><<<g, kT, 0, s>>>(L.g.n, L.dinv, b, L.res, L.d0, x, L.coef, accumulate, done);
   cudaError_t e = cudaGetLastError();
-  double* din = L.d0;
-  double* dout = L.d1;
+  Real* din = L.d0;
+  Real* dout = L.d1;
   for (int j = 1; j < degree && e == cudaSuccess; ++j) {
-    mg_cheb_step_kernel<Rows><<<g, kT, 0, s>>>(A, L.g.n, dinv, din, dout, L.res, x, coef, j, done);
+    mg_cheb_step_kernel<Real, StencilRowsT<Real>><<<g, kT, 0, s>>>(A, L.g.n, L.dinv, din, dout, L.res, x, L.coef, j,
+                                                                   done);
     e = cudaGetLastError();
-    double* t = din;
+    Real* t = din;
     din = dout;
     dout = t;
   }
   return e;
 }
 
-template <typename Rows>
-cudaError_t level_cycle(const HxMg& M, int l, const Rows& A, const double* dinv, const double* b, double* x,
-                        const int* done, cudaStream_t s);
-
-cudaError_t cycle_from(const HxMg& M, int l, const double* b, double* x, const int* done, cudaStream_t s) {
-  return level_cycle(M, l, stencil_rows(M.levels[l]), M.levels[l].dinv, b, x, done, s);
+template <typename Real>
+cudaError_t level_cycle(const HxMg& M, const LevelView<Real>* V, int l, const Real* b, Real* x, const int* done,
+                        cudaStream_t s) {
+  const LevelView<Real>& L = V[l];
+  if (l == M.n_levels - 1) return smooth(L, b, x, M.coarse_degree, 0, done, s);
+  const LevelView<Real>& C = V[l + 1];
+  const StencilRowsT<Real> A{L.g, L.val};
+  const unsigned g = grid_of(L.g.n);
+  cudaError_t e = smooth(L, b, x, M.smooth_degree, 0, done, s);
+  if (e != cudaSuccess) return e;
+  mg_residual_kernel<Real, StencilRowsT<Real>><<<g, kT, 0, s>>>(A, L.g.n, b, x, L.r, done);
+  mg_restrict_kernel<Real><<<grid_of(C.g.n), kT, 0, s>>>(L.g, L.dir, L.r, C.g, C.dir, C.b, done);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = level_cycle(M, V, l + 1, C.b, C.x, done, s)) != cudaSuccess) return e;
+  mg_prolong_kernel<Real><<<g, kT, 0, s>>>(C.g, C.dir, C.x, L.g, L.dir, x, done);
+  mg_residual_kernel<Real, StencilRowsT<Real>><<<g, kT, 0, s>>>(A, L.g.n, b, x, L.r, done);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return smooth(L, L.r, x, M.smooth_degree, 1, done, s);
 }
 
-template <typename Rows>
-cudaError_t level_cycle(const HxMg& M, int l, const Rows& A, const double* dinv, const double* b, double* x,
-                        const int* done, cudaStream_t s) {
-  const HxMgLevel& L = M.levels[l];
-  if (l == M.n_levels - 1) return smooth(A, L, dinv, b, x, M.coarse_degree, L.coef, 0, done, s);
-  const HxMgLevel& C = M.levels[l + 1];
-  const unsigned g = grid_of(L.g.n);
-  cudaError_t e = smooth(A, L, dinv, b, x, M.smooth_degree, L.coef, 0, done, s);
-  if (e != cudaSuccess) return e;
-  mg_residual_kernel<Rows><<<g, kT, 0, s>>>(A, L.g.n, b, x, L.r, done);
-  mg_restrict_kernel<<<grid_of(C.g.n), kT, 0, s>>>(L.g, L.dir, L.r, C.g, C.dir, C.b, done);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cycle_from(M, l + 1, C.b, C.x, done, s)) != cudaSuccess) return e;
-  mg_prolong_kernel<<<g, kT, 0, s>>>(C.g, C.dir, C.x, L.g, L.dir, x, done);
-  mg_residual_kernel<Rows><<<g, kT, 0, s>>>(A, L.g.n, b, x, L.r, done);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return smooth(A, L, dinv, L.r, x, M.smooth_degree, L.coef, 1, done, s);
+template <typename Real>
+cudaError_t vcycle(const HxMg& M, const Real* r, Real* z, const int* done, cudaStream_t s) {
+  LevelView<Real> V[HX_MG_MAX_LEVELS];
+  for (int l = 0; l < M.n_levels; ++l) V[l] = view(M.levels[l], Real(0));
+  return level_cycle(M, V, 0, r, z, done, s);
 }
 
 }  // namespace
@@ -470,7 +495,22 @@ cudaError_t hx_mg_assemble(const HxMg& M, cudaStream_t s) {
 }
 
 cudaError_t hx_mg_vcycle(const HxMg& M, const double* r, double* z, const int* done, cudaStream_t s) {
-  return level_cycle(M, 0, stencil_rows(M.levels[0]), M.levels[0].dinv, r, z, done, s);
+  return vcycle<double>(M, r, z, done, s);
+}
+
+cudaError_t hx_mg_vcycle32(const HxMg& M, const float* r, float* z, const int* done, cudaStream_t s) {
+  return vcycle<float>(M, r, z, done, s);
+}
+
+// FP32 copies of every level's stencil and inverse diagonal (the inner solver of mixed solves)
+cudaError_t hx_mg_to_float(const HxMg& M, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < M.n_levels && e == cudaSuccess; ++l) {
+    const HxMgLevel& L = M.levels[l];
+    e = hx_launch_to_float(27 * L.g.n, L.val, L.val32, s);
+    if (e == cudaSuccess) e = hx_launch_to_float(L.g.n, L.dinv, L.dinv32, s);
+  }
+  return e;
 }
 
 int hx_mg_vcycle_launches(const HxMg& M) {

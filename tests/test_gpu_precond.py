@@ -327,3 +327,27 @@ def test_mg_needs_a_structured_mesh(hx):
     with pytest.raises(hx.HxError) as ei:
         op.set_preconditioner(hx.HX_PREC_LOR_MG, 3)
     assert ei.value.status == -7
+
+
+@pytest.mark.parametrize("alpha,dirichlet", [(0.0, True), (0.0, False), (1000.0, True)])
+def test_mixed_solve_with_multigrid(hx, alpha, dirichlet):
+    """Mixed precision with the LOR multigrid: the FP32 inner CG is preconditioned by the V-cycle
+    in FP32; the FP64 refinement still reaches 1e-10 and the oracle's solution."""
+    from oracle import fem
+    from oracle.solve import jacobi_pcg, jacobi_pcg_nullspace
+    p, shape = 4, (4, 4, 4)
+    V, EV, om = case(shape, p, dirichlet=dirichlet)
+    mesh = hx.Mesh.box(*shape, p, p + 2, V, dirichlet_faces=63 if dirichlet else 0)
+    nu = 1.0 if alpha == 0.0 else 1e-2
+    op = hx.Operator(mesh, alpha, nu)
+    op.set_preconditioner(hx.HX_PREC_LOR_MG, 2)
+    b = S.random_vector(om.n_dof, 47)
+    x64, info64 = op.solve(to_dev(b), rtol=1e-10)
+    x, info = op.solve_mixed(to_dev(b), rtol=1e-10)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    assert info["refinements"] <= 4
+    oop = fem.Operator(om, alpha, nu)
+    xo = (jacobi_pcg(oop, b, 1e-12) if dirichlet else jacobi_pcg_nullspace(oop, b, 1e-12))[0]
+    assert rel_err(x.cpu().numpy(), xo) <= 1e-8
+    # the inner solves need about as many iterations per refinement as the FP64 solve in all
+    assert info["iterations"] <= info["refinements"] * (info64["iterations"] + 5)
