@@ -502,6 +502,19 @@ def run_batch(hx, torch, args):
         best = min(by_lanes, key=lambda k: by_lanes[k][0])
         t_bat, infos = by_lanes[best]
         dof_applies = sum(o.n_dof * (i["iterations"] + 1) for o, i in zip(ops, infos))
+        if name == "projection_step":
+            # the same step with every solve in mixed precision (FP32 inner CG, FP64 refinement),
+            # one solve after another
+            mixed = lambda: [o.solve_mixed(b, rtol=RTOL) for o, b in zip(ops, bs)]
+            mixed()
+            t_mix, infos_mix = timed(mixed, args.batch_reps)
+            res["projection_step_mixed"] = {
+                "instances": len(ops), "solve_s": t_mix, "speedup_vs_fp64_batched": t_bat / t_mix,
+                "inner_iterations": [i["iterations"] for _, i in infos_mix],
+                "refinements": [i["refinements"] for _, i in infos_mix],
+                "max_rel_residual": max(i["rel_residual"] for _, i in infos_mix),
+                "converged": all(i["status"] == 0 for _, i in infos_mix),
+                "timing": f"{args.batch_reps} reps after 1 warm-up, sequential"}
         res[name] = {"instances": len(ops), "n_dof_total": sum(o.n_dof for o in ops),
                      "iterations_total": sum(i["iterations"] for i in infos),
                      "converged": all(i["status"] == 0 for i in infos),
