@@ -375,6 +375,28 @@ __global__ void __launch_bounds__(NT, MINB)
   //    du/dxi_3 from the folded parts of that same contraction (kept in registers)
   const bool owner = tid < NE * Q2;
   const int cel = tid / Q2, c = tid - cel * Q2;         // element, column (jq, iq) = (c / q, c % q)
+  // coefficients in the kernel's precision, converted once (an FP32 kernel would otherwise
+  // convert them at every point on the FP64 pipe)
+  const Real alpha_r = Real(A.alpha), nu_r = Real(A.nu);
+  // on-the-fly geometry along this thread's z-column: for a trilinear map dx/dxi_3 does not
+  // depend on xi_3 and the other two Jacobian columns are affine in it.  Used by the FP32
+  // kernel, which is bound by shared-memory reads (the map coefficients are read once per
+  // column instead of once per point); the FP64 kernel keeps the registers for its contractions.
+  constexpr bool COLJ = sizeof(Real) == 4;
+  Real P0[3], R0[3], P1[3], R1[3], J2[3];
+  if (COLJ && GEOM == HX_KGEOM_ONTHEFLY && owner) {
+    const Real* a = geo + cel * 24;
+    const Real x1 = T.xq[c % Q], x2 = T.xq[c / Q];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const Real* ad = a + d * 8;
+      P0[d] = ad[1] + ad[4] * x2;
+      R0[d] = ad[5] + ad[7] * x2;
+      P1[d] = ad[2] + ad[4] * x1;
+      R1[d] = ad[6] + ad[7] * x1;
+      J2[d] = ad[3] + ad[5] * x1 + (ad[6] + ad[7] * x1) * x2;
+    }
+  }
   const int cs = (c / Q) * SY + (c % Q);                // the column's offset in a region
   Real du[Q];
   if (owner) {
@@ -438,11 +460,21 @@ __global__ void __launch_bounds__(NT, MINB)
       } else {
         const int iq = c % Q, jq = c / Q;
         Real j0[3], j1[3], j2[3];
-        trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
+        if (COLJ) {
+          const Real z = T.xq[kq];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            j0[d] = P0[d] + z * R0[d];
+            j1[d] = P1[d] + z * R1[d];
+            j2[d] = J2[d];
+          }
+        } else {
+          trilinear_jacobian(geo + cel * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
+        }
         const Real w = T.wq[iq] * T.wq[jq] * T.wq[kq];
-        Real nu = Real(A.nu);
+        Real nu = nu_r;
         if (NUF) nu = (e < A.E) ? Real(__ldg(A.nu_q + e * Q3 + pt)) : Real(0);
-        point_factors(j0, j1, j2, Real(A.alpha) * w, nu * w, f);
+        point_factors(j0, j1, j2, alpha_r * w, nu * w, f);
         if (e >= A.E) {
 #pragma unroll
           for (int m = 0; m < 7; ++m) f[m] = Real(0);
@@ -684,6 +716,7 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
     __syncthreads();
   }
   // factors into shared memory: F[f][c][b][a]
+  const Real alpha_r = Real(A.alpha), nu_r = Real(A.nu);
   for (int t = tid; t < NE * Q3; t += NT) {
     const int el = t / Q3, pt = t - el * Q3;
     const long long e = e0 + el;
@@ -697,8 +730,8 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
         Real j0[3], j1[3], j2[3];
         trilinear_jacobian(geo + el * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
         const Real w = T.wq[iq] * T.wq[jq] * T.wq[kq];
-        const Real nu = Real(NUF ? A.nu_q[e * Q3 + pt] : A.nu);
-        point_factors(j0, j1, j2, Real(A.alpha) * w, nu * w, f);
+        const Real nu = NUF ? Real(A.nu_q[e * Q3 + pt]) : nu_r;
+        point_factors(j0, j1, j2, alpha_r * w, nu * w, f);
       }
     }
 #pragma unroll
