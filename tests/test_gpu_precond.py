@@ -351,3 +351,33 @@ def test_mixed_solve_with_multigrid(hx, alpha, dirichlet):
     assert rel_err(x.cpu().numpy(), xo) <= 1e-8
     # the inner solves need about as many iterations per refinement as the FP64 solve in all
     assert info["iterations"] <= info["refinements"] * (info64["iterations"] + 5)
+
+
+def _face_mask(shape, p, faces):
+    gx, gy, gz = p * shape[0] + 1, p * shape[1] + 1, p * shape[2] + 1
+    K, J, I = np.meshgrid(np.arange(gz), np.arange(gy), np.arange(gx), indexing="ij")
+    I, J, K = I.ravel(), J.ravel(), K.ravel()
+    sel = [(1, I == 0), (2, I == gx - 1), (4, J == 0), (8, J == gy - 1), (16, K == 0), (32, K == gz - 1)]
+    mask = np.zeros(gx * gy * gz, bool)
+    for bit, m in sel:
+        if faces & bit:
+            mask |= m
+    return mask
+
+
+@pytest.mark.parametrize("shape,p,q,faces", [((4, 4, 2), 1, 2, 63), ((2, 2, 2), 3, 4, 3), ((4, 2, 2), 2, 4, 16 | 32),
+                                             ((1, 1, 1), 8, 9, 63), ((2, 2, 2), 4, 6, 1)])
+def test_mg_vcycle_more_cases(hx, shape, p, q, faces):
+    """Q_1 meshes (the LOR mesh is the mesh), q = p + 1, partial Dirichlet faces, one element of Q_8."""
+    from oracle import fem, precond
+    V = S.structured_vertices(*shape, 0.1, 990 + p)
+    om = fem.StructuredMesh(*shape, p, q, V, S.structured_elem_vert(*shape), dirichlet_boundary=False)
+    om.dirichlet = _face_mask(shape, p, faces)
+    mesh = hx.Mesh.box(*shape, p, q, V, dirichlet_faces=faces)
+    op = hx.Operator(mesh, 3.0, 0.4)
+    op.set_preconditioner(hx.HX_PREC_LOR_MG, 3)
+    A = precond.lor_matrix(om, 3.0, 0.4, "collocated")
+    levels = precond.mg_hierarchy(A, tuple(p * s + 1 for s in shape), om.dirichlet)
+    r = np.where(om.dirichlet, 0.0, S.uniform_pm1(991, om.n_dof))
+    z = op.precond_apply(to_dev(r)).cpu().numpy()
+    assert rel_err(z, precond.vcycle(levels, r, smooth_degree=3)) <= 1e-11
