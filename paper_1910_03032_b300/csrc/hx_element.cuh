@@ -231,7 +231,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // Wait for phase 0 of `bar` with a bound on the attempts (each try_wait itself suspends
 // for a while); false when the bound was reached.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar) {
-  for (int it = 0; it < (1 << 22); ++it)
+  for (int it = 0; it < (1 << 16); ++it)
     if (mbar_try_wait(bar, 0u)) return true;
   return false;
 }
