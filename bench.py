@@ -21,7 +21,9 @@ end-to-end number through host buffers, the CPU oracle baseline, and the
 SM clocks sampled during the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hx|reference]
-                       [--p P] [--n N] [--geom stored|onthefly] [--sweep]
+                       [--p P] [--n N] [--geom stored|onthefly] [--no-cpu] [--no-mixed]
+                       [--sweep] [--grad] [--precond] [--batch [--batch-reps R]]
+       python bench.py --vcycle [--p P] [--n N]     (the LOR multigrid V-cycle alone)
 """
 from __future__ import annotations
 

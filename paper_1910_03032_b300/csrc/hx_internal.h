@@ -199,7 +199,6 @@ cudaError_t hx_lor_values(const HxTables& T, const HxLorBuild& b, const double* 
 cudaError_t hx_lor_coefficients(const unsigned long long* bound, int degree, double* coef, cudaStream_t s);
 cudaError_t hx_lor_precondition(const HxLorMatrix& A, const HxChebWork& w, const double* r, double* z,
                                 const int* done, cudaStream_t s);
-cudaError_t hx_lor_spmv(const HxLorMatrix& A, const double* x, double* y, cudaStream_t s);
 
 // ---- geometric multigrid V-cycle on the LOR matrix of a structured mesh (hx_mg.cu) ----
 struct HxGrid {

@@ -294,16 +294,6 @@ __global__ void __launch_bounds__(kT) cheb_step_kernel(long long n, const long l
   }
 }
 
-__global__ void __launch_bounds__(kT) spmv_kernel(long long n, const long long* __restrict__ off,
-                                                  const int* __restrict__ col, const double* __restrict__ val,
-                                                  const double* __restrict__ x, double* __restrict__ y) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (long long o = off[g]; o < off[g + 1]; ++o) s += __ldg(val + o) * __ldg(x + __ldg(col + o));
-    y[g] = s;
-  }
-}
-
 // ---- exclusive scan of n counts into off[0..n] (three passes, 2048 entries per block) ----
 constexpr int kScanT = 1024, kScanPer = 2;
 constexpr int kScanB = kScanT * kScanPer;
@@ -435,7 +425,3 @@ cudaError_t hx_lor_precondition(const HxLorMatrix& A, const HxChebWork& w, const
   return e;
 }
 
-cudaError_t hx_lor_spmv(const HxLorMatrix& A, const double* x, double* y, cudaStream_t s) {
-  spmv_kernel<<<grid_of(A.n), kT, 0, s>>>(A.n, A.off, A.col, A.val, x, y);
-  return cudaGetLastError();
-}
