@@ -47,7 +47,16 @@ import synthetic as S  # noqa: E402
 METRIC = "Helmholtz apply GDoF/s & PCG time, p=2-8; mixed/batched vs FP64 at 1e-10"
 ALPHA, NU, RTOL = 1000.0, 1e-2, 1e-10
 SWEEP_N = {2: 160, 3: 96, 4: 96, 5: 64, 6: 64, 7: 48, 8: 48}
-HBM_GBS = 6518.0  # measured copy bandwidth of the B300s
+def _measured_hbm_gbs(fallback=6400.0):
+    """The measured copy bandwidth of the B300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return fallback
+
+
+HBM_GBS = _measured_hbm_gbs()
 # FP64 peak of the B300: 2 DFMA per clock per SM (a throughput probe measured
 # 565 G DFMA/s at ~1.94 GHz: 1.97 per clock per SM) x 148 SMs x 2032 MHz x 2 flops.
 FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
