@@ -61,9 +61,9 @@ HBM_GBS = _measured_hbm_gbs()
 # 565 G DFMA/s at ~1.94 GHz: 1.97 per clock per SM) x 148 SMs x 2032 MHz x 2 flops.
 FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch, keyed by
-# (p, N, geom): the 32^3 capture of the current kernel (497.8 MB read + 28.4 MB written)
+# (p, N, geom): the 32^3 capture of the current kernel (496.3 MB read + 28.4 MB written)
 # scaled by the element count (27x at 96^3); traffic grows in proportion to the elements.
-NCU_TRAFFIC = {(4, 96, "stored"): (497.797120e6 + 28.446464e6) * 27}
+NCU_TRAFFIC = {(4, 96, "stored"): (496.308736e6 + 28.430848e6) * 27}
 
 
 def alg_flops_per_element(p: int, q: int) -> int:
