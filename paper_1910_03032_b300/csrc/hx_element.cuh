@@ -379,10 +379,10 @@ __global__ void __launch_bounds__(NT, MINB)
   // convert them at every point on the FP64 pipe)
   const Real alpha_r = Real(A.alpha), nu_r = Real(A.nu);
   // on-the-fly geometry along this thread's z-column: for a trilinear map dx/dxi_3 does not
-  // depend on xi_3 and the other two Jacobian columns are affine in it.  Used by the FP32
-  // kernel, which is bound by shared-memory reads (the map coefficients are read once per
-  // column instead of once per point); the FP64 kernel keeps the registers for its contractions.
-  constexpr bool COLJ = sizeof(Real) == 4;
+  // depend on xi_3 and the other two Jacobian columns are affine in it, so the map
+  // coefficients are read once per column and each point costs two 3-vector updates
+  // (+13-16% on the FP64 on-the-fly apply despite a few spilled registers)
+  constexpr bool COLJ = true;
   Real P0[3], R0[3], P1[3], R1[3], J2[3];
   if (COLJ && GEOM == HX_KGEOM_ONTHEFLY && owner) {
     const Real* a = geo + cel * 24;

@@ -65,12 +65,15 @@ __device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsign
 // ---------------------------------------------------------------------------
 // geometry setup: factors[e][c][pt], c = (m, G00, G01, G02, G11, G12, G22)
 // ---------------------------------------------------------------------------
+// One thread per z-column (element, iq, jq) of Gauss points: along the column dx/dxi_3 of the
+// trilinear map is constant and the other two Jacobian columns are affine in xi_3, so each point
+// costs two 3-vector updates instead of a full Jacobian evaluation.
 __global__ void __launch_bounds__(kThreads) geometry_kernel(const __grid_constant__ HxTables T, long long E, int EB,
                                                              const double* __restrict__ X8,
                                                              const double* __restrict__ nu_q, double alpha, double nu,
                                                              double* __restrict__ factors, int* bad) {
   extern __shared__ double cf[];  // EB x 24
-  const int q = T.q, Q3 = q * q * q;
+  const int q = T.q, Q2 = q * q, Q3 = Q2 * q;
   const long long e0 = (long long)blockIdx.x * EB;
   for (int el = threadIdx.x; el < EB; el += blockDim.x) {
     const long long e = e0 + el;
@@ -80,18 +83,36 @@ __global__ void __launch_bounds__(kThreads) geometry_kernel(const __grid_constan
   }
   __syncthreads();
   int nbad = 0;
-  for (int t = threadIdx.x; t < EB * Q3; t += blockDim.x) {
-    const int el = t / Q3, pt = t - el * Q3;
+  for (int t = threadIdx.x; t < EB * Q2; t += blockDim.x) {
+    const int el = t / Q2, col = t - el * Q2;
     const long long e = e0 + el;
     if (e >= E) continue;
-    const int iq = pt % q, jq = (pt / q) % q, kq = pt / (q * q);
-    double j0[3], j1[3], j2[3], f[7];
-    hx::trilinear_jacobian(cf + el * 24, T.xq[iq], T.xq[jq], T.xq[kq], j0, j1, j2);
-    const double w = T.wq[iq] * T.wq[jq] * T.wq[kq];
-    const double nuv = nu_q ? nu_q[e * Q3 + pt] : nu;
-    const double det = hx::point_factors(j0, j1, j2, alpha * w, nuv * w, f);
-    if (!(det > 0.0)) ++nbad;
-    for (int c = 0; c < 7; ++c) factors[(e * 7 + c) * Q3 + pt] = f[c];
+    const int iq = col % q, jq = col / q;
+    const double x1 = T.xq[iq], x2 = T.xq[jq], w12 = T.wq[iq] * T.wq[jq];
+    const double* a = cf + el * 24;
+    double P0[3], R0[3], P1[3], R1[3], j2[3];
+    for (int d = 0; d < 3; ++d) {
+      const double* ad = a + d * 8;
+      P0[d] = ad[1] + ad[4] * x2;
+      R0[d] = ad[5] + ad[7] * x2;
+      P1[d] = ad[2] + ad[4] * x1;
+      R1[d] = ad[6] + ad[7] * x1;
+      j2[d] = ad[3] + ad[5] * x1 + (ad[6] + ad[7] * x1) * x2;
+    }
+    for (int kq = 0; kq < q; ++kq) {
+      const double z = T.xq[kq];
+      double j0[3], j1[3], f[7];
+      for (int d = 0; d < 3; ++d) {
+        j0[d] = P0[d] + z * R0[d];
+        j1[d] = P1[d] + z * R1[d];
+      }
+      const int pt = kq * Q2 + col;
+      const double w = w12 * T.wq[kq];
+      const double nuv = nu_q ? nu_q[e * Q3 + pt] : nu;
+      const double det = hx::point_factors(j0, j1, j2, alpha * w, nuv * w, f);
+      if (!(det > 0.0)) ++nbad;
+      for (int c = 0; c < 7; ++c) factors[(e * 7 + c) * Q3 + pt] = f[c];
+    }
   }
   if (nbad) atomicAdd(bad, nbad);
 }
@@ -488,8 +509,8 @@ unsigned grid_for(long long n) {
 
 cudaError_t hx_launch_geometry(const HxTables& T, long long E, const double* X8, const double* nu_q, double alpha,
                                double nu, double* factors, int* bad, cudaStream_t s) {
-  const int Q3 = T.q * T.q * T.q;
-  const int EB = Q3 >= 1024 ? 1 : 1024 / Q3;
+  const int Q2 = T.q * T.q;
+  const int EB = Q2 >= kThreads ? 1 : kThreads / Q2;  // one thread per z-column
   const long long blocks = (E + EB - 1) / EB;
   if (blocks == 0) return cudaSuccess;
   geometry_kernel<<<(unsigned)blocks, kThreads, EB * 24 * sizeof(double), s>>>(T, E, EB, X8, nu_q, alpha, nu, factors, bad);
