@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(kT) mg_cell_kernel(const __grid_constant__ HxT
       hx::trilinear_coeffs(x8, cf);
     }
     const double hs = T.xn[s0 + 1] - T.xn[s0], ht = T.xn[t0 + 1] - T.xn[t0], hu = T.xn[u0 + 1] - T.xn[u0];
-    double a[36];  // upper triangle of the symmetric 8 x 8 cell matrix
+    double a[36];  // upper triangle of the symmetric 8 x 8 cell matrix (constant indices: registers)
+#pragma unroll
     for (int k = 0; k < 36; ++k) a[k] = 0.0;
     for (int qp = 0; qp < 8; ++qp) {
       double j0[3], j1[3], j2[3], f[7];
@@ -298,22 +299,26 @@ __global__ void __launch_bounds__(kT) mg_cell_kernel(const __grid_constant__ HxT
         j2[d] *= 0.5 * hu;
       }
       hx::point_factors(j0, j1, j2, am, nu, f);
-      int k = 0;
+#pragma unroll
       for (int c = 0; c < 8; ++c) {
         const double mc = f[0] * q1[qp][c][0];
         const double gx = q1[qp][c][1], gy = q1[qp][c][2], gz = q1[qp][c][3];
         const double G0 = f[1] * gx + f[2] * gy + f[3] * gz;
         const double G1 = f[2] * gx + f[4] * gy + f[5] * gz;
         const double G2 = f[3] * gx + f[5] * gy + f[6] * gz;
-        for (int c2 = c; c2 < 8; ++c2, ++k)
-          a[k] += mc * q1[qp][c2][0] + G0 * q1[qp][c2][1] + G1 * q1[qp][c2][2] + G2 * q1[qp][c2][3];
+#pragma unroll
+        for (int c2 = c; c2 < 8; ++c2)
+          a[c * 8 - c * (c - 1) / 2 + (c2 - c)] +=
+              mc * q1[qp][c2][0] + G0 * q1[qp][c2][1] + G1 * q1[qp][c2][2] + G2 * q1[qp][c2][3];
       }
     }
     const long long base = cx + sy * cy + sz * cz;
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int dxc = c & 1, dyc = (c >> 1) & 1, dzc = (c >> 2) & 1;
       const long long i = base + dxc + sy * dyc + sz * dzc;
       if (dir[i]) continue;
+#pragma unroll
       for (int c2 = 0; c2 < 8; ++c2) {
         const int dx = (c2 & 1) - dxc, dy = ((c2 >> 1) & 1) - dyc, dz = ((c2 >> 2) & 1) - dzc;
         const long long j = i + dx + sy * dy + sz * dz;
