@@ -381,3 +381,25 @@ def test_mg_vcycle_more_cases(hx, shape, p, q, faces):
     r = np.where(om.dirichlet, 0.0, S.uniform_pm1(991, om.n_dof))
     z = op.precond_apply(to_dev(r)).cpu().numpy()
     assert rel_err(z, precond.vcycle(levels, r, smooth_degree=3)) <= 1e-11
+
+
+@pytest.mark.parametrize("kind,dirichlet", [("LOR_MG", False), ("LOR_MG", True), ("LOR_MC", True)])
+def test_preconditioner_symmetric_positive_at_size(hx, kind, dirichlet):
+    """At 32^3, p = 5 (4.2 M DoFs): the preconditioner is a symmetric positive operator on the
+    constrained space, (B x).y = x.(B y) and (B x).x > 0, as CG requires (a property that holds at
+    any size; the oracle checks the same cycle element by element on small grids)."""
+    N, p = 32, 5
+    V = S.structured_vertices(N, N, N, 0.1, 1910)
+    mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=63 if dirichlet else 0)
+    op = hx.Operator(mesh, 0.0 if not dirichlet else 10.0, 1.0)
+    op.set_preconditioner(getattr(hx, "HX_PREC_" + kind), 2 if kind == "LOR_MG" else 8)
+    dmask = torch.zeros(mesh.n_dof, dtype=torch.bool, device="cuda")
+    if dirichlet:
+        xyz = mesh.node_coords()
+        dmask = ((xyz <= 1e-14) | (xyz >= 1 - 1e-14)).any(dim=1)
+    x = to_dev(S.uniform_pm1(71, mesh.n_dof)).masked_fill(dmask, 0.0)
+    y = to_dev(S.uniform_pm1(72, mesh.n_dof)).masked_fill(dmask, 0.0)
+    bx, by = op.precond_apply(x), op.precond_apply(y)
+    lhs, rhs = torch.dot(bx, y).item(), torch.dot(x, by).item()
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + torch.norm(bx).item() * torch.norm(y).item())
+    assert torch.dot(bx, x).item() > 0
