@@ -496,9 +496,9 @@ def run_batch(hx, torch, args):
     for name, specs, faces_of, prec_of in [
             ("batch64", batch_specs(), lambda k: 63, lambda k: (hx.HX_PREC_JACOBI, 0)),
             ("batch64_mg", batch_specs(), lambda k: 63,
-             lambda k: (hx.HX_PREC_LOR_MG, 2) if batch_specs()[k][2] == 0.0 else (hx.HX_PREC_JACOBI, 0)),
+             lambda k: (hx.HX_PREC_LOR_MG, 1) if batch_specs()[k][2] == 0.0 else (hx.HX_PREC_JACOBI, 0)),
             ("projection_step", [(64, 5, 1000.0, 1e-2)] * 3 + [(64, 5, 0.0, 1.0)], lambda k: 63 if k < 3 else 0,
-             lambda k: (hx.HX_PREC_JACOBI, 0) if k < 3 else (hx.HX_PREC_LOR_MG, 2))]:
+             lambda k: (hx.HX_PREC_JACOBI, 0) if k < 3 else (hx.HX_PREC_LOR_MG, 1))]:
         ops, bs, xs = build(specs, faces_of, prec_of)
         seq = lambda: [hx.hx_solve_pcg(o.handle, b, x, RTOL, 20000, False) for o, b, x in zip(ops, bs, xs)]
         seq()
@@ -609,8 +609,8 @@ def run_precond(hx, torch, args):
     Per preconditioner: set-up time (selection: LOR pattern + values), solve time, iterations."""
     cases = [("poisson_neumann_64_p5", 64, 5, 0.0, 1.0, 0), ("helmholtz_96_p4", 96, 4, 1000.0, 1e-2, 63)]
     precs = [("jacobi", hx.HX_PREC_JACOBI, 0), ("lor_mc_k8", hx.HX_PREC_LOR_MC, 8),
-             ("lor_mc_k16", hx.HX_PREC_LOR_MC, 16), ("lor_mg_s2", hx.HX_PREC_LOR_MG, 2),
-             ("lor_mg_s3", hx.HX_PREC_LOR_MG, 3)]
+             ("lor_mc_k16", hx.HX_PREC_LOR_MC, 16), ("lor_mg_s1", hx.HX_PREC_LOR_MG, 1),
+             ("lor_mg_s2", hx.HX_PREC_LOR_MG, 2)]
     out = {}
     s = torch.cuda.current_stream()
     for name, N, p, alpha, nu, faces in cases:
@@ -638,7 +638,7 @@ def run_precond(hx, torch, args):
             torch.cuda.synchronize()
             res[pname] = {"setup_s": t_setup, "solve_s": e0.elapsed_time(e1) / 1e3, "iterations": info["iterations"],
                           "true_rel_residual": info["true_rel_residual"], "status": info["status"]}
-            if pname in ("jacobi", "lor_mg_s2"):
+            if pname in ("jacobi", "lor_mg_s1"):
                 # the same preconditioner inside the mixed-precision refinement (FP32 inner CG)
                 xm, infom = op.solve_mixed(b, rtol=RTOL)
                 e0.record(s)
@@ -655,7 +655,7 @@ def run_precond(hx, torch, args):
 
 
 def run_vcycle(args):
-    """The LOR multigrid preconditioner alone: one V-cycle (smoothing degree 2) against one
+    """The LOR multigrid preconditioner alone: one V-cycle (smoothing degree 1) against one
     high-order apply on the pure-Neumann Poisson of an N^3, Q_p mesh (the projection step's
     pressure solve); CUDA events, 3 warm-up calls, 10 timed."""
     import torch
@@ -667,7 +667,7 @@ def run_vcycle(args):
     r = torch.as_tensor(S.uniform_pm1(5, mesh.n_dof), device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    op.set_preconditioner(hx.HX_PREC_LOR_MG, 2)
+    op.set_preconditioner(hx.HX_PREC_LOR_MG, 1)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     s = torch.cuda.current_stream()
