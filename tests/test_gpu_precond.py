@@ -265,7 +265,8 @@ def test_lor_errors(hx):
 # geometric multigrid V-cycle on the LOR matrix (Sec. 5.2)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("N,p,dirichlet,alpha,deg", [(4, 2, True, 0.0, 3), (2, 4, True, 5.0, 2), (4, 2, False, 0.0, 3),
-                                                     (3, 3, True, 1.0, 3), (4, 4, True, 100.0, 4)])
+                                                     (3, 3, True, 1.0, 3), (4, 4, True, 100.0, 4), (4, 2, True, 0.0, 1),
+                                                     (4, 4, False, 0.0, 1), (2, 4, True, 5.0, 1)])
 def test_mg_vcycle_matches_oracle(hx, N, p, dirichlet, alpha, deg):
     from oracle import precond
     shape = (N, N, N)
