@@ -93,13 +93,15 @@ __global__ void __launch_bounds__(kT) mg_cheb_first_kernel(long long n, const Re
                                                            const Real* __restrict__ b, Real* __restrict__ res,
                                                            Real* __restrict__ d, Real* __restrict__ x,
                                                            const double* __restrict__ coef, int accumulate,
-                                                           const int* done) {
+                                                           int more, const int* done) {
   if (done && *(volatile const int*)done) return;
   const Real c0 = Real(coef[0]);
   MG_STRIDE(i, n) {
     const Real s = dinv[i] * b[i];
-    res[i] = s;
-    d[i] = c0 * s;
+    if (more) {  // the recurrence continues: keep its residual and direction
+      res[i] = s;
+      d[i] = c0 * s;
+    }
     x[i] = accumulate ? x[i] + c0 * s : c0 * s;
   }
 }
@@ -401,7 +403,8 @@ cudaError_t smooth(const LevelView<Real>& L, const Real* b, Real* x, int degree,
                    cudaStream_t s) {
   const StencilRowsT<Real> A{L.g, L.val};
   const unsigned g = grid_of(L.g.n);
-  mg_cheb_first_kernel<Real><<<g, kT, 0, s>>>(L.g.n, L.dinv, b, L.res, L.d0, x, L.coef, accumulate, done);
+  mg_cheb_first_kernel<Real><<<g, kT, 0, s>>>(L.g.n, L.dinv, b, L.res, L.d0, x, L.coef, accumulate, degree > 1,
+                                              done);
   cudaError_t e = cudaGetLastError();
   Real* din = L.d0;
   Real* dout = L.d1;
