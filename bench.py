@@ -24,6 +24,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hx|reference]
                        [--p P] [--n N] [--geom stored|onthefly] [--no-cpu] [--no-mixed]
                        [--sweep] [--grad] [--precond] [--batch [--batch-reps R]]
        python bench.py --vcycle [--p P] [--n N]     (the LOR multigrid V-cycle alone)
+       python bench.py --cheb [--p P] [--n N]       (the LOR-Chebyshev preconditioner alone)
 """
 from __future__ import annotations
 
@@ -687,6 +688,46 @@ def run_vcycle(args):
                       "setup_s": t_setup, **out}), flush=True)
 
 
+def run_cheb(args):
+    """The LOR-Chebyshev preconditioner (HX_PREC_LOR_MC) alone on the pure-Neumann Poisson of an
+    N^3, Q_p mesh: one application at degree 1 (the Jacobi step) and at degree 16; the 15
+    Chebyshev steps (one sliced-ELL SpMV each) take the difference.  Algorithmic bytes of a step:
+    12 B per stored entry (value + column) + 56 B per row (own d_in, D^-1, res read/write, d_out,
+    z read/write); the gathered neighbours of d_in are taken as cache hits.  CUDA events, 3 warm-up
+    calls, 10 timed."""
+    import torch
+    import paper_1910_03032_b300 as hx
+    N, p = args.n, args.p
+    V = S.structured_vertices(N, N, N, 0.1, S.DEFAULT_MESH_SEED)
+    mesh = hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=0)
+    op = hx.Operator(mesh, 0.0, 1.0)
+    r = torch.as_tensor(S.uniform_pm1(5, mesh.n_dof), device="cuda")
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for k in (1, 16):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op.set_preconditioner(hx.HX_PREC_LOR_MC, k)
+        torch.cuda.synchronize()
+        out[f"setup_k{k}_s"] = time.perf_counter() - t0
+        for _ in range(3):
+            op.precond_apply(r)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(10):
+            op.precond_apply(r)
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[f"k{k}_ms"] = e0.elapsed_time(e1) / 10
+    nnz = op.lor_csr()[1].numel()
+    step_ms = (out["k16_ms"] - out["k1_ms"]) / 15
+    step_bytes = 12 * nnz + 56 * mesh.n_dof
+    print(json.dumps({"probe": "lor_chebyshev", "mesh": f"{N}^3", "p": p, "n_dof": mesh.n_dof, "nnz": nnz, **out,
+                      "step_ms": step_ms, "step_bytes": step_bytes, "step_gbs": step_bytes / step_ms / 1e6}),
+          flush=True)
+
+
 def run_sweep(hx, torch):
     """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
     out = []
@@ -730,6 +771,8 @@ def main():
     ap.add_argument("--precond", action="store_true", help="add the preconditioner comparison (Jacobi vs LOR)")
     ap.add_argument("--vcycle", action="store_true",
                     help="time one LOR multigrid V-cycle against one apply (pure-Neumann Poisson, --p, --n) and exit")
+    ap.add_argument("--cheb", action="store_true",
+                    help="time the LOR-Chebyshev preconditioner at degrees 1 and 16 (pure-Neumann Poisson, --p, --n) and exit")
     ap.add_argument("--grad", action="store_true", help="add the adjoint-gradient measurement (32^3, p = 4)")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
@@ -743,6 +786,9 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.vcycle:
         run_vcycle(args)
+        return
+    if args.cheb:
+        run_cheb(args)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":

@@ -125,7 +125,7 @@ struct hx_op {
   bool dinv_stale = true;
   bool has_field = false;       // the coefficients include a per-point nu field
   // low-order refined operator (Sec. 5.2) and its Chebyshev-Jacobi inverse (HX_PREC_LOR)
-  HxLorMatrix lor = {0, nullptr, nullptr, nullptr, nullptr};
+  HxLorMatrix lor = {};
   long long lor_nnz = 0;
   bool lor_values_set = false;        // values of the current alpha, nu assembled
   int lor_collocated = 0;             // 1: alpha Mc + nu K_LOR (HX_PREC_LOR_MC)
@@ -413,6 +413,9 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->lor.col);
   dfree(op->lor.val);
   dfree(op->lor.dinv);
+  dfree(op->lor.soff);
+  dfree(op->lor.scol);
+  dfree(op->lor.sval);
   dfree(op->lor_bound);
   dfree(op->cheb.res);
   dfree(op->cheb.d0);
@@ -539,7 +542,7 @@ hx_status lor_csr_values(hx_op* op, cudaStream_t s, int* nl) {
                        s),
          "LOR values");
   HX_TRY(hx_lor_coefficients(op->lor_bound, op->cheb.degree, op->cheb.coef, s), "Chebyshev coefficients");
-  *nl += 3;
+  *nl += 4;
   op->lor_values_set = true;
   return HX_OK;
 }
@@ -656,8 +659,29 @@ hx_status lor_setup(hx_op* op, int degree, cudaStream_t s) {
       if ((st = dalloc(&op->lor.col, (size_t)nnz, "LOR columns")) || (st = dalloc(&op->lor.val, (size_t)nnz, "LOR values")))
         break;
       e = hx_lor_fill(b, op->lor.off, op->lor.col, s);
-      if (e != cudaSuccess) st = cuda_fail(e, "LOR pattern fill");
-      op->launches += 6;
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "LOR pattern fill");
+        break;
+      }
+      // the sliced-ELL copy: slice widths, their offsets, then the columns
+      const long long ns = (n + 31) / 32;
+      long long sn = 0;
+      if ((st = dalloc(&op->lor.soff, (size_t)ns + 1, "LOR slice offsets"))) break;
+      e = hx_lor_sell_count(n, op->lor.off, count, s);
+      if (e == cudaSuccess) e = hx_lor_scan(ns, count, sums, op->lor.soff, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&sn, op->lor.soff + ns, sizeof(long long), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "LOR slices");
+        break;
+      }
+      if ((st = dalloc(&op->lor.scol, (size_t)sn, "LOR slice columns")) ||
+          (st = dalloc(&op->lor.sval, (size_t)sn, "LOR slice values")))
+        break;
+      op->lor.n = n;
+      e = hx_lor_sell_copy(op->lor, op->lor.col, nullptr, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "LOR slice columns");
+      op->launches += 6 + 5;
     } while (0);
     dfree(count);
     dfree(sums);
@@ -665,8 +689,14 @@ hx_status lor_setup(hx_op* op, int degree, cudaStream_t s) {
     if (st) {
       dfree(op->lor.col);
       dfree(op->lor.val);
+      dfree(op->lor.soff);
+      dfree(op->lor.scol);
+      dfree(op->lor.sval);
       op->lor.col = nullptr;
       op->lor.val = nullptr;
+      op->lor.soff = nullptr;
+      op->lor.scol = nullptr;
+      op->lor.sval = nullptr;
       return st;
     }
     op->lor.n = n;

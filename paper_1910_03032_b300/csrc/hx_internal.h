@@ -181,6 +181,12 @@ struct HxLorMatrix {
   int* col;        // [nnz], sorted per row
   double* val;     // [nnz], Dirichlet rows and columns eliminated (identity rows)
   double* dinv;    // [n]
+  // Sliced-ELL copy for the Chebyshev steps: rows in slices of 32, each slice stored column-major
+  // over its longest row, so entry k of row g sits at soff[g / 32] + 32 k + g % 32 and a warp's
+  // loads are coalesced.  Padding entries have value 0 (column g; column 0 past the last row).
+  long long* soff; // [ceil(n / 32) + 1]
+  int* scol;
+  double* sval;
 };
 struct HxChebWork {
   int degree;      // Chebyshev steps (1: plain LOR-Jacobi)
@@ -193,6 +199,11 @@ cudaError_t hx_lor_count(const HxLorBuild& b, long long* count, int* bad, cudaSt
 long long hx_lor_scan_blocks(long long n);
 cudaError_t hx_lor_scan(long long n, const long long* count, long long* sums, long long* off, cudaStream_t s);
 cudaError_t hx_lor_fill(const HxLorBuild& b, const long long* off, int* col, cudaStream_t s);
+// Sliced-ELL pattern: count[t] = 32 x (the longest row of slice t), t < ceil(n / 32)
+cudaError_t hx_lor_sell_count(long long n, const long long* off, long long* count, cudaStream_t s);
+// Copies the CSR columns (col != nullptr) and/or values (val != nullptr) into the sliced-ELL arrays
+// of A (A.soff set), with the padding entries.
+cudaError_t hx_lor_sell_copy(const HxLorMatrix& A, const int* col, const double* val, cudaStream_t s);
 // collocated = 0: alpha M_LOR + nu K_LOR; 1: alpha Mc + nu K_LOR (collocated Gauss-Lobatto mass)
 cudaError_t hx_lor_values(const HxTables& T, const HxLorBuild& b, const double* X8, double alpha, double nu,
                           int collocated, const HxLorMatrix& A, unsigned long long* bound, cudaStream_t s);

@@ -11,7 +11,8 @@
 // The matrix is stored in CSR with the Dirichlet rows and columns eliminated (identity rows),
 // built row by row without atomics: a row visits the (element, local node) pairs of its DoF
 // through the transpose map and the (up to 8) sub-elements around each, in a fixed order, so
-// pattern and values are deterministic.
+// pattern and values are deterministic.  The Chebyshev steps read a sliced-ELL copy (slices of
+// 32 rows, column-major), refreshed from the CSR values whenever they change.
 #include <cuda_runtime.h>
 
 #include "hx_element.cuh"
@@ -274,9 +275,12 @@ __global__ void __launch_bounds__(kT) cheb_first_kernel(long long n, const doubl
   }
 }
 
-// res -= D^-1 A d_in, d_out = c1 d_in + c2 res, z += d_out
-__global__ void __launch_bounds__(kT) cheb_step_kernel(long long n, const long long* __restrict__ off,
-                                                       const int* __restrict__ col, const double* __restrict__ val,
+constexpr int kB = 9;  // entries per load batch in the Chebyshev step (27 = 3 batches on a hex mesh)
+
+// res -= D^-1 A d_in, d_out = c1 d_in + c2 res, z += d_out.  One thread per row over the sliced-ELL
+// copy; the grid stride is a multiple of 32, so a warp always covers one slice.
+__global__ void __launch_bounds__(kT, 8) cheb_step_kernel(long long n, const long long* __restrict__ soff,
+                                                       const int* __restrict__ scol, const double* __restrict__ sval,
                                                        const double* __restrict__ dinv, const double* __restrict__ din,
                                                        double* __restrict__ dout, double* __restrict__ res,
                                                        double* __restrict__ z, const double* __restrict__ coef, int j,
@@ -284,13 +288,61 @@ __global__ void __launch_bounds__(kT) cheb_step_kernel(long long n, const long l
   if (done && *(volatile const int*)done) return;
   const double c1 = coef[2 * j], c2 = coef[2 * j + 1];
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+    const long long s0 = __ldg(soff + (g >> 5)), s1 = __ldg(soff + (g >> 5) + 1);
+    const int w = (int)((s1 - s0) >> 5);
+    const long long b = s0 + (g & 31);
+    // batches of kB entries: all their column and value loads issue before the dependent
+    // gathers of d_in, so each thread keeps several memory requests in flight
     double ad = 0.0;
-    for (long long o = off[g]; o < off[g + 1]; ++o) ad += __ldg(val + o) * __ldg(din + __ldg(col + o));
+    int k = 0;
+    for (; k + kB <= w; k += kB) {
+      int c[kB];
+      double v[kB];
+#pragma unroll
+      for (int a = 0; a < kB; ++a) {
+        c[a] = __ldg(scol + b + 32LL * (k + a));
+        v[a] = __ldg(sval + b + 32LL * (k + a));
+      }
+#pragma unroll
+      for (int a = 0; a < kB; ++a) ad += v[a] * __ldg(din + c[a]);
+    }
+    for (; k < w; ++k) ad += __ldg(sval + b + 32LL * k) * __ldg(din + __ldg(scol + b + 32LL * k));
     const double rs = res[g] - dinv[g] * ad;
     res[g] = rs;
     const double dn = c1 * din[g] + c2 * rs;
     dout[g] = dn;
     z[g] += dn;
+  }
+}
+
+// count[t] = 32 x the longest row of slice t
+__global__ void __launch_bounds__(kT) sell_count_kernel(long long n, const long long* __restrict__ off,
+                                                        long long* __restrict__ count) {
+  const long long ns = (n + 31) / 32;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ns; t += (long long)gridDim.x * blockDim.x) {
+    long long w = 0;
+    const long long g1 = (32 * t + 32 < n) ? 32 * t + 32 : n;
+    for (long long g = 32 * t; g < g1; ++g) w = max(w, off[g + 1] - off[g]);
+    count[t] = 32 * w;
+  }
+}
+
+// one thread per (slice, lane) position: row g's entries in slice order, then the padding
+__global__ void __launch_bounds__(kT) sell_copy_kernel(long long n, const long long* __restrict__ off,
+                                                       const int* __restrict__ col, const double* __restrict__ val,
+                                                       const long long* __restrict__ soff, int* __restrict__ scol,
+                                                       double* __restrict__ sval) {
+  const long long np = 32 * ((n + 31) / 32);
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < np; g += (long long)gridDim.x * blockDim.x) {
+    const long long s0 = soff[g >> 5];
+    const int w = (int)((soff[(g >> 5) + 1] - s0) >> 5);
+    const long long b = s0 + (g & 31);
+    const long long o0 = g < n ? off[g] : 0;
+    const int len = g < n ? (int)(off[g + 1] - o0) : 0;
+    for (int k = 0; k < w; ++k) {
+      if (col) scol[b + 32LL * k] = k < len ? col[o0 + k] : (g < n ? (int)g : 0);
+      if (val) sval[b + 32LL * k] = k < len ? val[o0 + k] : 0.0;
+    }
   }
 }
 
@@ -391,6 +443,17 @@ cudaError_t hx_lor_fill(const HxLorBuild& b, const long long* off, int* col, cud
   return cudaGetLastError();
 }
 
+cudaError_t hx_lor_sell_count(long long n, const long long* off, long long* count, cudaStream_t s) {
+  sell_count_kernel<<<grid_of((n + 31) / 32), kT, 0, s>>>(n, off, count);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_lor_sell_copy(const HxLorMatrix& A, const int* col, const double* val, cudaStream_t s) {
+  sell_copy_kernel<<<grid_of(A.n), kT, 0, s>>>(A.n, A.off, col, val, A.soff, col ? A.scol : nullptr,
+                                               val ? A.sval : nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t hx_lor_values(const HxTables& T, const HxLorBuild& b, const double* X8, double alpha, double nu,
                           int collocated, const HxLorMatrix& A, unsigned long long* bound, cudaStream_t s) {
   lor_values_kernel<<<grid_of(b.n), kT, 0, s>>>(T, b.n, b.toff, b.tidx, b.R, b.dir, X8, alpha, nu, collocated, A.off,
@@ -400,7 +463,9 @@ cudaError_t hx_lor_values(const HxTables& T, const HxLorBuild& b, const double* 
   e = cudaMemsetAsync(bound, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   lor_diag_kernel<<<grid_of(b.n), kT, 0, s>>>(b.n, A.off, A.col, A.val, A.dinv, bound);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !A.sval) return e;
+  return hx_lor_sell_copy(A, nullptr, A.val, s);
 }
 
 cudaError_t hx_lor_coefficients(const unsigned long long* bound, int degree, double* coef, cudaStream_t s) {
@@ -416,7 +481,7 @@ cudaError_t hx_lor_precondition(const HxLorMatrix& A, const HxChebWork& w, const
   double* din = w.d0;
   double* dout = w.d1;
   for (int j = 1; j < w.degree && e == cudaSuccess; ++j) {
-    cheb_step_kernel<<<g, kT, 0, s>>>(A.n, A.off, A.col, A.val, A.dinv, din, dout, w.res, z, w.coef, j, done);
+    cheb_step_kernel<<<g, kT, 0, s>>>(A.n, A.soff, A.scol, A.sval, A.dinv, din, dout, w.res, z, w.coef, j, done);
     e = cudaGetLastError();
     double* t = din;
     din = dout;
