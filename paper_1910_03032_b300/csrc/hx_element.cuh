@@ -243,14 +243,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar) {
 // ---------------------------------------------------------------------------
 //
 // FP32 (4-byte banks, shared-memory-bound kernel): rows are not padded (SY = q), so the
-// column stages of consecutive threads read consecutive words; the plane stride is odd
-// for the line stages; and the element stride is padded so that the columns of the next
-// element continue the bank sequence (R3 = q^2 mod 32) for warps that straddle elements.
+// column stages of consecutive threads read consecutive words; the plane stride SZ >= q^2 is
+// the one that gives the fewest shared-memory wavefronts over all stages of the operator
+// kernel's block (a count of the distinct words per bank of every warp access, taken for each
+// q at its block shape; odd q^2 | 1 where no other stride does markedly better); and the
+// element stride is padded so that the columns of the next element continue the bank
+// sequence (R3 = q^2 mod 32) for warps that straddle elements.
+template <int Q>
+constexpr int f32_plane_stride() {
+  return Q == 3 ? 14 : Q == 4 ? 27 : Q == 6 ? 39 : Q == 7 ? 72 : Q == 8 ? 73 : Q == 10 ? 107 : ((Q * Q) | 1);
+}
 template <int Q, typename Real = double>
 struct Layout {
   static constexpr bool F32 = sizeof(Real) == 4;
   static constexpr int SY = F32 ? Q : ((Q % 2 == 0) ? Q + 1 : Q);
-  static constexpr int SZ = F32 ? ((Q * Q) | 1) : Q * SY;
+  static constexpr int SZ = F32 ? f32_plane_stride<Q>() : Q * SY;
+  static_assert(SZ >= Q * SY, "planes must not overlap");
   static constexpr int RG = Q * SZ;  // one region
   // the three regions D, X, Y of one element (element stride)
   static constexpr int R3 = F32 ? 3 * RG + (((Q * Q - 3 * RG) % 32) + 32) % 32 : 3 * RG;
