@@ -222,3 +222,26 @@ def test_destroy_mesh_before_operator(hx):
     op = hx.hx_op_create(m, 1.0, 1.0)
     hx.hx_mesh_destroy(m)
     hx.hx_op_destroy(op)
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_unstructured_mesh(hx, p):
+    """A mesh whose central edge has valence 5 (10 elements share its DoFs), numbering from node
+    positions: both geometry modes vs the oracle, constrained and not, and a Jacobi-PCG solve."""
+    from oracle import fem
+    from oracle.solve import jacobi_pcg
+    from tests.unstructured import star_prism
+    V, EV, om = star_prism(p)
+    mesh = hx.Mesh.general(p, p + 2, V, EV, om.n_dof, om.restriction.astype(np.int32),
+                           om.dirichlet.astype(np.uint8))
+    oop = fem.Operator(om, 1.3, 0.7)
+    x = S.random_vector(om.n_dof, 81)
+    for gm in (hx.HX_GEOM_STORED, hx.HX_GEOM_ONTHEFLY):
+        op = hx.Operator(mesh, 1.3, 0.7, geom_mode=gm)
+        for constrained in (False, True):
+            _assert_close(op.apply(to_dev(x), constrained=constrained).cpu().numpy(),
+                          oop.apply(x, constrained=constrained))
+    b = S.random_vector(om.n_dof, 82)
+    u, info = op.solve(to_dev(b), rtol=1e-10)
+    assert info["status"] == 0 and info["true_rel_residual"] <= 1.01e-10
+    assert rel_err(u.cpu().numpy(), jacobi_pcg(oop, b, 1e-12)[0]) <= 1e-8

@@ -134,6 +134,35 @@ def test_lor_matrix_matches_oracle(hx, p, dirichlet):
     assert np.array_equal(A != 0, Ao != 0) or np.all(np.abs(Ao[(A != 0) != (Ao != 0)]) <= 1e-14 * np.abs(Ao).max())
 
 
+@pytest.mark.parametrize("p", [2, 3])
+def test_lor_on_unstructured_mesh(hx, p):
+    """Valence-5 central edge: LOR rows of 33 entries (sliced-ELL slices wider than 27 and a
+    partial load batch) vs the oracle: the matrix, the Chebyshev apply of both mass forms, and
+    the LOR-PCG solution."""
+    from oracle import fem, precond
+    from oracle.solve import jacobi_pcg
+    from tests.unstructured import star_prism
+    V, EV, om = star_prism(p)
+    mesh = hx.Mesh.general(p, p + 2, V, EV, om.n_dof, om.restriction.astype(np.int32),
+                           om.dirichlet.astype(np.uint8))
+    op = hx.Operator(mesh, 2.0, 0.7)
+    op.set_preconditioner(hx.HX_PREC_LOR, 5)
+    ro, col, val = op.lor_csr()
+    assert int(np.diff(ro.cpu().numpy()).max()) == 33
+    A = _dense(ro, col, val, om.n_dof)
+    Ao = precond.lor_operator(om, 2.0, 0.7).assembled(constrained=True)
+    assert np.abs(A - Ao).max() <= 1e-13 * np.abs(Ao).max()
+    r = np.where(om.dirichlet, 0.0, S.uniform_pm1(71, om.n_dof))
+    assert rel_err(op.precond_apply(to_dev(r)).cpu().numpy(), precond.chebyshev_apply(Ao, r, 5)) <= 1e-12
+    op.set_preconditioner(hx.HX_PREC_LOR_MC, 7)
+    Amc = precond.lor_matrix(om, 2.0, 0.7, "collocated")
+    assert rel_err(op.precond_apply(to_dev(r)).cpu().numpy(), precond.chebyshev_apply(Amc, r, 7)) <= 1e-12
+    b = S.random_vector(om.n_dof, 72)
+    x, info = op.solve(to_dev(b), rtol=1e-10)
+    assert info["status"] == 0 and info["true_rel_residual"] <= 1.01e-10
+    assert rel_err(x.cpu().numpy(), jacobi_pcg(fem.Operator(om, 2.0, 0.7), b, 1e-12)[0]) <= 1e-8
+
+
 def test_lor_matrix_follows_coefficients(hx):
     from oracle import precond
     p, shape = 3, (2, 2, 2)

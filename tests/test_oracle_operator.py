@@ -114,3 +114,22 @@ def test_nu_field_linearity():
     K2 = fem.Operator(mesh, 0.0, nu2).apply(x)
     K12 = fem.Operator(mesh, 0.0, nu1 + 2 * nu2).apply(x)
     np.testing.assert_allclose(K12, K1 + 2 * K2, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_unstructured_star_prism(p):
+    """A mesh whose central edge has valence 5 (numbering from node positions): 1^T M 1 is the
+    prism's closed-form volume (bilinear quads, linear in z: the quadrature is exact), K 1 = 0,
+    and the assembled matrix is symmetric with a one-dimensional null space of K."""
+    from tests.unstructured import star_prism, star_prism_volume
+    V, EV, om = star_prism(p, dirichlet_bottom=False)
+    one = np.ones(om.n_dof)
+    assert abs(one @ fem.Operator(om, 1.0, 0.0).apply(one) - star_prism_volume()) < 1e-13
+    K = fem.Operator(om, 0.0, 1.0)
+    assert np.abs(K.apply(one)).max() < 1e-13
+    assert np.bincount(om.restriction.ravel()).max() == 10     # the central edge: 5 sectors x 2 layers
+    if p <= 2:
+        A = K.assembled()
+        assert np.abs(A - A.T).max() < 1e-13
+        ev = np.linalg.eigvalsh(A)
+        assert abs(ev[0]) < 1e-11 and ev[1] > 1e-6

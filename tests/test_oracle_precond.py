@@ -257,3 +257,22 @@ def test_mg_pcg_iterations_bounded_under_refinement():
             its.append(it + 1)
     assert its_mg[-1] <= its_mg[0] + 6 and its_mg[-1] <= 20, its_mg
     assert its_j[-1] >= 2 * its_j[1] - 5 and its_j[-1] > 3 * its_mg[-1], its_j
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_lor_on_unstructured_star_prism(p):
+    """The LOR matrix on a mesh whose central edge has valence 5: 1^T M_LOR 1 = the volume (the
+    sub-elements of a multilinear map tile it exactly), K_LOR 1 = 0, and the rows of the central
+    edge's interior DoFs couple to 2 x 5 + 1 = 11 nodes in each of 3 layers (33 entries)."""
+    from tests.unstructured import star_prism, star_prism_volume
+    V, EV, om = star_prism(p, dirichlet_bottom=False)
+    one = np.ones(om.n_dof)
+    M = precond.lor_matrix(om, 1.0, 0.0, constrained=False)
+    assert abs(one @ M @ one - star_prism_volume()) < 1e-13
+    K = precond.lor_matrix(om, 0.0, 1.0, constrained=False)
+    assert np.abs(K @ one).max() < 1e-13
+    X = om.node_coords()
+    axis = (np.hypot(X[:, 0], X[:, 1]) < 1e-12) & (X[:, 2] > 1e-12) & (X[:, 2] < 1 - 1e-12)
+    assert axis.sum() == 3 * p - 1
+    assert np.all((K[axis] != 0).sum(axis=1) == 33)
+    assert (K != 0).sum(axis=1).max() == 33
