@@ -658,7 +658,8 @@ def run_precond(hx, torch, args):
 def run_vcycle(args):
     """The LOR multigrid preconditioner alone: one V-cycle (smoothing degree 1) against one
     high-order apply on the pure-Neumann Poisson of an N^3, Q_p mesh (the projection step's
-    pressure solve); CUDA events, 3 warm-up calls, 10 timed."""
+    pressure solve); CUDA events, 3 warm-up calls, 10 timed.  Then the FP64 MG-PCG solve and
+    the mixed-precision solve with the FP32 V-cycle, each timed on its second call."""
     import torch
     import paper_1910_03032_b300 as hx
     N, p = args.n, args.p
@@ -684,6 +685,17 @@ def run_vcycle(args):
         e1.record(s)
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / 10
+    # the two solves that use it, to 1e-10: FP64 MG-PCG and the mixed-precision refinement
+    # (FP32 inner CG with the FP32 V-cycle); the second call of each is timed
+    b = r - r.mean()
+    for name, fn in (("solve", lambda: op.solve(b, rtol=RTOL)), ("solve_mixed", lambda: op.solve_mixed(b, rtol=RTOL))):
+        fn()
+        e0.record(s)
+        x, info = fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[name + "_s"] = e0.elapsed_time(e1) / 1e3
+        out[name + "_iterations"] = info["iterations"]
     print(json.dumps({"probe": "lor_multigrid_vcycle", "mesh": f"{N}^3", "p": p, "n_dof": mesh.n_dof,
                       "setup_s": t_setup, **out}), flush=True)
 

@@ -54,11 +54,36 @@ template <typename Real>
 struct StencilRowsT {
   HxGrid g;
   const Real* val;  // [27][n]
+  // Row i times x.  FP64 rows are bound by the FP64 pipe (27 multiply-adds per 240 B); FP32 rows
+  // by memory latency, so each z-plane's 9 stencil values (always in bounds: [27][n]) and 9
+  // neighbours (an out-of-grid neighbour reads x[i] instead) are loaded before any is used and
+  // the out-of-grid terms skipped afterwards, in the same order.
   __device__ __forceinline__ Real dot(long long i, const Real* __restrict__ x) const {
     int ix, iy, iz;
     coords(g, i, ix, iy, iz);
     const long long sy = g.mx, sz = (long long)g.mx * g.my;
     Real s = Real(0);
+    if constexpr (sizeof(Real) == 4) {
+      const bool okx[3] = {ix > 0, true, ix + 1 < g.mx}, oky[3] = {iy > 0, true, iy + 1 < g.my};
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        const bool okz = iz + dz >= 0 && iz + dz < g.mz;
+        Real v[9], xv[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          const int dx = a % 3 - 1, dy = a / 3 - 1;
+          const bool ok = okz && oky[dy + 1] && okx[dx + 1];
+          v[a] = __ldg(val + (long long)((dz + 1) * 9 + a) * g.n + i);
+          xv[a] = __ldg(x + (ok ? i + dx + dy * sy + dz * sz : i));
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          const int dx = a % 3 - 1, dy = a / 3 - 1;
+          if (okz && oky[dy + 1] && okx[dx + 1]) s += v[a] * xv[a];
+        }
+      }
+      return s;
+    }
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
       if (iz + dz < 0 || iz + dz >= g.mz) continue;
@@ -131,25 +156,39 @@ __global__ void __launch_bounds__(kT) mg_residual_kernel(Rows A, long long n, co
 }
 
 // b_c = P^T r_f
+// The transfer weights are powers of 1/2, exact in either precision: the restriction's are
+// compile-time constants of the unrolled 27-point loop, and every term of a prolongation shares
+// one weight (1/2 per odd coordinate of the fine node), applied once to the sum of the coarse
+// values (scaling by a power of 2 is exact, so the sum is the same as term by term).
 template <typename Real>
 __global__ void __launch_bounds__(kT) mg_restrict_kernel(HxGrid fg, const unsigned char* __restrict__ fdir,
                                                          const Real* __restrict__ rf, HxGrid cg,
                                                          const unsigned char* __restrict__ cdir,
                                                          Real* __restrict__ bc, const int* done) {
   if (done && *(volatile const int*)done) return;
+  const long long sy = fg.mx, sz = (long long)fg.mx * fg.my;
   MG_STRIDE(I, cg.n) {
     Real s = Real(0);
     if (!cdir[I]) {
       int X, Y, Z;
       coords(cg, I, X, Y, Z);
-      for (int k = 0; k < 27; ++k) {
-        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-        const int ix = 2 * X + dx, iy = 2 * Y + dy, iz = 2 * Z + dz;
-        if (!inside(fg, ix, iy, iz)) continue;
-        const long long i = index(fg, ix, iy, iz);
-        if (fdir[i]) continue;
-        const Real w = Real((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-        s += w * rf[i];
+      const int cx = 2 * X, cy = 2 * Y, cz = 2 * Z;
+      const long long c = index(fg, cx, cy, cz);
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        if (cz + dz < 0 || cz + dz >= fg.mz) continue;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          if (cy + dy < 0 || cy + dy >= fg.my) continue;
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (cx + dx < 0 || cx + dx >= fg.mx) continue;
+            const long long i = c + dx + dy * sy + dz * sz;
+            if (fdir[i]) continue;
+            const Real w = Real(1) / Real(1 << ((dx != 0) + (dy != 0) + (dz != 0)));
+            s += w * rf[i];
+          }
+        }
       }
     }
     bc[I] = s;
@@ -163,29 +202,23 @@ __global__ void __launch_bounds__(kT) mg_prolong_kernel(HxGrid cg, const unsigne
                                                         const unsigned char* __restrict__ fdir,
                                                         Real* __restrict__ xf, const int* done) {
   if (done && *(volatile const int*)done) return;
+  const long long sy = cg.mx, sz = (long long)cg.mx * cg.my;
   MG_STRIDE(i, fg.n) {
     if (fdir[i]) continue;
     int ix, iy, iz;
     coords(fg, i, ix, iy, iz);
+    // coarse neighbours: (i/2) and, along an odd coordinate, (i/2) + 1 as well
+    const int ox = ix & 1, oy = iy & 1, oz = iz & 1;
+    const long long J0 = index(cg, ix >> 1, iy >> 1, iz >> 1);
     Real s = Real(0);
-    for (int oz = 0; oz < 2; ++oz) {
-      if ((iz & 1) == 0 && oz) break;
-      const int Z = (iz & 1) ? (iz - 1) / 2 + oz : iz / 2;
-      const double wz = (iz & 1) ? 0.5 : 1.0;
-      for (int oy = 0; oy < 2; ++oy) {
-        if ((iy & 1) == 0 && oy) break;
-        const int Y = (iy & 1) ? (iy - 1) / 2 + oy : iy / 2;
-        const double wy = (iy & 1) ? 0.5 : 1.0;
-        for (int ox = 0; ox < 2; ++ox) {
-          if ((ix & 1) == 0 && ox) break;
-          const int X = (ix & 1) ? (ix - 1) / 2 + ox : ix / 2;
-          const double wx = (ix & 1) ? 0.5 : 1.0;
-          const long long J = index(cg, X, Y, Z);
-          if (!cdir[J]) s += Real(wx * wy * wz) * xc[J];
+    for (int bz = 0; bz <= oz; ++bz)
+      for (int by = 0; by <= oy; ++by)
+        for (int bx = 0; bx <= ox; ++bx) {
+          const long long J = J0 + bx + by * sy + bz * sz;
+          if (!cdir[J]) s += xc[J];
         }
-      }
-    }
-    xf[i] += s;
+    const int k = ox + oy + oz;
+    xf[i] += s * (k == 0 ? Real(1) : k == 1 ? Real(0.5) : k == 2 ? Real(0.25) : Real(0.125));
   }
 }
 
