@@ -206,7 +206,8 @@ HX_API hx_status hx_op_load_vector(hx_op* op, const double* f_q, double* b, void
 /*
  * Jacobi-preconditioned CG (Sec. 5, Sec. 5.3; Jacobi = diagonal of A_c) for
  * A_c x = P b.  Stops when ||r_k||_2 <= rtol ||P b||_2 (recurrence residual) or
- * after max_it iterations.
+ * after max_it iterations (max_it = 0: no iteration; HX_ERR_NOT_CONVERGED
+ * unless the initial residual already meets the tolerance, as when P b = 0).
  *   b         device, n_dof (entries at Dirichlet DoFs are ignored)
  *   x         device, n_dof; input initial guess if use_x0 != 0 (Dirichlet
  *             entries taken as 0), else ignored; output solution (0 at Dirichlet DoFs)

@@ -263,7 +263,8 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffers
   HX_GRID_STRIDE(g, B.n) { B.r[g] -= B.Ap[g]; }
 }
 
-// z = D^-1 r, p = z; rz = (r, z), rr = (r, r); finishes at once if rr <= tol^2 ||b||^2.
+// z = D^-1 r, p = z; rz = (r, z), rr = (r, r); finishes at once if rr <= tol^2 ||b||^2, or
+// as not converged if the iteration cap is 0.
 // Null-space mode also sums z and r: the preconditioned residual is orthogonalized against
 // the constants (z - mean z, Sec. 5.3) and p is finished by a direction pass with beta = 0.
 template <typename Real>
@@ -292,6 +293,9 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffersT<R
       s->status = -6;  // HX_ERR_BREAKDOWN
       s->done = 1;
     } else if (out[1] <= s->tol2) {
+      s->done = 1;
+    } else if (s->max_it <= 0) {
+      s->status = -5;  // HX_ERR_NOT_CONVERGED: no iteration allowed
       s->done = 1;
     }
   }
