@@ -45,9 +45,12 @@ hx_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// Allocates *p unless it is already allocated: every buffer keeps one size for its owner's
+// lifetime (a buffer to be resized is freed first), so a group of allocations that failed part
+// way is completed, without leaks, by the next call.  Targets start as nullptr.
 template <typename T>
 hx_status dalloc(T** p, size_t count, const char* what) {
-  *p = nullptr;
+  if (*p) return HX_OK;
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) {
@@ -96,6 +99,7 @@ struct hx_op {
   double* scalars = nullptr;            // [2] device scalars (dot products)
   unsigned int* counters = nullptr;     // [2]
   HxCgState* st = nullptr;
+  bool solver_ready = false;      // the whole solver workspace above and below exists
   HxCgState* st_host = nullptr;   // pinned
   cudaStream_t stream = nullptr;  // private non-blocking stream for solves
   cudaEvent_t ev = nullptr;
@@ -109,6 +113,7 @@ struct hx_op {
   float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
   double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual
   HxCgState* st32 = nullptr;
+  bool mixed_ready = false;     // the FP32 workspace above exists
   cudaGraphExec_t graph32 = nullptr;
   bool graph32_failed = false;
   bool mixed_stale = true;      // FP32 factors / diagonal need refreshing from the FP64 ones
@@ -141,6 +146,40 @@ struct hx_op {
 };
 
 namespace {
+
+// Frees every multigrid level, also the partial hierarchy of a failed set-up (the finest
+// level's Chebyshev vectors belong to the LOR workspace and stay).
+void mg_free(hx_op* op) {
+  for (int l = 0; l < op->mg.n_levels; ++l) {
+    HxMgLevel& L = op->mg.levels[l];
+    dfree(L.r);
+    dfree(L.coef);
+    dfree(L.val);
+    dfree(L.dinv);
+    dfree(L.bound);
+    if (l > 0) {
+      dfree(L.dir_own);
+      dfree(L.b);
+      dfree(L.x);
+      dfree(L.res);
+      dfree(L.d0);
+      dfree(L.d1);
+    }
+    dfree(L.val32);
+    dfree(L.dinv32);
+    dfree(L.b32);
+    dfree(L.x32);
+    dfree(L.r32);
+    dfree(L.res32);
+    dfree(L.d032);
+    dfree(L.d132);
+    L = HxMgLevel{};
+  }
+  op->mg.n_levels = 0;
+  op->mg_built = false;
+  op->mg32 = false;
+  dfree(op->mg_mc);
+}
 
 hx_apply_launcher apply_launcher(int p) {
   static const hx_apply_launcher t[] = {nullptr, hx_launch_apply_p1, hx_launch_apply_p2, hx_launch_apply_p3,
@@ -422,31 +461,7 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->cheb.d1);
   dfree(op->cheb.coef);
   dfree(op->zl);
-  for (int l = 0; l < op->mg.n_levels; ++l) {
-    HxMgLevel& L = op->mg.levels[l];
-    dfree(L.r);
-    dfree(L.coef);
-    dfree(L.val);
-    dfree(L.dinv);
-    dfree(L.bound);
-    if (l > 0) {
-      dfree(L.dir_own);
-      dfree(L.b);
-      dfree(L.x);
-      dfree(L.res);
-      dfree(L.d0);
-      dfree(L.d1);
-    }
-    dfree(L.val32);
-    dfree(L.dinv32);
-    dfree(L.b32);
-    dfree(L.x32);
-    dfree(L.r32);
-    dfree(L.res32);
-    dfree(L.d032);
-    dfree(L.d132);
-  }
-  dfree(op->mg_mc);
+  mg_free(op);
   dfree(op->zl32);
   delete op;
 }
@@ -567,14 +582,24 @@ hx_status lor_assemble(hx_op* op, cudaStream_t s, int* nl) {
   return lor_csr_values(op, s, nl);
 }
 
-// The multigrid levels of a structured mesh (allocated once; values by hx_mg_assemble).
+hx_status mg_alloc(hx_op* op, cudaStream_t s);
+
+// The multigrid levels of a structured mesh (allocated once; values by hx_mg_assemble).  A
+// failed allocation frees the partial hierarchy, so a later call starts from scratch.
 hx_status mg_setup(hx_op* op, int smooth_degree, cudaStream_t s) {
-  const hx_mesh* m = op->mesh;
   HxMg& M = op->mg;
   M.smooth_degree = smooth_degree;
   M.smooth_ratio = 10.0;
   M.coarse_degree = 16;
   if (op->mg_built) return HX_OK;
+  const hx_status st = mg_alloc(op, s);
+  if (st) mg_free(op);
+  return st;
+}
+
+hx_status mg_alloc(hx_op* op, cudaStream_t s) {
+  const hx_mesh* m = op->mesh;
+  HxMg& M = op->mg;
   hx_status st = HX_OK;
   HxMgLevel& F = M.levels[0];
   F.g = HxGrid{(int)m->grid[0], (int)m->grid[1], (int)m->grid[2], m->n_dof};
@@ -613,12 +638,13 @@ hx_status mg_setup(hx_op* op, int smooth_degree, cudaStream_t s) {
 hx_status lor_workspace(hx_op* op, int degree) {
   const long long n = op->mesh->n_dof;
   hx_status st = HX_OK;
-  if (!op->zl) {
-    if ((st = dalloc(&op->zl, (size_t)n, "preconditioned residual")) || (st = dalloc(&op->cheb.res, (size_t)n, "cheb res")) ||
-        (st = dalloc(&op->cheb.d0, (size_t)n, "cheb d0")) || (st = dalloc(&op->cheb.d1, (size_t)n, "cheb d1")) ||
-        (st = dalloc(&op->cheb.coef, 2 * HX_LOR_MAX_DEGREE, "cheb coefficients")))
-      return st;
-  }
+  // each buffer on its own: a call after a failed allocation fills in only what is missing
+  if ((!op->zl && (st = dalloc(&op->zl, (size_t)n, "preconditioned residual"))) ||
+      (!op->cheb.res && (st = dalloc(&op->cheb.res, (size_t)n, "cheb res"))) ||
+      (!op->cheb.d0 && (st = dalloc(&op->cheb.d0, (size_t)n, "cheb d0"))) ||
+      (!op->cheb.d1 && (st = dalloc(&op->cheb.d1, (size_t)n, "cheb d1"))) ||
+      (!op->cheb.coef && (st = dalloc(&op->cheb.coef, 2 * HX_LOR_MAX_DEGREE, "cheb coefficients"))))
+    return st;
   op->cheb.degree = degree;
   return HX_OK;
 }
@@ -687,16 +713,15 @@ hx_status lor_setup(hx_op* op, int degree, cudaStream_t s) {
     dfree(sums);
     dfree(bad);
     if (st) {
+      // nothing of a failed pattern survives: a later call starts from scratch (no leak)
+      dfree(op->lor.off);
+      dfree(op->lor.dinv);
+      dfree(op->lor_bound);
       dfree(op->lor.col);
       dfree(op->lor.val);
       dfree(op->lor.soff);
       dfree(op->lor.scol);
       dfree(op->lor.sval);
-      op->lor.col = nullptr;
-      op->lor.val = nullptr;
-      op->lor.soff = nullptr;
-      op->lor.scol = nullptr;
-      op->lor.sval = nullptr;
       return st;
     }
     op->lor.n = n;
@@ -914,7 +939,7 @@ HxCgBuffers cg_buffers(const hx_op* op) {
 }
 
 hx_status ensure_solver(hx_op* op) {
-  if (op->st) return HX_OK;
+  if (op->solver_ready) return HX_OK;
   const long long n = op->mesh->n_dof;
   hx_status s;
   if ((s = dalloc(&op->x, n, "cg x")) || (s = dalloc(&op->r, n, "cg r")) || (s = dalloc(&op->p, n, "cg p")) ||
@@ -922,12 +947,13 @@ hx_status ensure_solver(hx_op* op) {
       (s = dalloc(&op->partial, HX_RED_VALUES * HX_RED_BLOCKS, "cg partials")) || (s = dalloc(&op->scalars, 2, "scalars")) ||
       (s = dalloc(&op->counters, 2, "counters")) || (s = dalloc(&op->st, 1, "cg state")))
     return s;
-  HX_TRY(cudaMallocHost((void**)&op->st_host, sizeof(HxCgState)), "pinned state");
-  HX_TRY(cudaStreamCreateWithFlags(&op->stream, cudaStreamNonBlocking), "solver stream");
-  HX_TRY(cudaEventCreateWithFlags(&op->ev, cudaEventDisableTiming), "solver event");
+  if (!op->st_host) HX_TRY(cudaMallocHost((void**)&op->st_host, sizeof(HxCgState)), "pinned state");
+  if (!op->stream) HX_TRY(cudaStreamCreateWithFlags(&op->stream, cudaStreamNonBlocking), "solver stream");
+  if (!op->ev) HX_TRY(cudaEventCreateWithFlags(&op->ev, cudaEventDisableTiming), "solver event");
   HX_TRY(cudaMemsetAsync(op->st, 0, sizeof(HxCgState), op->stream), "state init");
   HX_TRY(cudaMemsetAsync(op->counters, 0, 2 * sizeof(unsigned int), op->stream), "counter init");
   op->dinv_stale = true;  // computed by the first call that needs it
+  op->solver_ready = true;
   return HX_OK;
 }
 
@@ -1116,9 +1142,7 @@ hx_status hx_solve_pcg_host(hx_op* op, const double* b_host, double* x_host, dou
   const long long n = op->mesh->n_dof;
   hx_status s = ensure_solver(op);
   if (s) return s;
-  if (!op->hb) {
-    if ((s = dalloc(&op->hb, n, "staging b")) || (s = dalloc(&op->hx, n, "staging x"))) return s;
-  }
+  if ((s = dalloc(&op->hb, n, "staging b")) || (s = dalloc(&op->hx, n, "staging x"))) return s;
   // the uploads run on the solver stream after the caller's prior work on `stream`
   HX_TRY(cudaEventRecord(op->ev, (cudaStream_t)stream), "event record");
   HX_TRY(cudaStreamWaitEvent(op->stream, op->ev, 0), "stream wait");
@@ -1193,7 +1217,7 @@ hx_status ensure_mixed(hx_op* op) {
   const hx_mesh* m = op->mesh;
   const long long n = m->n_dof;
   hx_status s;
-  if (!op->st32) {
+  if (!op->mixed_ready) {
     if ((s = dalloc(&op->yE32, (size_t)m->E * m->N3, "FP32 E-vector")) || (s = dalloc(&op->d32, n, "FP32 d")) ||
         (s = dalloc(&op->r32, n, "FP32 r")) || (s = dalloc(&op->p32, n, "FP32 p")) ||
         (s = dalloc(&op->Ap32, n, "FP32 Ap")) || (s = dalloc(&op->dinv32, n, "FP32 dinv")) ||
@@ -1203,6 +1227,7 @@ hx_status ensure_mixed(hx_op* op) {
         (s = dalloc(&op->factors32, (size_t)m->E * 7 * m->q * m->q * m->q + 4, "FP32 factors")))
       return s;
     HX_TRY(cudaMemsetAsync(op->st32, 0, sizeof(HxCgState), op->stream), "FP32 state init");
+    op->mixed_ready = true;
   }
   if (op->prec == HX_PREC_LOR_MG && !op->mg32) {
     // FP32 copies of the multigrid levels: stencils, inverse diagonals, work vectors
