@@ -49,7 +49,7 @@ METRIC = "Helmholtz apply GDoF/s & PCG time, p=2-8; mixed/batched vs FP64 at 1e-
 ALPHA, NU, RTOL = 1000.0, 1e-2, 1e-10
 SWEEP_N = {2: 160, 3: 96, 4: 96, 5: 64, 6: 64, 7: 48, 8: 48}
 def _measured_hbm_gbs(fallback=6400.0):
-    """The measured copy bandwidth of the B300s (MEASURED_PEAKS.json), else the fallback."""
+    """The measured copy bandwidth of the B300 (MEASURED_PEAKS.json), else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["hbm_gbs"])
