@@ -373,7 +373,11 @@ HX_API hx_status hx_op_gradient(hx_op* op, const double* u, const double* lam, d
  *             after instance i - lanes has finished, so at most `lanes` solves run
  *             side by side (0 or >= n: all instances concurrently).  Small
  *             instances gain from overlap; the many short kernels of multigrid
- *             V-cycles run better in few lanes.
+ *             V-cycles run better in few lanes.  lanes < 0: autotuned — the first
+ *             hx_batch_solve times one solve of the whole batch for each of 1, 2,
+ *             4, 8, ... and n lanes (CUDA events on the batch's stream), keeps the
+ *             fastest graph and then solves as usual; the lane count never changes
+ *             the results, only their overlap.  hx_batch_lanes reports the choice.
  * The graph captures the operators' coefficients and preconditioners: after
  * hx_op_set_coefficients on an HX_GEOM_ONTHEFLY operator, or hx_op_set_preconditioner,
  * create the batch again.  Synchronous create.
@@ -386,6 +390,10 @@ HX_API hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* 
  * results or NULL.  Returns HX_OK when all converged, else the first failing status.
  * Synchronous. */
 HX_API hx_status hx_batch_solve(hx_batch* batch, void* stream, hx_solve_info* infos);
+
+/* The lane count the next hx_batch_solve runs with (after autotuning, the chosen one; before
+ * the first solve of an autotuned batch, n).  0 for a NULL batch. */
+HX_API int hx_batch_lanes(const hx_batch* batch);
 
 /* Frees the batch (not its operators or vectors); NULL is ignored. */
 HX_API void hx_batch_destroy(hx_batch* batch);

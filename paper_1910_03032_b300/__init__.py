@@ -81,6 +81,7 @@ SIGNATURES = {
     "hx_op_precond_apply": (_I, [_P, _P, _P, _P]),
     "hx_batch_create": (_I, [_I, _P, _P, _P, _D, _I, _I, ctypes.POINTER(_P)]),
     "hx_batch_solve": (_I, [_P, _P, _P]),
+    "hx_batch_lanes": (_I, [_P]),
     "hx_batch_destroy": (None, [_P]),
     "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
 }
@@ -350,7 +351,8 @@ def hx_op_precond_apply(op, r, z, stream=None):
 
 def hx_batch_create(ops, b, x, rtol=1e-10, max_it=10000, lanes=0):
     """ops: operator handles; b, x: CUDA float64 tensors (n_dof_i each), bound to the batch;
-    lanes: concurrent chains of solves (0: all instances at once)."""
+    lanes: concurrent chains of solves (0: all instances at once; < 0: chosen by timing at the
+    first solve)."""
     n = len(ops)
     if not (len(b) == len(x) == n) or n < 1:
         raise ValueError("ops, b and x must have the same positive length")
@@ -372,6 +374,10 @@ def hx_batch_solve(batch, n, stream=None, raise_on_fail=True):
     return [i.as_dict() for i in infos]
 
 
+def hx_batch_lanes(batch):
+    return _lib.hx_batch_lanes(batch)
+
+
 def hx_batch_destroy(batch):
     _lib.hx_batch_destroy(batch)
 
@@ -385,6 +391,11 @@ class Batch:
 
     def solve(self, stream=None, raise_on_fail=True):
         return hx_batch_solve(self.handle, len(self.ops), stream, raise_on_fail)
+
+    @property
+    def lanes(self):
+        """Lanes of the next solve (after autotuning: the chosen count)."""
+        return hx_batch_lanes(self.handle)
 
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None

@@ -1479,6 +1479,10 @@ struct hx_batch {
   cudaGraphExec_t exec = nullptr;
   HxCgState* st_host = nullptr;  // pinned, n states
   double* rn2_host = nullptr;    // pinned, n true-residual norms
+  double rtol = 0.0;             // stopping rule the graph was built with
+  int max_it = 0;
+  int lanes = 0;                 // lanes of the current graph
+  bool tune = false;             // pick the lanes by timing at the first solve
 };
 
 namespace {
@@ -1578,6 +1582,51 @@ hx_status build_batch_graph(hx_batch* B, double rtol, int max_it, int lanes) {
   return s;
 }
 
+// Autotuned lanes: one timed solve of the whole batch (CUDA events on its stream, the graph
+// uploaded first) for each of 1, 2, 4, ... and n lanes; the fastest graph is kept.  The lanes
+// only decide which solves overlap, never their arithmetic, so every run gives the same x.
+hx_status tune_lanes(hx_batch* B) {
+  std::vector<int> cand;
+  for (int L = 1; L < B->n; L *= 2) cand.push_back(L);
+  cand.push_back(B->n);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  hx_status s = HX_OK;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  int best = B->lanes;
+  float best_ms = -1.0f;
+  for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
+    const int L = cand[k];
+    if (L != B->lanes) {
+      cudaGraphExecDestroy(B->exec);
+      B->exec = nullptr;
+      if ((s = build_batch_graph(B, B->rtol, B->max_it, L))) break;
+      B->lanes = L;
+    }
+    float ms = 0.0f;
+    e = cudaGraphUpload(B->exec, B->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, B->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, B->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && (best_ms < 0.0f || ms < best_ms)) {
+      best_ms = ms;
+      best = L;
+    }
+  }
+  if (e != cudaSuccess && s == HX_OK) s = cuda_fail(e, "batch lane timing");
+  if (s == HX_OK && best != B->lanes) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    if ((s = build_batch_graph(B, B->rtol, B->max_it, best)) == HX_OK) B->lanes = best;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (s == HX_OK) B->tune = false;
+  return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1587,7 +1636,6 @@ hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, doub
   if (!out) return fail(HX_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n < 1 || !ops || !b || !x) return fail(HX_ERR_ARG, "need n >= 1 and non-NULL arrays");
-  if (lanes < 0) return fail(HX_ERR_ARG, "lanes must be >= 0");
   if (!(rtol >= 0.0) || max_it < 0) return fail(HX_ERR_ARG, "rtol must be >= 0 and max_it >= 0");
   for (int i = 0; i < n; ++i)
     if (!ops[i] || !b[i] || !x[i]) return fail(HX_ERR_ARG, "instance %d: NULL operator or vector", i);
@@ -1597,6 +1645,10 @@ hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, doub
   B->ops.assign(ops, ops + n);
   B->b.assign(b, b + n);
   B->x.assign(x, x + n);
+  B->rtol = rtol;
+  B->max_it = max_it;
+  B->tune = lanes < 0;
+  B->lanes = (lanes <= 0 || lanes > n) ? n : lanes;
   hx_status s = HX_OK;
   for (int i = 0; i < n && s == HX_OK; ++i) {
     s = ensure_solver(ops[i]);
@@ -1608,7 +1660,7 @@ hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, doub
   if (e == cudaSuccess && s == HX_OK) e = cudaMallocHost((void**)&B->st_host, sizeof(HxCgState) * n);
   if (e == cudaSuccess && s == HX_OK) e = cudaMallocHost((void**)&B->rn2_host, sizeof(double) * n);
   if (e != cudaSuccess && s == HX_OK) s = cuda_fail(e, "batch resources");
-  if (s == HX_OK) s = build_batch_graph(B, rtol, max_it, (lanes == 0 || lanes > n) ? n : lanes);
+  if (s == HX_OK) s = build_batch_graph(B, rtol, max_it, B->lanes);
   if (s != HX_OK) {
     hx_batch_destroy(B);
     return s;
@@ -1625,6 +1677,11 @@ hx_status hx_batch_solve(hx_batch* B, void* stream, hx_solve_info* infos) {
     hx_status st = ensure_dinv(B->ops[i], B->stream);
     if (st) return st;
   }
+  if (B->tune) {
+    hx_status st = tune_lanes(B);
+    if (st) return st;
+  }
+  if (!B->exec) return fail(HX_ERR_CUDA, "the batch lost its graph in a failed rebuild");
   HX_TRY(cudaGraphLaunch(B->exec, B->stream), "batch graph launch");
   for (int i = 0; i < B->n; ++i) {
     HX_TRY(cudaMemcpyAsync(B->st_host + i, B->ops[i]->st, sizeof(HxCgState), cudaMemcpyDeviceToHost, B->stream),
@@ -1654,6 +1711,8 @@ hx_status hx_batch_solve(hx_batch* B, void* stream, hx_solve_info* infos) {
   if (worst != HX_OK) return fail(worst, "at least one batch instance did not converge");
   return HX_OK;
 }
+
+int hx_batch_lanes(const hx_batch* B) { return B ? B->lanes : 0; }
 
 void hx_batch_destroy(hx_batch* B) {
   if (!B) return;

@@ -27,8 +27,11 @@ def test_batch_matches_individual_solves():
         bs.append(b)
         xs.append(torch.full_like(b, float("nan")))
         refs.append((x_ref, info))
-    for lanes in (0, 1, 2, 4):  # all concurrent, one chain, and chains of several solves
+    # all concurrent, one chain, chains of several solves, and autotuned (-1: timed at the
+    # first solve over 1, 2, 4 and 6 lanes; the results cannot depend on the choice)
+    for lanes in (0, 1, 2, 4, -1):
         batch = hx.Batch(ops, bs, xs, rtol=1e-10, lanes=lanes)
+        assert batch.lanes == (len(ops) if lanes <= 0 else lanes)
         for rep in range(2):  # the bound graph is reusable
             for x in xs:
                 x.fill_(float("nan"))
@@ -37,6 +40,8 @@ def test_batch_matches_individual_solves():
                 assert bi["status"] == 0 and bi["iterations"] == info["iterations"]
                 assert bi["true_rel_residual"] <= 1.01e-10
                 assert rel_err(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-14
+            if lanes < 0:
+                assert batch.lanes in (1, 2, 4, len(ops))
         del batch
 
 
