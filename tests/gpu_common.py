@@ -35,3 +35,17 @@ def to_dev(a):
 def rel_err(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def lor_row_oracle(om, g, alpha, nu):
+    """Row g of the oracle's alpha Mc + nu K_LOR (constrained): only the elements holding DoF g
+    contribute to it (its sub-elements and its collocated mass), so the oracle assembles that
+    patch of elements alone. Returns (global columns, values) of the row's non-zeros."""
+    from oracle import fem, precond
+    els = sorted({e for e, _ in om.elements_of_dof(int(g))})
+    R = np.stack([om.element_dofs(e) for e in els])
+    ids, Rl = np.unique(R, return_inverse=True)
+    sub = fem.Mesh(om.p, om.q, om.vertices, om.elem_vert[els], Rl.reshape(R.shape), len(ids), om.dirichlet[ids])
+    row = precond.lor_matrix(sub, alpha, nu, "collocated")[np.searchsorted(ids, g)]
+    nz = row != 0
+    return ids[nz], row[nz]

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from tests.gpu_common import case, require_gpu, to_dev, torch
+from tests.gpu_common import case, lor_row_oracle, require_gpu, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -51,20 +51,6 @@ def test_fullsize_fp32_apply_sampled(p, N):
     np.testing.assert_allclose(y[g], ref, rtol=0, atol=2e-5 * np.abs(ref).max())
 
 
-def _lor_row_oracle(om, g, alpha, nu):
-    """Row g of the oracle's alpha Mc + nu K_LOR (constrained): only the elements holding DoF g
-    contribute to it (its sub-elements and its collocated mass), so the oracle assembles that
-    patch of elements alone. Returns (global columns, values) of the row's non-zeros."""
-    from oracle import fem, precond
-    els = sorted({e for e, _ in om.elements_of_dof(int(g))})
-    R = np.stack([om.element_dofs(e) for e in els])
-    ids, Rl = np.unique(R, return_inverse=True)
-    sub = fem.Mesh(om.p, om.q, om.vertices, om.elem_vert[els], Rl.reshape(R.shape), len(ids), om.dirichlet[ids])
-    row = precond.lor_matrix(sub, alpha, nu, "collocated")[np.searchsorted(ids, g)]
-    nz = row != 0
-    return ids[nz], row[nz]
-
-
 # the two solves of the preconditioner benchmark: the projection step's pure-Neumann pressure
 # Poisson (64^3, p = 5) and the Helmholtz problem of the headline (96^3, p = 4)
 PRECOND_CASES = [(5, 64, 0.0, 1.0, False), (4, 96, 1000.0, 1e-2, True)]
@@ -94,7 +80,7 @@ def test_fullsize_lor_sampled_rows_and_symmetry(p, N, alpha, nu, dirichlet):
     for g in g_all:
         a, b = int(ro_h[g]), int(ro_h[g + 1])
         cols, vals = col[a:b].cpu().numpy().astype(np.int64), val[a:b].cpu().numpy()
-        oc, ov = _lor_row_oracle(om, g, alpha, nu)
+        oc, ov = lor_row_oracle(om, g, alpha, nu)
         union = np.union1d(cols, oc)
         mine, ref = np.zeros(len(union)), np.zeros(len(union))
         mine[np.searchsorted(union, cols)] = vals

@@ -276,3 +276,18 @@ def test_lor_on_unstructured_star_prism(p):
     assert axis.sum() == 3 * p - 1
     assert np.all((K[axis] != 0).sum(axis=1) == 33)
     assert (K != 0).sum(axis=1).max() == 33
+
+
+@pytest.mark.parametrize("dirichlet,alpha,nu", [(False, 0.0, 1.0), (True, 1000.0, 1e-2)])
+def test_lor_rows_from_element_patches(dirichlet, alpha, nu):
+    """The reference the full-size LOR tests use: a row of alpha Mc + nu K_LOR assembled from
+    only the elements holding its DoF equals that row of the whole mesh's assembly, for every
+    row of a small mesh (interior, face, edge and corner DoFs; with and without Dirichlet)."""
+    from tests.gpu_common import case, lor_row_oracle
+    V, EV, om = case((3, 3, 2), 3, dirichlet=dirichlet)
+    A = precond.lor_matrix(om, alpha, nu, "collocated")
+    for g in range(om.n_dof):
+        cols, vals = lor_row_oracle(om, g, alpha, nu)
+        nz = np.nonzero(A[g])[0]
+        assert np.array_equal(cols, nz), g
+        assert np.abs(vals - A[g, nz]).max() <= 1e-15 * np.abs(A[g]).max(), g
