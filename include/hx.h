@@ -317,9 +317,15 @@ HX_API hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream);
  * HX_ERR_UNSUPPORTED (a LOR form on an operator with a nu field, a LOR row with more
  * than 64 distinct columns, HX_PREC_LOR_MG on a mesh without a logical grid;
  * mixed-precision solves reject HX_PREC_LOR and HX_PREC_LOR_MC).
- * The first selection of a LOR form allocates and builds the sparsity pattern (one
- * synchronization of `stream`) and, for HX_PREC_LOR_MG, the grid hierarchy; later calls
- * are stream-ordered.
+ * The first selection of a LOR form allocates and builds the sparsity pattern (two
+ * synchronizations of `stream`) and, for HX_PREC_LOR_MG, the grid hierarchy; later calls
+ * are stream-ordered.  Device memory: HX_PREC_LOR / HX_PREC_LOR_MC hold A_LOR twice, as
+ * CSR (12 B per entry, 27 entries per interior row of a structured mesh) and as the
+ * sliced-ELL copy the Chebyshev steps read (slices of 32 rows, column-major, padded to
+ * the slice's longest row), plus 4 work vectors; HX_PREC_LOR_MG holds 27 stencil values
+ * per grid node on every level (the fine level has n_dof nodes, each coarser ~1/8 of the
+ * one above) and 6 work vectors per level.  A failed allocation leaves the previous
+ * preconditioner selected and may be retried.
  */
 HX_API hx_status hx_op_set_preconditioner(hx_op* op, int kind, int degree, void* stream);
 
