@@ -407,14 +407,15 @@ HX_API void hx_batch_destroy(hx_batch* batch);
 /*
  * Operator apply that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc.  Examples are code running while a stream is captured into a
- * CUDA graph (allocation is not a stream operation), code inside a framework
- * whose pool allocator owns all device memory, and latency-bound loops that
- * cannot pay for the device synchronization cudaMalloc / cudaFree bring.
- * hx_op_create allocates an element-vector workspace; this call instead uses
- * a fixed array in the library's static device memory (HX_NOALLOC_MAX_EVEC
- * doubles, 32 MiB, held by every GPU that loads the library until the process
- * exits) and takes everything else from the caller.
+ * cudaMalloc.  Examples are code inside a framework whose pool allocator owns
+ * all device memory (an allocation behind its back can fail or fragment the
+ * pool), services that fix their device memory budget at start-up, and
+ * latency-bound loops that cannot pay for the device synchronization
+ * cudaMalloc / cudaFree bring.  hx_op_create allocates an element-vector
+ * workspace; this call instead uses a fixed array in the library's static
+ * device memory (HX_NOALLOC_MAX_EVEC doubles, 32 MiB, held by every GPU that
+ * loads the library until the process exits) and takes everything else from
+ * the caller.
  *
  * Computes y = A x for A = alpha M + K(nu) with constant alpha, nu, geometric
  * factors recomputed from the element vertices (as HX_GEOM_ONTHEFLY), and no
@@ -435,9 +436,11 @@ HX_API void hx_batch_destroy(hx_batch* batch);
  *               reproduce hx_op_apply bit for bit)
  *   x, y        device, n_dof doubles, not overlapping
  *   stream      stream the two kernels are enqueued on
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current and caches it; make that
- * first call before capturing any stream.  Every call on a device shares the
+ * The first call on a device (and again the first call in any other CUDA
+ * context made current on it, e.g. after a device reset) looks up the scratch
+ * array's device address (cudaGetSymbolAddress) with that device current and
+ * caches it for that context; make that first call before capturing any
+ * stream.  Every call on a device shares the
  * one scratch array and leaves its contents behind; the element kernel
  * overwrites every entry it later reads, so nothing needs clearing, but calls
  * whose work overlaps on the GPU (different streams, or several threads) race

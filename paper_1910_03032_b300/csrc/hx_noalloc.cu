@@ -2,14 +2,15 @@
 //
 // The regular path keeps the element-vector workspace of an apply inside an
 // hx_op, which hx_op_create obtains with cudaMalloc.  Some callers cannot
-// make that call: code that runs while a stream is being captured into a CUDA
-// graph (allocation is not a stream operation and is refused or breaks the
-// capture), code inside a framework that owns all device memory through its
-// own pool allocator, and latency-bound loops that cannot afford the device
-// synchronization cudaMalloc / cudaFree imply.  hx_apply_noalloc serves them:
-// every array is passed in by the caller, and the one scratch buffer the
-// operator needs (the element vector between the element kernel and the
-// assembly) is a fixed-size array in this file's static device memory.
+// make that call: code inside a framework that owns all device memory through
+// its own pool allocator (a cudaMalloc behind its back can fail or fragment
+// the pool), services that fix their device memory budget at start-up, and
+// latency-bound loops that cannot afford the device synchronization
+// cudaMalloc / cudaFree imply.  hx_apply_noalloc serves them: every array is
+// passed in by the caller, and the one scratch buffer the operator needs (the
+// element vector between the element kernel and the assembly) is a
+// fixed-size array in this file's static device memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -28,23 +29,70 @@ static __device__ __align__(256) double g_noalloc_scratch[HX_NOALLOC_MAX_EVEC];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// The scratch array's device address, cached per device together with the
+// unique id of the CUDA context it was looked up in: a symbol's address
+// belongs to a context, so a reset device (a new primary context) or another
+// context made current by the caller triggers a new lookup.
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  double* addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
+
+// cuCtxGetCurrent / cuCtxGetId from the driver, reached through the runtime
+// (the library does not link libcuda)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess) return e;
+    if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+      return cudaErrorNotSupported;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+    get_id = reinterpret_cast<CtxGetIdFn>(f1);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (!ctx) {
+    *id = 0;  // no context current yet: the runtime binds the primary context at the lookup
+    return cudaSuccess;
+  }
+  return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of the scratch array in the current device's current context.
+// The lookup (cudaGetSymbolAddress, with that device current) runs once per
+// device and context; later calls reuse the cached address.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  if (id == 0 || g_slot[dev].ctx_id != id || !g_slot[dev].addr) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(ptr);
+    if (id == 0) {
+      e = current_context_id(&id);  // the context the lookup just bound
+      if (e != cudaSuccess) return e;
+    }
+    g_slot[dev].ctx_id = id;
+    g_slot[dev].addr = static_cast<double*>(ptr);
   }
-  *out = g_scratch_addr[dev];
+  *out = g_slot[dev].addr;
   return cudaSuccess;
 }
 

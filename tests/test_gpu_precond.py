@@ -249,8 +249,11 @@ def test_lor_neumann_poisson(hx):
 
 
 def test_lor_in_a_batch(hx):
+    from oracle import fem
+    from oracle.solve import jacobi_pcg
     ops, bs, xs, refs = [], [], [], []
-    for k, (N, p, prec) in enumerate([(4, 3, hx.HX_PREC_LOR), (3, 5, hx.HX_PREC_JACOBI), (5, 2, hx.HX_PREC_LOR)]):
+    cases = [(4, 3, hx.HX_PREC_LOR), (3, 5, hx.HX_PREC_JACOBI), (5, 2, hx.HX_PREC_LOR)]
+    for k, (N, p, prec) in enumerate(cases):
         V = S.structured_vertices(N, N, N, 0.1, 500 + k)
         mesh = hx.Mesh.structured(N, N, N, p, p + 2, V)
         op = hx.Operator(mesh, 0.0, 1.0)
@@ -262,9 +265,15 @@ def test_lor_in_a_batch(hx):
         xs.append(torch.zeros_like(b))
     batch = hx.Batch(ops, bs, xs, rtol=1e-10)
     infos = batch.solve()
-    for (xr, ir), x, i in zip(refs, xs, infos):
+    for k, ((xr, ir), x, i, b) in enumerate(zip(refs, xs, infos, bs)):
         assert i["status"] == 0 and i["iterations"] == ir["iterations"]
         assert torch.equal(x, xr)
+        # the preconditioner changes the iterates, not the solution: the oracle's Jacobi-PCG
+        # solution of the same Poisson problem (to 1e-12) within the solution tolerance
+        N, p, _ = cases[k]
+        _, _, om = case((N, N, N), p, seed=500 + k)
+        xo, _, _, conv = jacobi_pcg(fem.Operator(om, 0.0, 1.0), b.cpu().numpy(), 1e-12, 20000)
+        assert conv and rel_err(x.cpu().numpy(), xo) <= 1e-8
 
 
 def test_lor_errors(hx):
