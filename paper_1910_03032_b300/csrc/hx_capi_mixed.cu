@@ -1,0 +1,311 @@
+// C ABI of libhx.so (include/hx.h): mixed precision -- FP64 iterative refinement around an
+// FP32 PCG with the FP32 operator (not part of the paper's method).
+#include "hx_capi_internal.h"
+
+using namespace hxc;
+
+// ---------------------------------------------------------------------------
+// mixed precision: FP64 iterative refinement around an FP32 Jacobi-PCG
+// ---------------------------------------------------------------------------
+namespace hxc {
+
+HxApplyArgsF apply_args32(const hx_op* op, const float* x, const int* done) {
+  const hx_mesh* m = op->mesh;
+  HxApplyArgsF a;
+  a.E = m->E;
+  a.R = m->R;
+  a.x = x;
+  a.yE = op->yE32;
+  a.factors = op->factors32;
+  a.X8 = m->X8;
+  a.nu_q = op->use_field ? op->nu_q : nullptr;
+  a.alpha = op->alpha;
+  a.nu = op->nu;
+  a.constrained = 1;
+  a.done = done;
+  a.err = op->kerr;
+  return a;
+}
+
+cudaError_t element_apply32(const hx_op* op, const float* x, const int* done, cudaStream_t s) {
+  static const hx_apply32_launcher t[] = {nullptr, hx_launch_apply32_p1, hx_launch_apply32_p2, hx_launch_apply32_p3,
+                                          hx_launch_apply32_p4, hx_launch_apply32_p5, hx_launch_apply32_p6,
+                                          hx_launch_apply32_p7, hx_launch_apply32_p8};
+  const HxApplyArgsF a = apply_args32(op, x, done);
+  return t[op->mesh->p](op->mesh->T32, a, op->geom, s);
+}
+
+HxCgBuffersF cg_buffers32(const hx_op* op) {
+  const hx_mesh* m = op->mesh;
+  HxCgBuffersF b;
+  b.n = m->n_dof;
+  b.off = m->off;
+  b.idx = m->idx;
+  b.dir = m->dir;
+  b.x = op->d32;
+  b.r = op->r32;
+  b.p = op->p32;
+  b.Ap = op->Ap32;
+  b.dinv = op->dinv32;
+  b.yE = op->yE32;
+  b.partial = op->partial;
+  b.st = op->st32;
+  b.z = (op->prec == HX_PREC_LOR_MG) ? op->zl32 : nullptr;
+  b.cond = 0ull;
+  b.nullspace = op->singular ? 1 : 0;
+  return b;
+}
+
+// FP32 workspace and the FP32 rounding of the stored factors and inverse diagonal.
+hx_status ensure_mixed(hx_op* op) {
+  const hx_mesh* m = op->mesh;
+  const long long n = m->n_dof;
+  hx_status s;
+  if (!op->mixed_ready) {
+    if ((s = dalloc(&op->yE32, (size_t)m->E * m->N3, "FP32 E-vector")) || (s = dalloc(&op->d32, n, "FP32 d")) ||
+        (s = dalloc(&op->r32, n, "FP32 r")) || (s = dalloc(&op->p32, n, "FP32 p")) ||
+        (s = dalloc(&op->Ap32, n, "FP32 Ap")) || (s = dalloc(&op->dinv32, n, "FP32 dinv")) ||
+        (s = dalloc(&op->rn2, 1, "residual norm")) || (s = dalloc(&op->st32, 1, "FP32 state")))
+      return s;
+    if (op->geom == HX_GEOM_STORED &&
+        (s = dalloc(&op->factors32, (size_t)m->E * 7 * m->q * m->q * m->q + 4, "FP32 factors")))
+      return s;
+    HX_TRY(cudaMemsetAsync(op->st32, 0, sizeof(HxCgState), op->stream), "FP32 state init");
+    op->mixed_ready = true;
+  }
+  if (op->prec == HX_PREC_LOR_MG && !op->mg32) {
+    // FP32 copies of the multigrid levels: stencils, inverse diagonals, work vectors
+    for (int l = 0; l < op->mg.n_levels; ++l) {
+      HxMgLevel& L = op->mg.levels[l];
+      const size_t nl = (size_t)L.g.n;
+      if ((s = dalloc(&L.val32, 27 * nl, "FP32 MG stencil")) || (s = dalloc(&L.dinv32, nl, "FP32 MG dinv")) ||
+          (s = dalloc(&L.r32, nl, "FP32 MG r")) || (s = dalloc(&L.res32, nl, "FP32 MG res")) ||
+          (s = dalloc(&L.d032, nl, "FP32 MG d0")) || (s = dalloc(&L.d132, nl, "FP32 MG d1")))
+        return s;
+      if (l > 0 && ((s = dalloc(&L.b32, nl, "FP32 MG b")) || (s = dalloc(&L.x32, nl, "FP32 MG x")))) return s;
+    }
+    if ((s = dalloc(&op->zl32, (size_t)n, "FP32 preconditioned residual"))) return s;
+    op->mg32 = true;
+    op->mixed_stale = true;
+  }
+  if (op->mixed_stale) {
+    if (op->geom == HX_GEOM_STORED)
+      HX_TRY(hx_launch_to_float((long long)m->E * 7 * m->q * m->q * m->q, op->factors, op->factors32, op->stream),
+             "FP32 factors");
+    if (op->prec == HX_PREC_LOR_MG) {
+      HX_TRY(hx_mg_to_float(op->mg, op->stream), "FP32 multigrid levels");
+      op->launches += 2 * op->mg.n_levels;
+    } else if (op->prec == HX_PREC_JACOBI) {
+      // the inner solver's Jacobi diagonal: the diagonal of the FP32 operator, computed in FP32
+      static const hx_diag32_launcher t[] = {nullptr, hx_launch_diag32_p1, hx_launch_diag32_p2, hx_launch_diag32_p3,
+                                             hx_launch_diag32_p4, hx_launch_diag32_p5, hx_launch_diag32_p6,
+                                             hx_launch_diag32_p7, hx_launch_diag32_p8};
+      HxDiagArgsF d;
+      d.E = m->E;
+      d.factors = op->factors32;
+      d.X8 = m->X8;
+      d.nu_q = op->use_field ? op->nu_q : nullptr;
+      d.alpha = op->alpha;
+      d.nu = op->nu;
+      d.dE = op->yE32;
+      HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
+      HX_TRY(hx_launch_assemble32(n, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
+             "FP32 diagonal assembly");
+      HX_TRY(hx_launch_dinv32(n, op->Ap32, m->dir, op->dinv32, op->stream), "FP32 dinv");
+      op->launches += 3;
+    } else {
+      if ((s = ensure_dinv(op, op->stream))) return s;
+      HX_TRY(hx_launch_to_float(n, op->dinv, op->dinv32, op->stream), "FP32 dinv");
+      op->launches += 1;
+    }
+    op->launches += (op->geom == HX_GEOM_STORED) ? 1 : 0;
+    op->mixed_stale = false;
+  }
+  return HX_OK;
+}
+
+cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s, unsigned long long cond = 0ull) {
+  HxCgBuffersF b = cg_buffers32(op);
+  b.cond = cond;
+  cudaError_t e = element_apply32(op, op->p32, &op->st32->done, s);
+  if (e == cudaSuccess) e = hx_launch_cg_assemble_pap(b, s);
+  if (e == cudaSuccess) e = hx_launch_cg_update(b, s);
+  if (e == cudaSuccess && b.z) {
+    e = hx_mg_vcycle32(op->mg, op->r32, op->zl32, &op->st32->done, s);
+    if (e == cudaSuccess) e = hx_launch_cg_rz(b, s);
+  }
+  if (e == cudaSuccess) e = hx_launch_cg_direction(b, s);
+  return e;
+}
+
+void ensure_graph32(hx_op* op) {
+  if (op->graph32 || op->graph32_failed) return;
+  if (!build_while_graph(op->stream, [op](unsigned long long h) { return cg_iteration32(op, op->stream, h); },
+                         &op->graph32))
+    op->graph32_failed = true;
+}
+
+// FP64 residual r = P b - A_c x into op->r, ||r||^2 into op->rn2 (x in op->x).
+hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_t st) {
+  const double* shift = op->singular ? &op->st->shift : nullptr;  // pure Neumann: b minus its mean
+  const hx_mesh* m = op->mesh;
+  if (x_is_zero) {
+    HX_TRY(cudaMemsetAsync(op->Ap, 0, sizeof(double) * m->n_dof, st), "zero");
+  } else {
+    HX_TRY(element_apply(op, op->x, 1, nullptr, st), "refinement apply");
+    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st),
+           "refinement assembly");
+    op->launches += 2;
+  }
+  HX_TRY(hx_launch_ir_residual(m->n_dof, b, op->Ap, m->dir, op->r, op->partial, op->counters, op->rn2, st, shift),
+         "refinement residual");
+  op->launches += 1;
+  return HX_OK;
+}
+
+hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
+                      cudaStream_t user, hx_solve_info* info) {
+  const hx_mesh* m = op->mesh;
+  if (op->prec == HX_PREC_LOR)
+    return fail(HX_ERR_UNSUPPORTED, "mixed-precision solves take the Jacobi, collocated mass or multigrid preconditioner");
+  hx_status s = ensure_solver(op);
+  if (s) return s;
+  cudaStream_t st = op->stream;
+  HX_TRY(cudaEventRecord(op->ev, user), "event record");
+  HX_TRY(cudaStreamWaitEvent(st, op->ev, 0), "stream wait");
+  if ((s = ensure_mixed(op))) return s;
+  ensure_graph32(op);
+  const long long launches0 = op->launches;
+  HX_TRY(cudaMemsetAsync(op->x, 0, sizeof(double) * m->n_dof, st), "x init");
+  if (op->singular) {
+    HX_TRY(hx_launch_cg_mean(cg_buffers(op), b, st), "mean of b");
+    op->launches += 1;
+  }
+  if ((s = outer_residual(op, b, true, st))) return s;
+  double rn2 = 0.0;
+  HX_TRY(cudaMemcpyAsync(&rn2, op->rn2, sizeof(double), cudaMemcpyDeviceToHost, st), "norm read");
+  HX_TRY(cudaStreamSynchronize(st), "solver sync");
+  const double bn = std::sqrt(rn2);
+  double rel = bn > 0 ? 1.0 : 0.0, prev = rel;
+  int inner_total = 0, outer = 0, status = HX_OK, stalls = 0;
+  const HxCgBuffersF buf = cg_buffers32(op);
+  while (rel > rtol) {
+    if (inner_total >= max_it) {
+      status = HX_ERR_NOT_CONVERGED;
+      break;
+    }
+    // inner FP32 Jacobi-PCG on A_c d = r / ||r|| from d = 0
+    HX_TRY(hx_launch_ir_scale_down(m->n_dof, op->r, op->rn2, op->r32, st), "scale down");
+    if (op->singular) {
+      HX_TRY(hx_launch_cg_mean(buf, (const float*)op->r32, st), "inner mean");
+      op->launches += 1;
+    }
+    HX_TRY(hx_launch_cg_init(buf, (const float*)op->r32, (const float*)nullptr, inner_rtol, max_it - inner_total, st),
+           "inner init");
+    if (op->prec == HX_PREC_LOR_MG) {
+      HX_TRY(hx_mg_vcycle32(op->mg, op->r32, op->zl32, &op->st32->done, st), "inner first V-cycle");
+      op->launches += hx_mg_vcycle_launches(op->mg);
+    }
+    HX_TRY(hx_launch_cg_start(buf, st), "inner start");
+    op->launches += 3;
+    if (op->singular) {
+      HX_TRY(hx_launch_cg_direction(buf, st), "inner first direction");
+      op->launches += 1;
+    }
+    if (op->graph32) {
+      HX_TRY(cudaGraphLaunch(op->graph32, st), "graph launch");
+      HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
+      HX_TRY(cudaStreamSynchronize(st), "solver sync");
+      op->launches += iteration_launches(op) * (long long)op->st_host->loops;
+      if (!op->st_host->done) return fail(HX_ERR_CUDA, "inner CG graph loop ended before the solver finished");
+    } else {
+      for (;;) {
+        HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
+        HX_TRY(cudaStreamSynchronize(st), "solver sync");
+        if (op->st_host->done) break;
+        for (int i = 0; i < kChunk; ++i) HX_TRY(cg_iteration32(op, st), "inner iteration");
+        op->launches += iteration_launches(op) * kChunk;
+      }
+    }
+    const HxCgState cs = *op->st_host;
+    inner_total += cs.iter;
+    ++outer;
+    if (cs.status == HX_ERR_BREAKDOWN) {
+      status = HX_ERR_BREAKDOWN;
+      break;
+    }
+    // x += ||r|| d in FP64, then the FP64 residual of the new x
+    HX_TRY(hx_launch_ir_update(m->n_dof, op->x, op->d32, op->rn2, st), "refinement update");
+    op->launches += 1;
+    if ((s = outer_residual(op, b, false, st))) return s;
+    HX_TRY(cudaMemcpyAsync(&rn2, op->rn2, sizeof(double), cudaMemcpyDeviceToHost, st), "norm read");
+    HX_TRY(cudaStreamSynchronize(st), "solver sync");
+    rel = bn > 0 ? std::sqrt(rn2) / bn : 0.0;
+    if (!std::isfinite(rel)) {
+      status = HX_ERR_BREAKDOWN;
+      break;
+    }
+    // refinement that stops contracting (FP32 operator error above the target) ends the solve
+    stalls = (rel > 0.5 * prev) ? stalls + 1 : 0;
+    if (stalls >= 2 && rel > rtol) {
+      status = HX_ERR_NOT_CONVERGED;
+      break;
+    }
+    prev = rel;
+  }
+  if (op->singular) {
+    HX_TRY(hx_launch_sum(m->n_dof, op->m1, op->partial, op->counters, op->vol, st), "volume");
+    HX_TRY(hx_launch_dot(m->n_dof, op->m1, op->x, op->partial, op->counters, op->vol + 1, st), "mean");
+    HX_TRY(hx_launch_shift(m->n_dof, op->x, op->vol + 1, op->vol, st), "mean shift");
+    op->launches += 3;
+  }
+  HX_TRY(cudaMemcpyAsync(x, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, st), "solution copy");
+  HX_TRY(cudaStreamSynchronize(st), "solver sync");
+  if ((s = check_kernel_flag(op, st))) return s;
+  hx_solve_info inf;
+  inf.iterations = inner_total;
+  inf.status = status;
+  inf.b_norm = bn;
+  inf.rel_residual = rel;
+  inf.true_rel_residual = rel;
+  inf.kernel_launches = (int)(op->launches - launches0);
+  inf.refinements = outer;
+  if (info) *info = inf;
+  if (status == HX_ERR_NOT_CONVERGED)
+    return fail(HX_ERR_NOT_CONVERGED, "mixed solve stopped at rel. residual %.3e after %d refinements", rel, outer);
+  if (status == HX_ERR_BREAKDOWN) return fail(HX_ERR_BREAKDOWN, "mixed solve breakdown");
+  return HX_OK;
+}
+
+}  // namespace hxc
+
+extern "C" {
+
+hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, double rtol, int max_it, double inner_rtol,
+                             void* stream, hx_solve_info* info) {
+  if (!op || !b || !x) return fail(HX_ERR_ARG, "NULL argument");
+  if (!(rtol >= 0.0) || max_it < 0 || !(inner_rtol > 0.0 && inner_rtol < 1.0))
+    return fail(HX_ERR_ARG, "need rtol >= 0, max_it >= 0 and 0 < inner_rtol < 1");
+  return solve_mixed(op, b, x, rtol, max_it, inner_rtol, (cudaStream_t)stream, info);
+}
+
+hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream) {
+  if (!op || !x || !y) return fail(HX_ERR_ARG, "NULL argument");
+  if ((const void*)x == (void*)y) return fail(HX_ERR_ARG, "x and y must not alias");
+  hx_status s = ensure_solver(op);
+  if (s) return s;
+  cudaStream_t us = (cudaStream_t)stream;
+  // the FP32 set-up runs on the solver stream; order it with the caller's stream both ways
+  HX_TRY(cudaEventRecord(op->ev, us), "event record");
+  HX_TRY(cudaStreamWaitEvent(op->stream, op->ev, 0), "stream wait");
+  if ((s = ensure_mixed(op))) return s;
+  HX_TRY(cudaEventRecord(op->ev, op->stream), "event record");
+  HX_TRY(cudaStreamWaitEvent(us, op->ev, 0), "stream wait");
+  const hx_mesh* m = op->mesh;
+  HX_TRY(element_apply32(op, x, nullptr, us), "FP32 element kernel");
+  HX_TRY(hx_launch_assemble32(m->n_dof, m->off, m->idx, op->yE32, m->dir, 1, x, y, us), "FP32 assembly");
+  op->launches += 2;
+  return HX_OK;
+}
+
+}  // extern "C"
