@@ -258,6 +258,22 @@ HX_API hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, doubl
 HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream);
 
 /*
+ * Failure-detection hook (the paper has no counterpart).  For p <= 4 with stored
+ * factors the FP32 operator kernel stages each block's factors into shared memory
+ * with one bulk (TMA) copy completed on an mbarrier, and waits for it with a bounded
+ * number of mbarrier try_wait attempts (default 65536).  A block whose wait gives up
+ * raises the operator's device error flag, skips its remaining stages and stores,
+ * and before it exits waits again with a far larger bound, so that no copy is still
+ * writing its shared memory.  hx_solve_pcg_mixed reports a raised flag as HX_ERR_CUDA
+ * ("... timed out").  attempts (>= 0, else HX_ERR_ARG) sets the first wait's bound
+ * for this operator's later mixed solves and FP32 applies; 0 makes every such wait
+ * give up at once (the copies themselves complete normally), which tests use to
+ * check that the failure surfaces as a status and that the next solve with the
+ * default bound runs normally.  Host-side only; drops the captured inner-CG graph.
+ */
+HX_API hx_status hx_op_set_wait_limit(hx_op* op, int attempts);
+
+/*
  * Preconditioners of the PCG solves (Sec. 5).
  *   HX_PREC_JACOBI           z = diag(A)^-1 r, the exact diagonal of alpha M + nu K (default)
  *   HX_PREC_COLLOCATED_MASS  z = (alpha Mc)^-1 r, Mc the mass matrix integrated with the

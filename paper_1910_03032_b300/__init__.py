@@ -74,6 +74,7 @@ SIGNATURES = {
     "hx_solve_pcg_host": (_I, [_P, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "hx_solve_pcg_mixed": (_I, [_P, _P, _P, _D, _I, _D, _P, ctypes.POINTER(SolveInfo)]),
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
+    "hx_op_set_wait_limit": (_I, [_P, _I]),
     "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
     "hx_op_collocated_mass": (_I, [_P, _P, _P]),
     "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, ctypes.c_int, _P]),
@@ -316,6 +317,10 @@ def hx_op_apply_f32(op, x, y, stream=None):
     _check(_lib.hx_op_apply_f32(op, _fptr(x, n, "x"), _fptr(y, n, "y"), _stream(stream)))
 
 
+def hx_op_set_wait_limit(op, attempts):
+    _check(_lib.hx_op_set_wait_limit(op, int(attempts)))
+
+
 def hx_op_gradient(op, u, lam, dnu_q, df_q, stream=None):
     E, n, _, q = hx_op_info(op)
     _check(_lib.hx_op_gradient(op, _dptr(u, n, "u"), _dptr(lam, n, "lam"), _dptr(dnu_q, E * q ** 3, "dnu_q"),
@@ -555,6 +560,9 @@ class Operator:
         y = torch.empty_like(x)
         hx_op_apply_f32(self.handle, x, y, stream)
         return y
+
+    def set_wait_limit(self, attempts):
+        hx_op_set_wait_limit(self.handle, attempts)
 
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None

@@ -96,6 +96,7 @@ struct hx_op {
   float* factors32 = nullptr;  // [E][7][Q3] FP32 rounding of the stored factors (+16 bytes: the bulk
                                // copies of the element kernel round their end up to 16 bytes)
   int* kerr = nullptr;         // device flag: a kernel's bounded wait gave up
+  int wait_limit = HX_WAIT_LIMIT_DEFAULT;  // attempts of the FP32 kernel's first wait for its factors
   float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
   double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual
   HxCgState* st32 = nullptr;

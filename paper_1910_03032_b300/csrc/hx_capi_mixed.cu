@@ -24,6 +24,7 @@ HxApplyArgsF apply_args32(const hx_op* op, const float* x, const int* done) {
   a.constrained = 1;
   a.done = done;
   a.err = op->kerr;
+  a.wait_limit = op->wait_limit;
   return a;
 }
 
@@ -176,6 +177,8 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
   if ((s = ensure_mixed(op))) return s;
   ensure_graph32(op);
   const long long launches0 = op->launches;
+  // the kernel error flag reports this solve only
+  HX_TRY(cudaMemsetAsync(op->kerr, 0, sizeof(int), st), "flag reset");
   HX_TRY(cudaMemsetAsync(op->x, 0, sizeof(double) * m->n_dof, st), "x init");
   if (op->singular) {
     HX_TRY(hx_launch_cg_mean(cg_buffers(op), b, st), "mean of b");
@@ -217,7 +220,10 @@ hx_status solve_mixed(hx_op* op, const double* b, double* x, double rtol, int ma
       HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
       HX_TRY(cudaStreamSynchronize(st), "solver sync");
       op->launches += iteration_launches(op) * (long long)op->st_host->loops;
-      if (!op->st_host->done) return fail(HX_ERR_CUDA, "inner CG graph loop ended before the solver finished");
+      if (!op->st_host->done) {
+        if ((s = check_kernel_flag(op, st))) return s;
+        return fail(HX_ERR_CUDA, "inner CG graph loop ended before the solver finished");
+      }
     } else {
       for (;;) {
         HX_TRY(cudaMemcpyAsync(op->st_host, op->st32, sizeof(HxCgState), cudaMemcpyDeviceToHost, st), "state read");
@@ -287,6 +293,19 @@ hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, double rtol,
   if (!(rtol >= 0.0) || max_it < 0 || !(inner_rtol > 0.0 && inner_rtol < 1.0))
     return fail(HX_ERR_ARG, "need rtol >= 0, max_it >= 0 and 0 < inner_rtol < 1");
   return solve_mixed(op, b, x, rtol, max_it, inner_rtol, (cudaStream_t)stream, info);
+}
+
+hx_status hx_op_set_wait_limit(hx_op* op, int attempts) {
+  if (!op) return fail(HX_ERR_ARG, "op is NULL");
+  if (attempts < 0) return fail(HX_ERR_ARG, "attempts must be >= 0");
+  op->wait_limit = attempts;
+  // the captured inner CG carries the limit as a kernel parameter: capture again at the next solve
+  if (op->graph32) {
+    cudaGraphExecDestroy(op->graph32);
+    op->graph32 = nullptr;
+  }
+  op->graph32_failed = false;
+  return HX_OK;
 }
 
 hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream) {

@@ -21,6 +21,7 @@ HxApplyArgs apply_args(const hx_op* op, const double* x, int constrained, const 
   a.constrained = constrained;
   a.done = done;
   a.err = op->kerr;
+  a.wait_limit = op->wait_limit;
   return a;
 }
 

@@ -230,8 +230,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 
 // Wait for phase 0 of `bar` with a bound on the attempts (each try_wait itself suspends
 // for a while); false when the bound was reached.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar) {
-  for (int it = 0; it < (1 << 16); ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, int limit) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, 0u)) return true;
   return false;
 }
@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(NT, MINB)
   Real* smem = reinterpret_cast<Real*>(smem_raw);
   Real* geo = smem + NE * R3;  // on-the-fly: NE x 24 map coefficients
   Real* sf = smem + ((NE * R3 + 3) & ~3);  // staged factors (16-byte aligned)
+  __shared__ int wait_failed;          // some thread's first wait for the factor copy gave up
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
   // the copy starts at the 16-byte boundary at or below element e0's first factor
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(NT, MINB)
       const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
       const long long b0 = e0 * FE * (long long)sizeof(Real), b1 = (e0 + nel) * FE * (long long)sizeof(Real);
       const long long a0 = b0 & ~15LL, a1 = (b1 + 15) & ~15LL;  // the factor array has 16 bytes of slack
+      wait_failed = 0;
       mbar_init(&fbar, 1);
       mbar_expect_tx(&fbar, (unsigned)(a1 - a0));
       bulk_load(sf, reinterpret_cast<const char*>(A.factors) + a0, (unsigned)(a1 - a0), &fbar);
@@ -436,8 +438,15 @@ __global__ void __launch_bounds__(NT, MINB)
   // 5. columns: pointwise v = m u (into D, over u), w = G grad u; then Dh^T along z of
   //    w_3 (folded parts kept in registers)
   Real Et[CQ], Ot[CQ];
-  if (STAGE && owner && !mbar_wait_bounded(&fbar) && A.err) atomicExch(A.err, 1);
-  if (owner) {
+  // a thread whose wait gave up raises the error flag and skips its pointwise work; after the
+  // next barrier the whole block skips the remaining stages and stores nothing
+  bool staged = true;
+  if (STAGE && owner && !mbar_wait_bounded(&fbar, A.wait_limit)) {
+    staged = false;
+    wait_failed = 1;
+    if (A.err) atomicExch(A.err, 1);
+  }
+  if (owner && staged) {
     const long long e = e0 + cel;
     Real* Dc = smem + cel * R3 + cs;
     Real* Xc = Dc + RG;
@@ -499,6 +508,12 @@ __global__ void __launch_bounds__(NT, MINB)
     products<Q, Q, -1>(T.Dte2, T.Dto2, ev, od, Et, Ot);  // rows doubled: (2E, 2O)
   }
   __syncthreads();
+  if (STAGE && wait_failed) {
+    // no copy may still be writing this block's shared memory when it exits: wait once more,
+    // with a far larger bound than the first wait
+    if (tid == 0) mbar_wait_bounded(&fbar, HX_WAIT_LIMIT_EXIT);
+    return;
+  }
   // 6. Dh^T along x (X, in place) and along y (Y, in place)
   for (int t = tid; t < NE * 2 * Q2; t += NT) {
     const int el = t / (2 * Q2), r = t - el * (2 * Q2);
@@ -531,8 +546,9 @@ __global__ void __launch_bounds__(NT, MINB)
   }
   __syncthreads();
   transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
-  // no copy may still be writing this block's shared memory when it exits
-  if (STAGE && tid == 0) mbar_wait_bounded(&fbar);
+  // no copy may still be writing this block's shared memory when it exits (every owner's
+  // first wait saw the copy complete, so this returns at once)
+  if (STAGE && tid == 0) mbar_wait_bounded(&fbar, HX_WAIT_LIMIT_EXIT);
 }
 
 // Load vector: bE = (B x B x B)^T (w detJ f) per element.

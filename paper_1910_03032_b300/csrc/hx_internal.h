@@ -1,4 +1,4 @@
-// Internal declarations shared by the C ABI (hx_capi.cu) and the kernel
+// Internal declarations shared by the C ABI (hx_capi_*.cu) and the kernel
 // translation units.  Not part of the public interface (see include/hx.h).
 #pragma once
 
@@ -23,8 +23,11 @@ struct HxApplyArgsT {
   int constrained;        // 1: Dirichlet DoFs of x read as zero
   const int* done;        // optional device flag: kernel returns at once when *done != 0
   int* err;               // optional device flag, set to 1 when a bounded wait gives up
+  int wait_limit;         // try_wait attempts of the first wait for the staged factors (FP32 kernel)
 };
 typedef HxApplyArgsT<double> HxApplyArgs;
+#define HX_WAIT_LIMIT_DEFAULT (1 << 16)  // attempts of the first bounded wait
+#define HX_WAIT_LIMIT_EXIT (1 << 20)     // attempts of the wait before a block exits
 typedef HxApplyArgsT<float> HxApplyArgsF;
 
 // Arguments of the diagonal kernel (sum-factorized diag of the element matrices).

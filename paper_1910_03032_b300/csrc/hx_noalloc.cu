@@ -157,6 +157,7 @@ extern "C" hx_status hx_apply_noalloc(int p, int q, int64_t n_elem, int64_t n_do
   a.constrained = 0;
   a.done = nullptr;
   a.err = nullptr;
+  a.wait_limit = HX_WAIT_LIMIT_DEFAULT;
   e = launch_order(p, T, a, s);
   if (e == cudaSuccess) e = hx_launch_assemble(n_dof, t_offsets, t_indices, scratch, nullptr, 0, nullptr, 0.0, y, s);
   if (e != cudaSuccess) {
