@@ -20,11 +20,16 @@ isolated apply throughput, the roofline of the element kernel, the
 end-to-end number through host buffers, the CPU oracle baseline, and the
 SM clocks sampled during the timed region.
 
+The default run also carries a bounded per-order sweep (p = 2..8 on the FP64 sweep meshes:
+FP64 apply, FP32 apply, on-the-fly apply, FP64 set-up + PCG step and mixed-precision step,
+each timed with CUDA events) and the measured FP64 / FP32 FMA rates of the device.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hx|reference]
                        [--p P] [--n N] [--geom stored|onthefly] [--no-cpu] [--no-mixed]
-                       [--sweep] [--grad] [--precond] [--batch [--batch-reps R]]
+                       [--no-sweep] [--sweep-reps R] [--grad] [--precond] [--batch [--batch-reps R]]
        python bench.py --vcycle [--p P] [--n N]     (the LOR multigrid V-cycle alone)
        python bench.py --cheb [--p P] [--n N]       (the LOR-Chebyshev preconditioner alone)
+       python bench.py --peaks                      (the FP64 / FP32 FMA-rate probe alone)
 """
 from __future__ import annotations
 
@@ -65,6 +70,10 @@ FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
 # (p, N, geom): the 32^3 capture of the current kernel (496.3 MB read + 28.4 MB written)
 # scaled by the element count (27x at 96^3); traffic grows in proportion to the elements.
 NCU_TRAFFIC = {(4, 96, "stored"): (496.308736e6 + 28.430848e6) * 27}
+# sm__pipe_fp64_cycles_active (% of peak sustained) of the same capture: the FP64 pipe's
+# own utilization, which the algorithmic-flop fraction overstates (the even-odd folding
+# executes fewer flops than the algorithmic count)
+NCU_FP64_PIPE = {(4, 96, "stored"): 0.830}
 
 
 def alg_flops_per_element(p: int, q: int) -> int:
@@ -83,6 +92,32 @@ def alg_bytes_per_apply(p: int, q: int, E: int, n_dof: int, geom: str) -> int:
     n = p + 1
     geo = 7 * 8 * q ** 3 * E if geom == "stored" else 24 * 8 * E
     return 16 * n_dof + 4 * n ** 3 * E + geo
+
+
+# ---------------------------------------------------------------------------
+# measured arithmetic rates (the FMA-throughput probe of the library)
+# ---------------------------------------------------------------------------
+def measure_peaks(hx, torch, index=0):
+    """FP64 and FP32 FMA rates of this device: one probe launch each (16 independent FMA
+    chains per thread, 8 blocks of 256 threads per SM), timed with CUDA events on the
+    launching stream after one warm-up launch, SM clocks sampled meanwhile."""
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    with ClockSampler(index) as clk:
+        for name, fp64, iters in (("fp64", 1, 1 << 15), ("fp32", 0, 1 << 21)):
+            hx.hx_probe_fma(fp64, max(1, iters // 16))
+            torch.cuda.synchronize()
+            e0.record(s)
+            flops = hx.hx_probe_fma(fp64, iters)
+            e1.record(s)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            out[name + "_tflops"] = flops / t / 1e12
+            out[name + "_ms"] = 1e3 * t
+    out["clocks"] = clk.summary()
+    out["kernel"] = "fma_probe_kernel (paper_1910_03032_b300/csrc/hx_probe.cu), via hx_probe_fma"
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -195,17 +230,17 @@ def make_problem(hx, torch, p: int, N: int, geom: str):
     return mesh, op, b
 
 
-def time_applies(op, torch, x, reps=20, warm=3):
+def time_applies(op, torch, x, reps=20, warm=3, constrained=True):
     """Average device time of hx_op_apply (element kernel + assembly) with CUDA events on its stream."""
     y = torch.empty_like(x)
     s = torch.cuda.current_stream()
     for _ in range(warm):
-        op.apply(x, y, constrained=True)
+        op.apply(x, y, constrained=constrained)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
     for _ in range(reps):
         e0.record(s)
-        op.apply(x, y, constrained=True)
+        op.apply(x, y, constrained=constrained)
         e1.record(s)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -337,18 +372,20 @@ def run_hx(args, world, rank, local):
     # end to end through host buffers (pinned), public API, copies inside the timed region
     bh = b.cpu().pin_memory()
     xh = torch.zeros(n_dof, dtype=torch.float64).pin_memory()
+    e2e_steps = min(args.steps, 5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         op.set_coefficients(ALPHA, NU)
         info_h = hx.hx_solve_pcg_host(op.handle, bh, xh, RTOL, 20000, False)
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
-    e2e = world * n_dof * args.steps * (info_h["iterations"] + 1) / t_e2e / 1e9
+    e2e = world * n_dof * e2e_steps * (info_h["iterations"] + 1) / t_e2e / 1e9
     clocks = clk.summary()
     del bh, xh
 
     mixed = measure_mixed(hx, torch, op, b, x, args, t / args.steps, world) if not args.no_mixed else None
+    peaks = measure_peaks(hx, torch, local)
 
     line = None
     if rank == 0:
@@ -372,19 +409,24 @@ def run_hx(args, world, rank, local):
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                          "kernel": f"apply_kernel<P={p},Q={q}> (+ assembly, timed together)",
                          "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 148 SMs x 2032 MHz (derived)",
+                         "probe_tflops": peaks["fp64_tflops"],
+                         "frac_of_probe": achieved / peaks["fp64_tflops"],
+                         "fp64_pipe_ncu": NCU_FP64_PIPE.get((p, N, args.geom)),
                          "alg_flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
                          "hbm_gbs": bytes_alg / t_apply_mean / 1e9,
                          "hbm_frac": bytes_alg / t_apply_mean / 1e9 / HBM_GBS},
-            "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n_dof, "d2h_bytes_per_step": 8 * n_dof},
+            "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n_dof, "d2h_bytes_per_step": 8 * n_dof,
+                    "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "mixed": mixed,
+            "peaks_probe": peaks,
         }
     del op, mesh, b, x
     torch.cuda.empty_cache()
-    if rank == 0 and args.sweep:
-        line["sweep"] = run_sweep(hx, torch)
+    if rank == 0 and not args.no_sweep:
+        line["sweep"] = run_sweep(hx, torch, args, peaks)
     if rank == 0 and args.grad:
         line["grad"] = run_grad(hx, torch, args)
     if rank == 0 and args.precond:
@@ -740,33 +782,77 @@ def run_cheb(args):
           flush=True)
 
 
-def run_sweep(hx, torch):
-    """p = 2..8 on the FP64 sweep meshes, stored and on-the-fly: apply GDoF/s and PCG time."""
-    out = []
+def run_sweep(hx, torch, args, peaks):
+    """p = 2..8 on the FP64 sweep meshes (stored factors): per order the FP64 apply (GDoF/s, fraction
+    of the derived and of the probed FP64 peak), the FP32 apply (fraction of the measured HBM
+    bandwidth), the on-the-fly FP64 apply on the same mesh, the FP64 step (set-up + Jacobi-PCG to
+    1e-10) and the mixed-precision step (set-up + FP64 refinement around FP32 PCG to 1e-10) with its
+    refinements and its relative difference from the FP64 solution.  Applies: 10 timed after 3
+    warm-up; steps: args.sweep_reps timed after one warm-up; CUDA events on the current stream."""
+    out = {}
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            r = fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps, r
+
     for p in range(2, 9):
         N = SWEEP_N[p]
-        for geom in ("stored", "onthefly"):
-            mesh, op, b = make_problem(hx, torch, p, N, geom)
-            t_med, t_mean = time_applies(op, torch, b)
-            t32 = time_applies_f32(op, torch, b.float())
-            x = torch.zeros_like(b)
-            run_step(op, b, x)  # warm
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            info = run_step(op, b, x)
-            torch.cuda.synchronize()
-            t_pcg = time.perf_counter() - t0
-            flops = alg_flops_per_element(p, p + 2) * mesh.n_elem
-            out.append({"p": p, "N": N, "geom": geom, "n_dof": mesh.n_dof, "apply_ms": 1e3 * t_mean,
-                        "apply_gdofs": mesh.n_dof / t_mean / 1e9,
-                        "alg_tflops": flops / t_mean / 1e12, "fp64_frac": flops / t_mean / 1e12 / FP64_PEAK_TFLOPS,
-                        "pcg_s": t_pcg, "pcg_iterations": info["iterations"],
-                        "pcg_gdofs": mesh.n_dof * (info["iterations"] + 1) / t_pcg / 1e9,
-                        "apply_f32_gdofs": mesh.n_dof / t32 / 1e9,
-                        "true_rel_residual": info["true_rel_residual"]})
-            del op, mesh, b, x
-            torch.cuda.empty_cache()
+        q = p + 2
+        mesh, op, b = make_problem(hx, torch, p, N, "stored")
+        E, n_dof = mesh.n_elem, mesh.n_dof
+        t_app = time_applies(op, torch, b, reps=10)[1]
+        flops = alg_flops_per_element(p, q) * E
+        t32 = time_applies_f32(op, torch, b.float(), reps=10)
+        bytes32 = 8 * n_dof + 4 * (p + 1) ** 3 * E + 7 * 4 * q ** 3 * E
+        x = torch.zeros_like(b)
+        t_fp64, info = timed(lambda: run_step(op, b, x), args.sweep_reps)
+        xm = torch.empty_like(b)
+
+        def mixed_step():
+            op.set_coefficients(ALPHA, NU)
+            return hx.hx_solve_pcg_mixed(op.handle, b, xm, RTOL, 100000, args.inner_rtol)
+
+        t_mix, infom = timed(mixed_step, args.sweep_reps)
+        diff = float(torch.linalg.norm(xm - x) / torch.linalg.norm(x))
+        del op, x, xm
+        torch.cuda.empty_cache()
+        otf = hx.Operator(mesh, ALPHA, NU, geom_mode=hx.HX_GEOM_ONTHEFLY)
+        t_otf = time_applies(otf, torch, b, reps=10)[1]
+        del otf
+        out[str(p)] = {
+            "mesh": f"{N}^3", "q": q, "n_dof": n_dof,
+            "apply_ms": 1e3 * t_app, "apply_gdofs": n_dof / t_app / 1e9,
+            "apply_fp64_frac": flops / t_app / 1e12 / FP64_PEAK_TFLOPS,
+            "apply_fp64_frac_of_probe": flops / t_app / 1e12 / peaks["fp64_tflops"],
+            "apply_f32_ms": 1e3 * t32, "apply_f32_gdofs": n_dof / t32 / 1e9,
+            "apply_f32_hbm_frac": bytes32 / t32 / 1e9 / HBM_GBS,
+            "apply_onthefly_gdofs": n_dof / t_otf / 1e9, "onthefly_vs_stored": t_app / t_otf,
+            "fp64_step_s": t_fp64, "fp64_iterations": info["iterations"],
+            "fp64_true_rel_residual": info["true_rel_residual"],
+            "fp64_step_gdofs": n_dof * (info["iterations"] + 1) / t_fp64 / 1e9,
+            "mixed_step_s": t_mix, "mixed_speedup": t_fp64 / t_mix, "mixed_refinements": infom["refinements"],
+            "mixed_inner_iterations": infom["iterations"], "mixed_rel_residual": infom["rel_residual"],
+            "mixed_rel_diff_vs_fp64": diff,
+        }
+        del mesh, b
+        torch.cuda.empty_cache()
+    out["timing"] = (f"applies: 10 timed after 3 warm-up; steps (set-up + solve to 1e-10): {args.sweep_reps} "
+                     "timed after 1 warm-up; CUDA events")
     return out
+
+
+def run_peaks(args):
+    import torch
+    import paper_1910_03032_b300 as hx
+    print(json.dumps({"probe": "fma_rates", **measure_peaks(hx, torch)}), flush=True)
 
 
 def main():
@@ -778,7 +864,9 @@ def main():
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--n", type=int, default=96)
     ap.add_argument("--geom", default="stored", choices=["stored", "onthefly"])
-    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-order sweep (p = 2..8)")
+    ap.add_argument("--sweep-reps", type=int, default=3)
+    ap.add_argument("--peaks", action="store_true", help="run the FP64 / FP32 FMA-rate probe alone and exit")
     ap.add_argument("--batch", action="store_true", help="add the batched-solve measurement (64 instances; projection-step set)")
     ap.add_argument("--precond", action="store_true", help="add the preconditioner comparison (Jacobi vs LOR)")
     ap.add_argument("--vcycle", action="store_true",
@@ -798,6 +886,9 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.vcycle:
         run_vcycle(args)
+        return
+    if args.peaks:
+        run_peaks(args)
         return
     if args.cheb:
         run_cheb(args)

@@ -421,6 +421,17 @@ HX_API int hx_batch_lanes(const hx_batch* batch);
 HX_API void hx_batch_destroy(hx_batch* batch);
 
 /*
+ * Arithmetic-throughput probe (not part of the paper's method): enqueues on `stream`
+ * one kernel that runs `iters` steps of 16 independent FMA chains per thread, in FP64
+ * (fp64 != 0) or FP32, over 8 blocks of 256 threads per SM, and stores in *flops (host)
+ * the floating-point operations it performs (2 per FMA).  Timing the launch with CUDA
+ * events gives the device's measured FMA rate: the denominator beside which the FP64
+ * operator's roofline fraction is reported.  HX_ERR_ARG for iters < 1 or flops NULL.
+ * Stream-ordered; allocates nothing.
+ */
+HX_API hx_status hx_probe_fma(int fp64, int64_t iters, void* stream, double* flops);
+
+/*
  * Operator apply that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc.  Examples are code inside a framework whose pool allocator owns

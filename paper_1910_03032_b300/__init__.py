@@ -84,6 +84,7 @@ SIGNATURES = {
     "hx_batch_solve": (_I, [_P, _P, _P]),
     "hx_batch_lanes": (_I, [_P]),
     "hx_batch_destroy": (None, [_P]),
+    "hx_probe_fma": (_I, [_I, _I64, _P, ctypes.POINTER(_D)]),
     "hx_apply_noalloc": (_I, [_I, _I, _I64, _I64, _P, _P, _P, _P, _D, _D, _P, _P, _P]),
 }
 
@@ -315,6 +316,13 @@ def hx_solve_pcg_mixed(op, b, x, rtol=1e-10, max_it=100000, inner_rtol=1e-5, str
 def hx_op_apply_f32(op, x, y, stream=None):
     n = hx_op_info(op)[1]
     _check(_lib.hx_op_apply_f32(op, _fptr(x, n, "x"), _fptr(y, n, "y"), _stream(stream)))
+
+
+def hx_probe_fma(fp64, iters, stream=None):
+    """Enqueue the FMA-throughput probe; returns the flops the launch performs."""
+    f = _D(0.0)
+    _check(_lib.hx_probe_fma(1 if fp64 else 0, int(iters), _stream(stream), ctypes.byref(f)))
+    return f.value
 
 
 def hx_op_set_wait_limit(op, attempts):
