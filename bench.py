@@ -74,6 +74,8 @@ NCU_TRAFFIC = {(4, 96, "stored"): (496.308736e6 + 28.430848e6) * 27}
 # own utilization, which the algorithmic-flop fraction overstates (the even-odd folding
 # executes fewer flops than the algorithmic count)
 NCU_FP64_PIPE = {(4, 96, "stored"): 0.830}
+# FP32 element kernels of the mixed-precision solve (include/hx.h HX_F32_*)
+F32_KERNELS = {0: "collocated", 1: "direct_staged", 2: "direct"}
 
 
 def alg_flops_per_element(p: int, q: int) -> int:
@@ -99,7 +101,7 @@ def alg_bytes_per_apply(p: int, q: int, E: int, n_dof: int, geom: str) -> int:
 # ---------------------------------------------------------------------------
 def measure_peaks(hx, torch, index=0):
     """FP64 and FP32 FMA rates of this device: one probe launch each (16 independent FMA
-    chains per thread, 8 blocks of 256 threads per SM), timed with CUDA events on the
+    chains per thread, one wave of resident 256-thread blocks), timed with CUDA events on the
     launching stream after one warm-up launch, SM clocks sampled meanwhile."""
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -476,6 +478,7 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
     torch.cuda.synchronize()
     t_mix = reduce_max(e0.elapsed_time(e1) / 1e3, world) / args.steps
     err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+    kind, tune_ms = op.f32_kernel()
     t32 = time_applies_f32(op, torch, b.float())
     n = p + 1
     geo = 7 * 4 * q ** 3 * E if args.geom == "stored" else 24 * 8 * E
@@ -484,9 +487,12 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
             "inner_iterations": info["iterations"], "inner_rtol": args.inner_rtol,
             "rel_residual_fp64": info["rel_residual"], "rel_diff_vs_fp64_solution": err,
             "apply_f32_gdofs": n_dof / t32 / 1e9, "apply_f32_ms": 1e3 * t32,
+            "f32_kernel": F32_KERNELS.get(kind, kind),
+            "f32_autotune_ms": {F32_KERNELS[k]: v for k, v in enumerate(tune_ms) if v >= 0},
             "roofline_f32": {"bound": "hbm", "achieved": bytes32 / t32 / 1e9, "peak": HBM_GBS, "unit": "GB/s",
                              "frac": bytes32 / t32 / 1e9 / HBM_GBS, "alg_bytes_per_launch": bytes32,
-                             "kernel": f"apply_kernel<float,P={p},Q={q}> (+ assembly, timed together)"}}
+                             "kernel": f"FP32 element kernel ({F32_KERNELS.get(kind, kind)}, P={p}, Q={q}) "
+                                       "+ assembly, timed together"}}
 
 
 def batch_specs(seed=4444, n=64):
@@ -822,6 +828,7 @@ def run_sweep(hx, torch, args, peaks):
 
         t_mix, infom = timed(mixed_step, args.sweep_reps)
         diff = float(torch.linalg.norm(xm - x) / torch.linalg.norm(x))
+        kind, tune_ms = op.f32_kernel()
         del op, x, xm
         torch.cuda.empty_cache()
         otf = hx.Operator(mesh, ALPHA, NU, geom_mode=hx.HX_GEOM_ONTHEFLY)
@@ -834,6 +841,8 @@ def run_sweep(hx, torch, args, peaks):
             "apply_fp64_frac_of_probe": flops / t_app / 1e12 / peaks["fp64_tflops"],
             "apply_f32_ms": 1e3 * t32, "apply_f32_gdofs": n_dof / t32 / 1e9,
             "apply_f32_hbm_frac": bytes32 / t32 / 1e9 / HBM_GBS,
+            "f32_kernel": F32_KERNELS.get(kind, kind),
+            "f32_autotune_ms": {F32_KERNELS[k]: v for k, v in enumerate(tune_ms) if v >= 0},
             "apply_onthefly_gdofs": n_dof / t_otf / 1e9, "onthefly_vs_stored": t_app / t_otf,
             "fp64_step_s": t_fp64, "fp64_iterations": info["iterations"],
             "fp64_true_rel_residual": info["true_rel_residual"],

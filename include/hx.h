@@ -258,10 +258,40 @@ HX_API hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, doubl
 HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream);
 
 /*
+ * The FP32 element kernel of the mixed-precision solve (the paper has no counterpart; all
+ * compute the same FP32 operator as hx_op_apply_f32, to FP32 rounding):
+ *   HX_F32_COLLOCATED     interpolate with B, differentiate with the q x q collocation matrix
+ *                         Dh at the Gauss points (the FP64 kernel's form), factors staged by
+ *                         one bulk copy per block for p <= 4
+ *   HX_F32_DIRECT_STAGED  the "B/D-direct" form (u, du/dxi by B and D along each direction,
+ *                         intermediates written and read once), element-interleaved shared
+ *                         memory, restriction and stored factors brought in by bulk (TMA)
+ *                         copies at block start; stored factors only
+ *   HX_F32_DIRECT         the same with the factors read from global memory (or recomputed
+ *                         from the vertices for on-the-fly geometry)
+ *   HX_F32_AUTO           (default) the fastest of the candidates for this order, quadrature,
+ *                         geometry mode and size class (log2 of the element count), timed once
+ *                         per process by the operator's first FP32 set-up (one warm-up and three
+ *                         timed launches of each candidate, CUDA events) and cached
+ * hx_op_set_f32_kernel selects one (HX_ERR_ARG for an unknown kind, HX_ERR_UNSUPPORTED for
+ * HX_F32_DIRECT_STAGED with on-the-fly geometry); it takes effect at the next FP32 set-up.
+ * hx_op_f32_kernel reports the kernel in use (*kind = -1 before the first FP32 set-up) and,
+ * when ms is not NULL, the autotuner's average time per launch of each candidate in ms
+ * (ms[kind], -1 where not timed).  Host-side only.
+ */
+#define HX_F32_AUTO (-1)
+#define HX_F32_COLLOCATED 0
+#define HX_F32_DIRECT_STAGED 1
+#define HX_F32_DIRECT 2
+HX_API hx_status hx_op_set_f32_kernel(hx_op* op, int kind);
+HX_API hx_status hx_op_f32_kernel(const hx_op* op, int* kind, float* ms /* 3 entries or NULL */);
+
+/*
  * Failure-detection hook (the paper has no counterpart).  For p <= 4 with stored
  * factors the FP32 operator kernel stages each block's factors into shared memory
  * with one bulk (TMA) copy completed on an mbarrier, and waits for it with a bounded
- * number of mbarrier try_wait attempts (default 65536).  A block whose wait gives up
+ * number of mbarrier try_wait attempts (default 65536); the HX_F32_DIRECT_STAGED kernel also
+ * copies each block's restriction that way and waits for it (same bound) before its gather.  A block whose wait gives up
  * raises the operator's device error flag, skips its remaining stages and stores,
  * and before it exits waits again with a far larger bound, so that no copy is still
  * writing its shared memory.  hx_solve_pcg_mixed reports a raised flag as HX_ERR_CUDA
@@ -423,7 +453,8 @@ HX_API void hx_batch_destroy(hx_batch* batch);
 /*
  * Arithmetic-throughput probe (not part of the paper's method): enqueues on `stream`
  * one kernel that runs `iters` steps of 16 independent FMA chains per thread, in FP64
- * (fp64 != 0) or FP32, over 8 blocks of 256 threads per SM, and stores in *flops (host)
+ * (fp64 != 0) or FP32, over one wave of resident blocks of 256 threads (at most 8 per SM),
+ * and stores in *flops (host)
  * the floating-point operations it performs (2 per FMA).  Timing the launch with CUDA
  * events gives the device's measured FMA rate: the denominator beside which the FP64
  * operator's roofline fraction is reported.  HX_ERR_ARG for iters < 1 or flops NULL.

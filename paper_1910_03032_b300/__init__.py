@@ -75,6 +75,8 @@ SIGNATURES = {
     "hx_solve_pcg_mixed": (_I, [_P, _P, _P, _D, _I, _D, _P, ctypes.POINTER(SolveInfo)]),
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
     "hx_op_set_wait_limit": (_I, [_P, _I]),
+    "hx_op_set_f32_kernel": (_I, [_P, _I]),
+    "hx_op_f32_kernel": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
     "hx_op_collocated_mass": (_I, [_P, _P, _P]),
     "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, ctypes.c_int, _P]),
@@ -325,6 +327,21 @@ def hx_probe_fma(fp64, iters, stream=None):
     return f.value
 
 
+HX_F32_AUTO, HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED, HX_F32_DIRECT = -1, 0, 1, 2
+
+
+def hx_op_set_f32_kernel(op, kind):
+    _check(_lib.hx_op_set_f32_kernel(op, int(kind)))
+
+
+def hx_op_f32_kernel(op):
+    """(kind in use or -1, [autotuner ms per launch of each candidate, -1 where not timed])"""
+    k = _I(0)
+    ms = (ctypes.c_float * 3)()
+    _check(_lib.hx_op_f32_kernel(op, ctypes.byref(k), ms))
+    return k.value, list(ms)
+
+
 def hx_op_set_wait_limit(op, attempts):
     _check(_lib.hx_op_set_wait_limit(op, int(attempts)))
 
@@ -572,6 +589,12 @@ class Operator:
     def set_wait_limit(self, attempts):
         hx_op_set_wait_limit(self.handle, attempts)
 
+    def set_f32_kernel(self, kind):
+        hx_op_set_f32_kernel(self.handle, kind)
+
+    def f32_kernel(self):
+        return hx_op_f32_kernel(self.handle)
+
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None
         if h is not None and _lib is not None:
@@ -580,4 +603,5 @@ class Operator:
 
 __all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
                               "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS",
-                              "HX_PREC_LOR", "HX_PREC_LOR_MC", "HX_PREC_LOR_MG"]
+                              "HX_PREC_LOR", "HX_PREC_LOR_MC", "HX_PREC_LOR_MG", "HX_F32_AUTO", "HX_F32_COLLOCATED",
+                              "HX_F32_DIRECT_STAGED", "HX_F32_DIRECT"]

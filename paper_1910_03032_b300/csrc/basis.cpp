@@ -166,6 +166,13 @@ int hx_build_tables(int p, int q, HxTables* t) {
   fold(Dh.data(), q, q, t->De, t->Do);
   fold(Dht.data(), q, q, t->Dte, t->Dto);
   {
+    std::vector<double> Dt(n * q);
+    for (int a = 0; a < q; ++a)
+      for (int j = 0; j < n; ++j) Dt[j * q + a] = D[a * n + j];
+    fold(D.data(), q, n, t->Dne, t->Dno);
+    fold(Dt.data(), n, q, t->Dnte, t->Dnto);
+  }
+  {
     const int HQ = q / 2, CQ = (q + 1) / 2;
     for (int a = 0; a < CQ; ++a) {
       for (int b = 0; b < CQ; ++b) t->De2[a * CQ + b] = (b < HQ ? 2.0 : 1.0) * t->De[a * CQ + b];
@@ -207,6 +214,10 @@ void hx_tables_to_float(const HxTables& d, HxTablesF* f) {
   cp(d.Do2, f->Do2, H);
   cp(d.Dte2, f->Dte2, H);
   cp(d.Dto2, f->Dto2, H);
+  cp(d.Dne, f->Dne, H);
+  cp(d.Dno, f->Dno, H);
+  cp(d.Dnte, f->Dnte, H);
+  cp(d.Dnto, f->Dnto, H);
   cp(d.B, f->B, HX_QMAX * HX_NMAX);
   cp(d.D, f->D, HX_QMAX * HX_NMAX);
   cp(d.xq, f->xq, HX_QMAX);

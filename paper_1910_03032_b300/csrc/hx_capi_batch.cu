@@ -86,7 +86,7 @@ hx_status build_batch_graph(hx_batch* B, double rtol, int max_it, int lanes) {
       }
       if (e3 == cudaSuccess) e3 = element_apply(op, op->x, 1, nullptr, cs);
       if (e3 == cudaSuccess)
-        e3 = hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, cs);
+        e3 = hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, cs);
       if (e3 == cudaSuccess)
         e3 = hx_launch_resnorm(m->n_dof, bi, op->Ap, m->dir, op->partial, op->counters, op->scalars, cs,
                                op->singular ? &op->st->shift : nullptr);

@@ -11,8 +11,11 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hx.h"
@@ -61,13 +64,14 @@ struct hx_mesh {
   long long E = 0, n_dof = 0;
   HxTables T;
   HxTablesF T32;  // FP32 rounding of T (inner solver of the mixed-precision refinement)
-  int* R = nullptr;              // [E][n^3], g or -(g+1) for Dirichlet
+  int* R = nullptr;              // [E][n^3] (+4 ints of slack), g or -(g+1) for Dirichlet
   int* off = nullptr;            // [n_dof + 1] transpose offsets
   int* idx = nullptr;            // [E n^3] E-vector positions, increasing per DoF
   unsigned char* dir = nullptr;  // [n_dof]
   double* X8 = nullptr;          // [E][8][3]
   long long n_dirichlet = 0;     // Dirichlet DoFs (0: no boundary condition fixes the constants)
   long long grid[3] = {0, 0, 0}; // structured meshes: the logical (pN+1)-node grid of the DoFs
+  HxGridAsm ga = {};  // box meshes: the grid the assembly indexes by arithmetic (ga.p = 0: none)
 };
 
 struct hx_op {
@@ -93,10 +97,13 @@ struct hx_op {
   bool graph_failed = false;
   long long launches = 0;  // kernels enqueued by this operator so far (graph replays included)
   // FP32 inner solver of the mixed-precision refinement (allocated at the first mixed solve)
-  float* factors32 = nullptr;  // [E][7][Q3] FP32 rounding of the stored factors (+16 bytes: the bulk
-                               // copies of the element kernel round their end up to 16 bytes)
+  float* factors32 = nullptr;  // [E][hx_f32_factor_stride(q)]: FP32 rounding of the stored factors,
+                               // each element's 7 Q3 values padded to whole 16-byte units
   int* kerr = nullptr;         // device flag: a kernel's bounded wait gave up
   int wait_limit = HX_WAIT_LIMIT_DEFAULT;  // attempts of the FP32 kernel's first wait for its factors
+  int f32_request = HX_F32_AUTO;  // FP32 element kernel asked for (hx_op_set_f32_kernel)
+  int f32_kind = -1;              // FP32 element kernel in use (-1: not chosen yet)
+  float f32_ms[3] = {-1.0f, -1.0f, -1.0f};  // autotuner: average time of each candidate (ms)
   float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
   double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual
   HxCgState* st32 = nullptr;

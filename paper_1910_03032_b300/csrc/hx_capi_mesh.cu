@@ -110,7 +110,8 @@ hx_status build_mesh(int p, int q, long long n_vert, const double* vert, long lo
     return fail(HX_ERR_UNSUPPORTED, "cannot build tables for p=%d q=%d", p, q);
   }
   hx_status s;
-  if ((s = dalloc(&m->R, Renc.size(), "mesh restriction")) || (s = dalloc(&m->off, off.size(), "mesh offsets")) ||
+  // 4 ints of slack: the FP32 kernel's bulk copies of restriction ranges round their end up to 16 bytes
+  if ((s = dalloc(&m->R, Renc.size() + 4, "mesh restriction")) || (s = dalloc(&m->off, off.size(), "mesh offsets")) ||
       (s = dalloc(&m->idx, idx.size(), "mesh transpose")) || (s = dalloc(&m->dir, dmask.size(), "mesh mask")) ||
       (s = dalloc(&m->X8, X8.size(), "mesh vertices"))) {
     hx_mesh_destroy(m);
@@ -192,6 +193,7 @@ hx_status hx_mesh_create_box(int nx, int ny, int nz, int p, int q, const double*
     (*out)->grid[0] = gx;
     (*out)->grid[1] = gy;
     (*out)->grid[2] = gz;
+    (*out)->ga = hx_grid_asm(p, nx, ny, nz, (int)gx, (int)gy);
   }
   return s;
 }

@@ -17,6 +17,7 @@ HxApplyArgsF apply_args32(const hx_op* op, const float* x, const int* done) {
   a.x = x;
   a.yE = op->yE32;
   a.factors = op->factors32;
+  a.fstride = hx_f32_factor_stride(m->q);
   a.X8 = m->X8;
   a.nu_q = op->use_field ? op->nu_q : nullptr;
   a.alpha = op->alpha;
@@ -33,7 +34,82 @@ cudaError_t element_apply32(const hx_op* op, const float* x, const int* done, cu
                                           hx_launch_apply32_p4, hx_launch_apply32_p5, hx_launch_apply32_p6,
                                           hx_launch_apply32_p7, hx_launch_apply32_p8};
   const HxApplyArgsF a = apply_args32(op, x, done);
-  return t[op->mesh->p](op->mesh->T32, a, op->geom, s);
+  return t[op->mesh->p](op->mesh->T32, a, op->geom, op->f32_kind, s);
+}
+
+// Autotuned choice of the FP32 element kernel, shared by the operators of one process with the
+// same order, quadrature, geometry mode and size class (log2 of the element count).
+struct F32Key {
+  int p, q, geom, field, size_class;
+  bool operator<(const F32Key& o) const {
+    return std::tie(p, q, geom, field, size_class) < std::tie(o.p, o.q, o.geom, o.field, o.size_class);
+  }
+};
+std::mutex g_f32_mutex;
+std::map<F32Key, int> g_f32_choice;
+
+// The FP32 element kernel this operator runs: the caller's choice (hx_op_set_f32_kernel), else the
+// fastest candidate for this order, quadrature and geometry mode, timed once per process and
+// size class on this operator (one warm-up and three timed element-kernel launches each, CUDA
+// events on the solver stream).  The candidates compute the same operator; they differ in how
+// the contractions are organized (collocated derivative or B/D-direct) and in whether the stored
+// factors arrive by bulk copies.
+hx_status tune_f32(hx_op* op) {
+  if (op->f32_kind >= 0) return HX_OK;
+  if (op->f32_request >= 0) {
+    op->f32_kind = op->f32_request;
+    return HX_OK;
+  }
+  const hx_mesh* m = op->mesh;
+  int size_class = 0;
+  for (long long e = m->E; e > 1; e >>= 1) ++size_class;
+  const F32Key key{m->p, m->q, op->geom, op->use_field ? 1 : 0, size_class};
+  {
+    std::lock_guard<std::mutex> lock(g_f32_mutex);
+    auto it = g_f32_choice.find(key);
+    if (it != g_f32_choice.end()) {
+      op->f32_kind = it->second;
+      return HX_OK;
+    }
+  }
+  cudaStream_t st = op->stream;
+  int cand[3], nc = 0;
+  cand[nc++] = HX_F32_COLLOCATED;
+  if (op->geom == HX_GEOM_STORED) cand[nc++] = HX_F32_DIRECT_STAGED;
+  cand[nc++] = HX_F32_DIRECT;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(op->p32, 0, sizeof(float) * m->n_dof, st);
+  int best = cand[0];
+  float best_ms = -1.0f;
+  for (int i = 0; i < 3; ++i) op->f32_ms[i] = -1.0f;
+  for (int k = 0; k < nc && e == cudaSuccess; ++k) {
+    op->f32_kind = cand[k];
+    e = element_apply32(op, op->p32, nullptr, st);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = element_apply32(op, op->p32, nullptr, st);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    op->launches += 4;
+    op->f32_ms[cand[k]] = ms / 3.0f;
+    if (e == cudaSuccess && (best_ms < 0.0f || ms < best_ms)) {
+      best_ms = ms;
+      best = cand[k];
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) {
+    op->f32_kind = -1;
+    return cuda_fail(e, "FP32 kernel timing");
+  }
+  op->f32_kind = best;
+  std::lock_guard<std::mutex> lock(g_f32_mutex);
+  g_f32_choice[key] = best;
+  return HX_OK;
 }
 
 HxCgBuffersF cg_buffers32(const hx_op* op) {
@@ -54,6 +130,7 @@ HxCgBuffersF cg_buffers32(const hx_op* op) {
   b.z = (op->prec == HX_PREC_LOR_MG) ? op->zl32 : nullptr;
   b.cond = 0ull;
   b.nullspace = op->singular ? 1 : 0;
+  b.ga = m->ga;
   return b;
 }
 
@@ -69,7 +146,7 @@ hx_status ensure_mixed(hx_op* op) {
         (s = dalloc(&op->rn2, 1, "residual norm")) || (s = dalloc(&op->st32, 1, "FP32 state")))
       return s;
     if (op->geom == HX_GEOM_STORED &&
-        (s = dalloc(&op->factors32, (size_t)m->E * 7 * m->q * m->q * m->q + 4, "FP32 factors")))
+        (s = dalloc(&op->factors32, (size_t)m->E * hx_f32_factor_stride(m->q) + 4, "FP32 factors")))
       return s;
     HX_TRY(cudaMemsetAsync(op->st32, 0, sizeof(HxCgState), op->stream), "FP32 state init");
     op->mixed_ready = true;
@@ -91,7 +168,8 @@ hx_status ensure_mixed(hx_op* op) {
   }
   if (op->mixed_stale) {
     if (op->geom == HX_GEOM_STORED)
-      HX_TRY(hx_launch_to_float((long long)m->E * 7 * m->q * m->q * m->q, op->factors, op->factors32, op->stream),
+      HX_TRY(hx_launch_to_float_strided(m->E, 7 * m->q * m->q * m->q, (int)hx_f32_factor_stride(m->q), op->factors,
+                                        op->factors32, op->stream),
              "FP32 factors");
     if (op->prec == HX_PREC_LOR_MG) {
       HX_TRY(hx_mg_to_float(op->mg, op->stream), "FP32 multigrid levels");
@@ -104,13 +182,14 @@ hx_status ensure_mixed(hx_op* op) {
       HxDiagArgsF d;
       d.E = m->E;
       d.factors = op->factors32;
+      d.fstride = hx_f32_factor_stride(m->q);
       d.X8 = m->X8;
       d.nu_q = op->use_field ? op->nu_q : nullptr;
       d.alpha = op->alpha;
       d.nu = op->nu;
       d.dE = op->yE32;
       HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
-      HX_TRY(hx_launch_assemble32(n, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
+      HX_TRY(hx_launch_assemble32(n, m->ga, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
              "FP32 diagonal assembly");
       HX_TRY(hx_launch_dinv32(n, op->Ap32, m->dir, op->dinv32, op->stream), "FP32 dinv");
       op->launches += 3;
@@ -122,7 +201,7 @@ hx_status ensure_mixed(hx_op* op) {
     op->launches += (op->geom == HX_GEOM_STORED) ? 1 : 0;
     op->mixed_stale = false;
   }
-  return HX_OK;
+  return tune_f32(op);
 }
 
 cudaError_t cg_iteration32(const hx_op* op, cudaStream_t s, unsigned long long cond = 0ull) {
@@ -154,7 +233,7 @@ hx_status outer_residual(hx_op* op, const double* b, bool x_is_zero, cudaStream_
     HX_TRY(cudaMemsetAsync(op->Ap, 0, sizeof(double) * m->n_dof, st), "zero");
   } else {
     HX_TRY(element_apply(op, op->x, 1, nullptr, st), "refinement apply");
-    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st),
+    HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st),
            "refinement assembly");
     op->launches += 2;
   }
@@ -295,6 +374,30 @@ hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, double rtol,
   return solve_mixed(op, b, x, rtol, max_it, inner_rtol, (cudaStream_t)stream, info);
 }
 
+hx_status hx_op_set_f32_kernel(hx_op* op, int kind) {
+  if (!op) return fail(HX_ERR_ARG, "op is NULL");
+  if (kind != HX_F32_AUTO && kind != HX_F32_COLLOCATED && kind != HX_F32_DIRECT_STAGED && kind != HX_F32_DIRECT)
+    return fail(HX_ERR_ARG, "unknown FP32 kernel kind %d", kind);
+  if (kind == HX_F32_DIRECT_STAGED && op->geom != HX_GEOM_STORED)
+    return fail(HX_ERR_UNSUPPORTED, "only stored factors can be staged");
+  op->f32_request = kind;
+  op->f32_kind = -1;  // resolved (or tuned) at the next FP32 set-up
+  if (op->graph32) {
+    cudaGraphExecDestroy(op->graph32);
+    op->graph32 = nullptr;
+  }
+  op->graph32_failed = false;
+  return HX_OK;
+}
+
+hx_status hx_op_f32_kernel(const hx_op* op, int* kind, float* ms) {
+  if (!op || !kind) return fail(HX_ERR_ARG, "NULL argument");
+  *kind = op->f32_kind;
+  if (ms)
+    for (int i = 0; i < 3; ++i) ms[i] = op->f32_ms[i];
+  return HX_OK;
+}
+
 hx_status hx_op_set_wait_limit(hx_op* op, int attempts) {
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
   if (attempts < 0) return fail(HX_ERR_ARG, "attempts must be >= 0");
@@ -322,7 +425,7 @@ hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stream) {
   HX_TRY(cudaStreamWaitEvent(us, op->ev, 0), "stream wait");
   const hx_mesh* m = op->mesh;
   HX_TRY(element_apply32(op, x, nullptr, us), "FP32 element kernel");
-  HX_TRY(hx_launch_assemble32(m->n_dof, m->off, m->idx, op->yE32, m->dir, 1, x, y, us), "FP32 assembly");
+  HX_TRY(hx_launch_assemble32(m->n_dof, m->ga, m->off, m->idx, op->yE32, m->dir, 1, x, y, us), "FP32 assembly");
   op->launches += 2;
   return HX_OK;
 }

@@ -14,6 +14,7 @@ HxApplyArgs apply_args(const hx_op* op, const double* x, int constrained, const 
   a.x = x;
   a.yE = op->yE;
   a.factors = op->factors;
+  a.fstride = 7LL * m->q * m->q * m->q;
   a.X8 = m->X8;
   a.nu_q = op->use_field ? op->nu_q : nullptr;
   a.alpha = op->alpha;
@@ -150,13 +151,14 @@ hx_status ensure_diag(hx_op* op, cudaStream_t s, int* nl) {
   HxDiagArgs d;
   d.E = m->E;
   d.factors = op->factors;
+  d.fstride = 7LL * m->q * m->q * m->q;
   d.X8 = m->X8;
   d.nu_q = op->use_field ? op->nu_q : nullptr;
   d.alpha = op->alpha;
   d.nu = op->nu;
   d.dE = op->yE;
   HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
-  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
+  HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
          "diagonal assembly");
   *nl += 2;
   op->diag_stale = false;
@@ -173,7 +175,7 @@ hx_status refresh_dinv(hx_op* op, cudaStream_t s, int* nl) {
   if (op->prec == HX_PREC_COLLOCATED_MASS) {
     if (!(op->alpha > 0.0)) return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
     HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
-    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->pdiag, s),
+    HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->pdiag, s),
            "collocated mass assembly");
     *nl += 2;
     d = op->pdiag;
@@ -283,7 +285,7 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
       la.fq = nullptr;
       la.yE = op->yE;
       e = load_launcher(m->p)(m->T, la, s);
-      if (e == cudaSuccess) e = hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->m1, s);
+      if (e == cudaSuccess) e = hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->m1, s);
       if (e != cudaSuccess) { st = cuda_fail(e, "mass row sums"); break; }
       op->launches += 2;
     }
@@ -340,7 +342,7 @@ hx_status hx_op_apply(hx_op* op, const double* x, double* y, int constrained, vo
   cudaStream_t s = (cudaStream_t)stream;
   const hx_mesh* m = op->mesh;
   HX_TRY(element_apply(op, x, constrained, nullptr, s), "element kernel");
-  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, constrained, x, 0.0, y, s), "assembly");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, constrained, x, 0.0, y, s), "assembly");
   op->launches += 2;
   return HX_OK;
 }
@@ -368,7 +370,7 @@ hx_status hx_op_load_vector(hx_op* op, const double* f_q, double* b, void* strea
   a.fq = f_q;
   a.yE = op->yE;
   HX_TRY(load_launcher(m->p)(m->T, a, s), "load kernel");
-  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, b, s), "assembly");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, b, s), "assembly");
   op->launches += 2;
   return HX_OK;
 }

@@ -27,6 +27,7 @@ HxCgBuffers cg_buffers(const hx_op* op) {
   b.z = (op->prec == HX_PREC_LOR || op->prec == HX_PREC_LOR_MG) ? op->zl : nullptr;
   b.cond = 0ull;
   b.nullspace = op->singular ? 1 : 0;
+  b.ga = m->ga;
   return b;
 }
 
@@ -152,7 +153,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   HX_TRY(hx_launch_cg_init(buf, b, use_x0 ? x : nullptr, rtol, max_it, st), "cg init");
   if (use_x0) {
     HX_TRY(element_apply(op, op->x, 1, nullptr, st), "cg x0 apply");
-    HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "cg x0 assembly");
+    HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "cg x0 assembly");
     HX_TRY(hx_launch_cg_residual(buf, st), "cg residual");
     op->launches += 3;
   }
@@ -189,7 +190,7 @@ hx_status solve_device(hx_op* op, const double* b, double* x, double rtol, int m
   }
   // true residual ||P b - A_c x|| with one extra apply
   HX_TRY(element_apply(op, op->x, 1, nullptr, st), "residual apply");
-  HX_TRY(hx_launch_assemble(m->n_dof, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "residual assembly");
+  HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, st), "residual assembly");
   HX_TRY(hx_launch_resnorm(m->n_dof, b, op->Ap, m->dir, op->partial, op->counters, op->scalars, st,
                            op->singular ? &op->st->shift : nullptr),
          "residual norm");

@@ -321,12 +321,12 @@ __global__ void __launch_bounds__(NT, MINB)
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
   // the copy starts at the 16-byte boundary at or below element e0's first factor
-  const int foff = STAGE ? (int)(((e0 * FE * (long long)sizeof(Real)) & 15) / (long long)sizeof(Real)) : 0;
+  const int foff = STAGE ? (int)(((e0 * A.fstride * (long long)sizeof(Real)) & 15) / (long long)sizeof(Real)) : 0;
 
   if (STAGE) {
     if (tid == 0) {
       const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
-      const long long b0 = e0 * FE * (long long)sizeof(Real), b1 = (e0 + nel) * FE * (long long)sizeof(Real);
+      const long long b0 = e0 * A.fstride * (long long)sizeof(Real), b1 = (e0 + nel) * A.fstride * (long long)sizeof(Real);
       const long long a0 = b0 & ~15LL, a1 = (b1 + 15) & ~15LL;  // the factor array has 16 bytes of slack
       wait_failed = 0;
       mbar_init(&fbar, 1);
@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(NT, MINB)
   } else if (GEOM == HX_KGEOM_STORED) {
     // pull this block's factors toward L2 while the forward contractions run
     const long long nel = (A.E - e0) < NE ? (A.E - e0) : NE;
-    const char* base = reinterpret_cast<const char*>(A.factors + e0 * 7 * Q3);
-    const long long bytes = nel * 7 * Q3 * (long long)sizeof(Real);
+    const char* base = reinterpret_cast<const char*>(A.factors + e0 * A.fstride);
+    const long long bytes = nel * A.fstride * (long long)sizeof(Real);
     for (long long off = (long long)tid * 128; off < bytes; off += (long long)NT * 128)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
   } else {
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(NT, MINB)
       Real f[7];
       if (STAGE) {
         if (e < A.E) {
-          const Real* fe = sf + foff + cel * FE + pt;
+          const Real* fe = sf + foff + cel * A.fstride + pt;
 #pragma unroll
           for (int m = 0; m < 7; ++m) f[m] = fe[m * Q3];
         } else {
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(NT, MINB)
         }
       } else if (GEOM == HX_KGEOM_STORED) {
         if (e < A.E) {
-          const Real* fe = A.factors + e * 7 * Q3 + pt;
+          const Real* fe = A.factors + e * A.fstride + pt;
 #pragma unroll
           for (int m = 0; m < 7; ++m) f[m] = __ldg(fe + m * Q3);
         } else {
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
     if (e < A.E) {
       if (GEOM == HX_KGEOM_STORED) {
 #pragma unroll
-        for (int c = 0; c < 7; ++c) f[c] = A.factors[(e * 7 + c) * Q3 + pt];
+        for (int c = 0; c < 7; ++c) f[c] = A.factors[e * A.fstride + c * Q3 + pt];
       } else {
         const int iq = pt % Q, jq = (pt / Q) % Q, kq = pt / (Q * Q);
         Real j0[3], j1[3], j2[3];
@@ -863,7 +863,7 @@ cudaError_t launch_apply_impl(const HxTablesT<Real>& T, const HxApplyArgsT<Real>
   using Lt = Layout<Q, Real>;
   constexpr bool STAGE = Lt::F32 && GEOM == HX_KGEOM_STORED && P <= 4;  // the kernel stages the factors
   // the copy rounds its start down and its end up to 16 bytes: up to 6 more words
-  const size_t words = STAGE ? (size_t)((NE * Lt::R3 + 3) & ~3) + (size_t)NE * 7 * Q * Q * Q + 8
+  const size_t words = STAGE ? (size_t)((NE * Lt::R3 + 3) & ~3) + (size_t)NE * ((7 * Q * Q * Q + 3) & ~3) + 8
                              : (size_t)NE * Lt::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0);
   const size_t shmem = sizeof(Real) * words;
   auto k = apply_kernel<Real, P, Q, NE, NT, MINB, GEOM, NUF>;
@@ -939,9 +939,14 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
     if (T.q == P + 2) return hx::launch_apply_q<double, P, P + 2>(T, A, geom, s);                         \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
-  cudaError_t hx_launch_apply32_p##P(const HxTablesF& T, const HxApplyArgsF& A, int geom, cudaStream_t s) { \
-    if (T.q == P + 1) return hx::launch_apply_q<float, P, P + 1>(T, A, geom, s);                          \
-    if (T.q == P + 2) return hx::launch_apply_q<float, P, P + 2>(T, A, geom, s);                          \
+  cudaError_t hx_launch_apply32_p##P(const HxTablesF& T, const HxApplyArgsF& A, int geom, int kind,      \
+                                     cudaStream_t s) {                                                     \
+    if (T.q == P + 1)                                                                                      \
+      return kind == 0 ? hx::launch_apply_q<float, P, P + 1>(T, A, geom, s)                                \
+                       : hx::launch_apply32_q<P, P + 1>(T, A, geom, kind == 1, s);                         \
+    if (T.q == P + 2)                                                                                      \
+      return kind == 0 ? hx::launch_apply_q<float, P, P + 2>(T, A, geom, s)                                \
+                       : hx::launch_apply32_q<P, P + 2>(T, A, geom, kind == 1, s);                         \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_diag_p##P(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {     \

@@ -16,7 +16,8 @@ struct HxApplyArgsT {
   const int* R;           // [E][n^3] restriction; g >= 0 free DoF, -(g+1) Dirichlet DoF
   const T* x;             // L-vector input
   T* yE;                  // [E][n^3] E-vector output
-  const T* factors;       // stored geometry: [E][7][q^3] (m, G00, G01, G02, G11, G12, G22)
+  const T* factors;       // stored geometry: [E][fstride], 7 planes of q^3 (m, G00, G01, G02, G11, G12, G22)
+  long long fstride;      // element stride of `factors` (7 q^3, or the padded FP32 stride)
   const double* X8;       // [E][8][3] element corner coordinates (on-the-fly geometry)
   const double* nu_q;     // [E][q^3] per-point viscosity or null (on-the-fly geometry)
   double alpha, nu;       // Helmholtz coefficients (on-the-fly geometry)
@@ -30,11 +31,16 @@ typedef HxApplyArgsT<double> HxApplyArgs;
 #define HX_WAIT_LIMIT_EXIT (1 << 20)     // attempts of the wait before a block exits
 typedef HxApplyArgsT<float> HxApplyArgsF;
 
+// Element stride of the FP32 factor array: the 7 q^3 factors of an element rounded up to
+// whole 16-byte units, so that every element's factors can be moved by one bulk copy.
+inline long long hx_f32_factor_stride(int q) { return ((7LL * q * q * q) + 3) & ~3LL; }
+
 // Arguments of the diagonal kernel (sum-factorized diag of the element matrices).
 template <typename T>
 struct HxDiagArgsT {
   long long E;
   const T* factors;       // stored geometry or null
+  long long fstride;      // element stride of `factors`
   const double* X8;
   const double* nu_q;
   double alpha, nu;
@@ -69,7 +75,8 @@ typedef cudaError_t (*hx_apply_launcher)(const HxTables&, const HxApplyArgs&, in
 typedef cudaError_t (*hx_diag_launcher)(const HxTables&, const HxDiagArgs&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_diag32_launcher)(const HxTablesF&, const HxDiagArgsF&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cudaStream_t);
-typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, cudaStream_t);
+// kind: HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED or HX_F32_DIRECT (include/hx.h)
+typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, int kind, cudaStream_t);
 typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cudaStream_t);
 
 #define HX_DECLARE_ORDER(P)                                                                        \
@@ -77,7 +84,7 @@ typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cuda
   cudaError_t hx_launch_diag_p##P(const HxTables&, const HxDiagArgs&, int, cudaStream_t);         \
   cudaError_t hx_launch_diag32_p##P(const HxTablesF&, const HxDiagArgsF&, int, cudaStream_t);     \
   cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);              \
-  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, cudaStream_t);  \
+  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, int, cudaStream_t); \
   cudaError_t hx_launch_grad_p##P(const HxTables&, const HxGradArgs&, cudaStream_t);
 HX_DECLARE_ORDER(1)
 HX_DECLARE_ORDER(2)
@@ -95,9 +102,35 @@ cudaError_t hx_launch_qpoint_coords(const HxTables& T, long long E, const double
                                     cudaStream_t s);
 cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int* off, const int* idx,
                                   const double* X8, double* xyz, cudaStream_t s);
+// Logical grid of a box mesh (elements nx x ny x nz numbered x fastest, DoFs on the
+// (p nx + 1) x (p ny + 1) x (p nz + 1) node grid, lexicographic local nodes): the assembly then
+// finds a DoF's element entries by index arithmetic instead of reading the transpose map, in the
+// same (increasing E-vector position) order.  p = 0: no such grid, the map is read.
+struct HxGridAsm {
+  int p, nx, ny, nz, gx, gy;
+  // n / d = (n m) >> s for 0 <= n < 2^31 (d = gx, gy, p): multiply-shift instead of division
+  unsigned mgx, mgy, mp;
+  int sgx, sgy, sp;
+};
+// Multiplier and shift of the division by d (1 <= d < 2^31) for dividends below 2^31:
+// s = 31 + ceil(log2 d), m = floor(2^s / d) + 1 (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994: exact for every 31-bit dividend).
+inline void hx_fastdiv_init(int d, unsigned* m, int* s) {
+  int l = 0;
+  while ((1LL << l) < d) ++l;
+  *s = 31 + l;
+  *m = (unsigned)((1ULL << *s) / (unsigned long long)d + 1ULL);
+}
+inline HxGridAsm hx_grid_asm(int p, int nx, int ny, int nz, int gx, int gy) {
+  HxGridAsm g = {p, nx, ny, nz, gx, gy, 0, 0, 0, 0, 0, 0};
+  hx_fastdiv_init(gx, &g.mgx, &g.sgx);
+  hx_fastdiv_init(gy, &g.mgy, &g.sgy);
+  hx_fastdiv_init(p, &g.mp, &g.sp);
+  return g;
+}
 // y[g] = sum_{k in off[g]..off[g+1]} yE[idx[k]]; with `constrained`, Dirichlet rows
 // (dir[g] != 0) take x[g] (x non-null) or dir_const.
-cudaError_t hx_launch_assemble(long long n_dof, const int* off, const int* idx, const double* yE,
+cudaError_t hx_launch_assemble(long long n_dof, const HxGridAsm& ga, const int* off, const int* idx, const double* yE,
                                const unsigned char* dir, int constrained, const double* x,
                                double dir_const, double* y, cudaStream_t s);
 
@@ -140,6 +173,7 @@ struct HxCgBuffersT {
   const Real* z;            // preconditioned residual computed outside the CG kernels, or NULL (Jacobi: dinv r)
   unsigned long long cond;  // CUDA graph conditional handle of the enclosing while loop, or 0
   int nullspace;            // 1: singular operator with the constants as null space (pure Neumann Poisson)
+  HxGridAsm ga;             // logical grid of a box mesh (ga.p = 0: read the transpose map)
 };
 typedef HxCgBuffersT<double> HxCgBuffers;
 typedef HxCgBuffersT<float> HxCgBuffersF;
@@ -251,14 +285,17 @@ cudaError_t hx_mg_vcycle32(const HxMg& M, const float* r, float* z, const int* d
 cudaError_t hx_mg_to_float(const HxMg& M, cudaStream_t s);
 int hx_mg_vcycle_launches(const HxMg& M);
 // mixed-precision refinement helpers
-cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
-                                 int constrained, const float* x, float* y, cudaStream_t s);
+cudaError_t hx_launch_assemble32(long long n, const HxGridAsm& ga, const int* off, const int* idx, const float* yE,
+                                 const unsigned char* dir, int constrained, const float* x, float* y, cudaStream_t s);
 cudaError_t hx_launch_ir_residual(long long n, const double* b, const double* Ax, const unsigned char* dir, double* r,
                                   double* partial, unsigned int* counter, double* rn2, cudaStream_t s,
                                   const double* shift = nullptr);
 cudaError_t hx_launch_ir_scale_down(long long n, const double* r, const double* rn2, float* r32, cudaStream_t s);
 cudaError_t hx_launch_ir_update(long long n, double* x, const float* d, const double* rn2, cudaStream_t s);
 cudaError_t hx_launch_to_float(long long n, const double* a, float* b, cudaStream_t s);
+// b[e * stride + k] = a[e * per + k] for k < per, b[e * stride + k] = 0 for per <= k < stride
+cudaError_t hx_launch_to_float_strided(long long E, int per, int stride, const double* a, float* b,
+                                       cudaStream_t s);
 cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,
                           double* out, cudaStream_t s);
 cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,

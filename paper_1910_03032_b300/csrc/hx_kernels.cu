@@ -196,11 +196,50 @@ __device__ __forceinline__ Real gather_sum(long long g, const int* __restrict__ 
   return s;
 }
 
+// The same sum for a DoF of a box mesh, its element entries found by index arithmetic: along
+// each axis a node interior to an element row belongs to one element, a node between two
+// elements to both (the lower one with local index p, the upper with 0); the entries are
+// visited with the element index increasing (z, then y, then x outermost to innermost), the
+// order of the transpose map.
+__device__ __forceinline__ int fast_div(int n, unsigned m, int s) {
+  return (int)(((unsigned long long)(unsigned)n * m) >> s);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real gather_sum_grid(long long g, const HxGridAsm& G, const Real* __restrict__ yE) {
+  const int p = G.p, n = p + 1, n3 = n * n * n;
+  const int gi = (int)g;  // n_dof < 2^31 (checked when the mesh is built)
+  const int t = fast_div(gi, G.mgx, G.sgx), I = gi - t * G.gx;
+  const int K = fast_div(t, G.mgy, G.sgy), J = t - K * G.gy;
+  int ex[2], lx[2], ey[2], ly[2], ez[2], lz[2];
+  auto axis = [&](int X, int ne, int* e, int* l) {
+    const int q = fast_div(X, G.mp, G.sp), r = X - q * p;
+    if (r == 0 && q > 0 && q < ne) {  // between elements q - 1 and q
+      e[0] = q - 1;
+      l[0] = p;
+      e[1] = q;
+      l[1] = 0;
+      return 2;
+    }
+    e[0] = q < ne ? q : ne - 1;
+    l[0] = q < ne ? r : p;
+    return 1;
+  };
+  const int cx = axis(I, G.nx, ex, lx), cy = axis(J, G.ny, ey, ly), cz = axis(K, G.nz, ez, lz);
+  Real s = Real(0);
+  for (int a = 0; a < cz; ++a)
+    for (int b = 0; b < cy; ++b) {
+      const int eyz = G.nx * (ey[b] + G.ny * ez[a]), lyz = n * (ly[b] + n * lz[a]);
+      for (int c = 0; c < cx; ++c) s += __ldg(yE + (ex[c] + eyz) * n3 + lx[c] + lyz);
+    }
+  return s;
+}
+
 #define HX_GRID_STRIDE(g, n) \
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (n); g += (long long)gridDim.x * blockDim.x)
 
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const int* __restrict__ off,
+__global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const HxGridAsm ga, const int* __restrict__ off,
                                                              const int* __restrict__ idx, const Real* __restrict__ yE,
                                                              const unsigned char* __restrict__ dir, int constrained,
                                                              const Real* __restrict__ x, double dir_const,
@@ -208,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const i
   HX_GRID_STRIDE(g, n) {
     Real s;
     if (constrained && dir[g]) s = x ? x[g] : Real(dir_const);
-    else s = gather_sum(g, off, idx, yE);
+    else s = ga.p ? gather_sum_grid(g, ga, yE) : gather_sum(g, off, idx, yE);
     y[g] = s;
   }
 }
@@ -317,7 +356,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuf
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, B.n) {
     const Real pg = B.p[g];
-    const Real ap = B.dir[g] ? pg : gather_sum(g, B.off, B.idx, B.yE);
+    const Real ap = B.dir[g] ? pg : (B.ga.p ? gather_sum_grid(g, B.ga, B.yE) : gather_sum(g, B.off, B.idx, B.yE));
     B.Ap[g] = ap;
     acc[0] += (double)pg * (double)ap;
   }
@@ -478,6 +517,16 @@ __global__ void __launch_bounds__(kThreads) to_float_kernel(long long n, const d
   HX_GRID_STRIDE(g, n) { b[g] = (float)a[g]; }
 }
 
+__global__ void __launch_bounds__(kThreads) to_float_strided_kernel(long long E, int per, int stride,
+                                                                     const double* __restrict__ a,
+                                                                     float* __restrict__ b) {
+  HX_GRID_STRIDE(g, E * stride) {
+    const long long e = g / stride;
+    const int k = (int)(g - e * stride);
+    b[g] = (k < per) ? (float)a[e * per + k] : 0.0f;
+  }
+}
+
 __global__ void __launch_bounds__(HX_RED_THREADS) dot_kernel(long long n, const double* __restrict__ a,
                                                               const double* __restrict__ c, double* partial,
                                                               unsigned int* counter, double* out) {
@@ -536,15 +585,17 @@ cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int*
   return cudaGetLastError();
 }
 
-cudaError_t hx_launch_assemble(long long n, const int* off, const int* idx, const double* yE, const unsigned char* dir,
+cudaError_t hx_launch_assemble(long long n, const HxGridAsm& ga, const int* off, const int* idx, const double* yE,
+                               const unsigned char* dir,
                                int constrained, const double* x, double dir_const, double* y, cudaStream_t s) {
-  assemble_kernel<double><<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, dir_const, y);
+  assemble_kernel<double><<<grid_for(n), kThreads, 0, s>>>(n, ga, off, idx, yE, dir, constrained, x, dir_const, y);
   return cudaGetLastError();
 }
 
-cudaError_t hx_launch_assemble32(long long n, const int* off, const int* idx, const float* yE, const unsigned char* dir,
+cudaError_t hx_launch_assemble32(long long n, const HxGridAsm& ga, const int* off, const int* idx, const float* yE,
+                                 const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s) {
-  assemble_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, off, idx, yE, dir, constrained, x, 0.0, y);
+  assemble_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, ga, off, idx, yE, dir, constrained, x, 0.0, y);
   return cudaGetLastError();
 }
 
@@ -667,6 +718,11 @@ cudaError_t hx_launch_ir_update(long long n, double* x, const float* d, const do
 }
 cudaError_t hx_launch_to_float(long long n, const double* a, float* b, cudaStream_t s) {
   to_float_kernel<<<grid_for(n), kThreads, 0, s>>>(n, a, b);
+  return cudaGetLastError();
+}
+cudaError_t hx_launch_to_float_strided(long long E, int per, int stride, const double* a, float* b,
+                                       cudaStream_t s) {
+  to_float_strided_kernel<<<grid_for(E * stride), kThreads, 0, s>>>(E, per, stride, a, b);
   return cudaGetLastError();
 }
 cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double* partial, unsigned int* counter,

@@ -150,6 +150,7 @@ extern "C" hx_status hx_apply_noalloc(int p, int q, int64_t n_elem, int64_t n_do
   a.x = x;
   a.yE = scratch;
   a.factors = nullptr;
+  a.fstride = 0;
   a.X8 = X8;
   a.nu_q = nullptr;
   a.alpha = alpha;
@@ -159,7 +160,9 @@ extern "C" hx_status hx_apply_noalloc(int p, int q, int64_t n_elem, int64_t n_do
   a.err = nullptr;
   a.wait_limit = HX_WAIT_LIMIT_DEFAULT;
   e = launch_order(p, T, a, s);
-  if (e == cudaSuccess) e = hx_launch_assemble(n_dof, t_offsets, t_indices, scratch, nullptr, 0, nullptr, 0.0, y, s);
+  const HxGridAsm no_grid = {};  // p = 0: the caller's transpose map is read
+  if (e == cudaSuccess)
+    e = hx_launch_assemble(n_dof, no_grid, t_offsets, t_indices, scratch, nullptr, 0, nullptr, 0.0, y, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(HX_ERR_CUDA, cudaGetErrorString(e));

@@ -3,7 +3,8 @@
 //
 // Every thread runs 16 independent FMA chains x <- x a + c (0 < a < 1, so the values stay
 // bounded and normal), enough independent work per warp to keep the FMA pipe issuing; the
-// caller times one launch with CUDA events and divides the returned flop count by it.
+// caller times one launch with CUDA events and divides the returned flop count by it.  The
+// grid is one wave of resident blocks (at most 8 of 256 threads per SM).
 #include <cuda_runtime.h>
 
 #include "hx.h"
@@ -48,7 +49,17 @@ extern "C" hx_status hx_probe_fma(int fp64, int64_t iters, void* stream, double*
     hx_internal_set_error(cudaGetErrorString(e));
     return HX_ERR_CUDA;
   }
-  const unsigned blocks = (unsigned)(sms * kBlocksPerSM);
+  // exactly the blocks that are resident at once (one wave: no partly filled last wave)
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_probe_kernel<double>, kThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_probe_kernel<float>, kThreads, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    hx_internal_set_error("hx_probe_fma: occupancy query failed");
+    return HX_ERR_CUDA;
+  }
+  const unsigned blocks = (unsigned)(sms * (per_sm < kBlocksPerSM ? per_sm : kBlocksPerSM));
   cudaStream_t s = (cudaStream_t)stream;
   if (fp64)
     fma_probe_kernel<double><<<blocks, kThreads, 0, s>>>(iters, 0.999999, 1e-7);

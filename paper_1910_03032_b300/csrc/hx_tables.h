@@ -45,6 +45,12 @@ struct HxTablesT {
   // even/odd parts of the result, ready to feed the next contraction along the same direction.
   T Dte2[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
   T Dto2[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_QMAX)];
+  // folded D (sigma = -1): M = q, L = n (derivative of the nodal basis at the Gauss points)
+  T Dne[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_NMAX)];
+  T Dno[HX_HALF_UP(HX_QMAX) * HX_HALF_UP(HX_NMAX)];
+  // folded D^T (sigma = -1): M = n, L = q
+  T Dnte[HX_HALF_UP(HX_NMAX) * HX_HALF_UP(HX_QMAX)];
+  T Dnto[HX_HALF_UP(HX_NMAX) * HX_HALF_UP(HX_QMAX)];
   // unfolded tables, row-major
   T B[HX_QMAX * HX_NMAX];
   T D[HX_QMAX * HX_NMAX];

@@ -1,3 +1,3 @@
 // Kernels of the order-1 operator (q = 2 and 3).
-#include "hx_element.cuh"
+#include "hx_element32.cuh"
 HX_DEFINE_ORDER(1)

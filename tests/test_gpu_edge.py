@@ -83,8 +83,12 @@ def test_single_element_every_order(hx, p):
             y = op.apply(to_dev(x)).cpu().numpy()
             assert rel_err(y, oop.apply(x)) <= 1e-12, (q, gm)
             x32 = x.astype(np.float32)       # the FP32 operator is the constrained A_c
-            y32 = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
-            assert rel_err(y32, oop.apply(x32.astype(np.float64), constrained=True)) <= 2e-5, (q, gm)
+            ref32 = oop.apply(x32.astype(np.float64), constrained=True)
+            kinds = [hx.HX_F32_COLLOCATED, hx.HX_F32_DIRECT] + ([hx.HX_F32_DIRECT_STAGED] if gm == 0 else [])
+            for kind in kinds:
+                op.set_f32_kernel(kind)
+                y32 = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
+                assert rel_err(y32, ref32) <= 2e-5, (q, gm, kind)
 
 
 @pytest.mark.parametrize("p", [1, 2, 4])

@@ -1,8 +1,9 @@
 """Failure detection without a GPU fault.
 
-For p <= 4 with stored factors the FP32 operator kernel stages each block's factors
-into shared memory with one bulk (TMA) copy and waits for it with a bounded number of
-mbarrier try_wait attempts.  Here that bound is set to 0 (hx_op_set_wait_limit), so
+For p <= 4 with stored factors the collocated FP32 operator kernel stages each block's
+factors into shared memory with one bulk (TMA) copy, and the B/D-direct kernel with staged
+factors copies each block's restriction and factors that way; both wait for the copies with
+a bounded number of mbarrier try_wait attempts.  Here that bound is set to 0 (hx_op_set_wait_limit), so
 every block's first wait gives up at once while the copies themselves complete
 normally: each block raises the operator's error flag, skips its remaining stages,
 and waits for its copy (with the far larger exit bound) before it exits.  The mixed
@@ -21,13 +22,15 @@ DEFAULT_WAIT_LIMIT = 1 << 16
 
 
 @pytest.mark.parametrize("p", [2, 4])
-def test_bounded_wait_gives_up_as_a_status(p):
+@pytest.mark.parametrize("kind", [0, 1])  # collocated (staged for p <= 4), B/D-direct staged
+def test_bounded_wait_gives_up_as_a_status(p, kind):
     from oracle import fem
     from oracle.solve import jacobi_pcg
     hx = require_gpu()
     shape = (4, 4, 3)
     V, EV, om = case(shape, p)
     op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1.0, 1.0)
+    op.set_f32_kernel(kind)
     b = S.random_vector(om.n_dof, 21)
     bd = to_dev(b)
     x0, info0 = op.solve_mixed(bd, rtol=1e-10)

@@ -23,20 +23,41 @@ def hx():
 
 @pytest.mark.parametrize("p,shape", [(1, (5, 5, 3)), (2, (5, 5, 3)), (3, (5, 5, 3)), (4, (5, 3, 3)), (5, (4, 3, 2)),
                                      (6, (3, 3, 1)), (7, (2, 2, 2)), (8, (3, 3, 1))])
-@pytest.mark.parametrize("geom", [0, 1])
-def test_fp32_apply_matches_oracle(hx, p, shape, geom):
+@pytest.mark.parametrize("geom,kind", [(0, -1), (0, 0), (0, 1), (0, 2), (1, -1), (1, 0), (1, 2)])
+def test_fp32_apply_matches_oracle(hx, p, shape, geom, kind):
+    """Every FP32 element kernel (collocated, B/D-direct with staged or loaded factors, and the
+    autotuner's pick) on meshes spanning several blocks with a ragged last block."""
     from oracle import fem
     V, EV, om = case(shape, p)
     op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1.7, 0.45, geom_mode=geom)
+    op.set_f32_kernel(kind)
     x32 = S.random_vector(om.n_dof, 3032).astype(np.float32)
     y = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
     ref = fem.Operator(om, 1.7, 0.45).apply(x32.astype(np.float64), constrained=True)
     assert rel_err(y, ref) <= 2e-5, rel_err(y, ref)
+    used, ms = op.f32_kernel()
+    assert used == kind if kind >= 0 else used in ((0, 1, 2) if geom == 0 else (0, 2))
+    if kind < 0 and used >= 0 and ms[used] >= 0:  # tuned here (not taken from the process cache)
+        assert ms[used] == min(m for m in ms if m >= 0)
+
+
+def test_fp32_kernel_selection_errors(hx):
+    V = S.structured_vertices(2, 2, 2, 0.1, 5)
+    mesh = hx.Mesh.structured(2, 2, 2, 3, 5, V)
+    op = hx.Operator(mesh, 1.0, 1.0, geom_mode=hx.HX_GEOM_ONTHEFLY)
+    with pytest.raises(hx.HxError) as ei:
+        op.set_f32_kernel(hx.HX_F32_DIRECT_STAGED)
+    assert ei.value.status == hx.HX_ERR_UNSUPPORTED
+    with pytest.raises(hx.HxError) as ei:
+        op.set_f32_kernel(7)
+    assert ei.value.status == hx.HX_ERR_ARG
+    assert op.f32_kernel()[0] == -1  # nothing chosen before the first FP32 set-up
 
 
 @pytest.mark.parametrize("p", [3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("geom", [0, 1])
-def test_mixed_solve_reaches_fp64_tolerance(hx, p, geom):
+@pytest.mark.parametrize("kind", [-1, 0, 2])
+def test_mixed_solve_reaches_fp64_tolerance(hx, p, geom, kind):
     """4^3 perturbed mesh, alpha = nu = 1, manufactured right-hand side (the small config at p = 4..8)."""
     from oracle import fem
     from oracle.solve import jacobi_pcg
@@ -44,6 +65,7 @@ def test_mixed_solve_reaches_fp64_tolerance(hx, p, geom):
     V, EV, om = case(shape, p)
     mesh = hx.Mesh.structured(*shape, p, p + 2, V)
     op = hx.Operator(mesh, 1.0, 1.0, geom_mode=geom)
+    op.set_f32_kernel(kind if (kind != 2 or geom == 1) else 1)  # stored: the staged direct kernel
     f = (1.0 + 3 * np.pi ** 2) * mms_exact(mesh.qpoint_coords().cpu().numpy())
     b = op.load_vector(to_dev(f))
     x, info = op.solve_mixed(b, rtol=1e-10, inner_rtol=1e-5)
