@@ -23,10 +23,13 @@ __global__ void __launch_bounds__(kThreads) fma_probe_kernel(long long iters, T 
   T x[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) x[k] = T(threadIdx.x + k) * T(1e-3);
+  // both multiplier and addend in registers (a constant-bank operand can slow the FMA issue)
+  const bool never = threadIdx.x > 4096u;  // false for every thread (at most 256 per block)
+  const T ar = never ? c : a, cr = never ? a : c;
 #pragma unroll 4
   for (long long i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], a, c);
+    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], ar, cr);
   }
   T s = T(0);
 #pragma unroll
