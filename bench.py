@@ -26,7 +26,8 @@ each timed with CUDA events) and the measured FP64 / FP32 FMA rates of the devic
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hx|reference]
                        [--p P] [--n N] [--geom stored|onthefly] [--no-cpu] [--no-mixed]
-                       [--no-sweep] [--sweep-reps R] [--grad] [--precond] [--batch [--batch-reps R]]
+                       [--no-sweep] [--sweep-reps R] [--f32-kernel K] [--grad] [--precond]
+                       [--batch [--batch-reps R]]
        python bench.py --vcycle [--p P] [--n N]     (the LOR multigrid V-cycle alone)
        python bench.py --cheb [--p P] [--n N]       (the LOR-Chebyshev preconditioner alone)
        python bench.py --peaks                      (the FP64 / FP32 FMA-rate probe alone)
@@ -75,7 +76,7 @@ NCU_TRAFFIC = {(4, 96, "stored"): (496.308736e6 + 28.430848e6) * 27}
 # executes fewer flops than the algorithmic count)
 NCU_FP64_PIPE = {(4, 96, "stored"): 0.830}
 # FP32 element kernels of the mixed-precision solve (include/hx.h HX_F32_*)
-F32_KERNELS = {0: "collocated", 1: "direct_staged", 2: "direct"}
+F32_KERNELS = {0: "collocated", 1: "direct_staged", 2: "direct", 3: "mma_bf16", 4: "mma_bf16x3"}
 
 
 def alg_flops_per_element(p: int, q: int) -> int:
@@ -461,6 +462,7 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
     p, q = args.p, args.p + 2
     E, n_dof = hx.hx_op_info(op.handle)[:2]
     xm = torch.empty_like(b)
+    op.set_f32_kernel(args.f32_kernel)
 
     def step():
         op.set_coefficients(ALPHA, NU)
@@ -887,6 +889,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--inner-rtol", type=float, default=1e-5)
+    ap.add_argument("--f32-kernel", type=int, default=-1,
+                    help="FP32 element kernel of the mixed-precision measurement: -1 autotuned (default), "
+                         "0 collocated, 1 direct staged, 2 direct, 3 tensor-core BF16, 4 tensor-core BF16x3")
     ap.add_argument("--cpu-elems", type=int, default=14)
     ap.add_argument("--ref-elems", type=int, default=6)
     ap.add_argument("--ref-iterations", type=int, default=100)

@@ -269,12 +269,21 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
  *                         copies at block start; stored factors only
  *   HX_F32_DIRECT         the same with the factors read from global memory (or recomputed
  *                         from the vertices for on-the-fly geometry)
- *   HX_F32_AUTO           (default) the fastest of the candidates for this order, quadrature,
+ *   HX_F32_MMA_BF16       the B/D-direct form with every 1D contraction on the tensor cores
+ *                         (warp-level mma.sync m16n8k16, BF16 operands, FP32 accumulation):
+ *                         operands rounded to BF16 (8 significant bits), so the operator is
+ *                         accurate to ~1e-2 relative, not to FP32; stored factors only
+ *   HX_F32_MMA_BF16X3     the same with each operand split into a high and a low BF16 part and
+ *                         three products accumulated (hi*hi + hi*lo + lo*hi, ~16 significant
+ *                         bits, ~1e-4 relative); stored factors only
+ *   HX_F32_AUTO           (default) the fastest of the FP32-accurate candidates
+ *                         (HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED, HX_F32_DIRECT) for this order,
+ *                         quadrature,
  *                         geometry mode and size class (log2 of the element count), timed once
  *                         per process by the operator's first FP32 set-up (one warm-up and three
  *                         timed launches of each candidate, CUDA events) and cached
  * hx_op_set_f32_kernel selects one (HX_ERR_ARG for an unknown kind, HX_ERR_UNSUPPORTED for
- * HX_F32_DIRECT_STAGED with on-the-fly geometry); it takes effect at the next FP32 set-up.
+ * a stored-factor kind with on-the-fly geometry); it takes effect at the next FP32 set-up.
  * hx_op_f32_kernel reports the kernel in use (*kind = -1 before the first FP32 set-up) and,
  * when ms is not NULL, the autotuner's average time per launch of each candidate in ms
  * (ms[kind], -1 where not timed).  Host-side only.
@@ -283,6 +292,8 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
 #define HX_F32_COLLOCATED 0
 #define HX_F32_DIRECT_STAGED 1
 #define HX_F32_DIRECT 2
+#define HX_F32_MMA_BF16 3
+#define HX_F32_MMA_BF16X3 4
 HX_API hx_status hx_op_set_f32_kernel(hx_op* op, int kind);
 HX_API hx_status hx_op_f32_kernel(const hx_op* op, int* kind, float* ms /* 3 entries or NULL */);
 

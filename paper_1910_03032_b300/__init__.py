@@ -328,6 +328,7 @@ def hx_probe_fma(fp64, iters, stream=None):
 
 
 HX_F32_AUTO, HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED, HX_F32_DIRECT = -1, 0, 1, 2
+HX_F32_MMA_BF16, HX_F32_MMA_BF16X3 = 3, 4
 
 
 def hx_op_set_f32_kernel(op, kind):
@@ -604,4 +605,4 @@ class Operator:
 __all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
                               "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS",
                               "HX_PREC_LOR", "HX_PREC_LOR_MC", "HX_PREC_LOR_MG", "HX_F32_AUTO", "HX_F32_COLLOCATED",
-                              "HX_F32_DIRECT_STAGED", "HX_F32_DIRECT"]
+                              "HX_F32_DIRECT_STAGED", "HX_F32_DIRECT", "HX_F32_MMA_BF16", "HX_F32_MMA_BF16X3"]

@@ -376,10 +376,10 @@ hx_status hx_solve_pcg_mixed(hx_op* op, const double* b, double* x, double rtol,
 
 hx_status hx_op_set_f32_kernel(hx_op* op, int kind) {
   if (!op) return fail(HX_ERR_ARG, "op is NULL");
-  if (kind != HX_F32_AUTO && kind != HX_F32_COLLOCATED && kind != HX_F32_DIRECT_STAGED && kind != HX_F32_DIRECT)
-    return fail(HX_ERR_ARG, "unknown FP32 kernel kind %d", kind);
-  if (kind == HX_F32_DIRECT_STAGED && op->geom != HX_GEOM_STORED)
-    return fail(HX_ERR_UNSUPPORTED, "only stored factors can be staged");
+  if (kind < HX_F32_AUTO || kind > HX_F32_MMA_BF16X3) return fail(HX_ERR_ARG, "unknown FP32 kernel kind %d", kind);
+  if ((kind == HX_F32_DIRECT_STAGED || kind == HX_F32_MMA_BF16 || kind == HX_F32_MMA_BF16X3) &&
+      op->geom != HX_GEOM_STORED)
+    return fail(HX_ERR_UNSUPPORTED, "FP32 kernel kind %d needs stored factors", kind);
   op->f32_request = kind;
   op->f32_kind = -1;  // resolved (or tuned) at the next FP32 set-up
   if (op->graph32) {
@@ -394,7 +394,7 @@ hx_status hx_op_f32_kernel(const hx_op* op, int* kind, float* ms) {
   if (!op || !kind) return fail(HX_ERR_ARG, "NULL argument");
   *kind = op->f32_kind;
   if (ms)
-    for (int i = 0; i < 3; ++i) ms[i] = op->f32_ms[i];
+    for (int i = 0; i < 3; ++i) ms[i] = op->f32_ms[i];  // the autotuner's candidates (kinds 0..2)
   return HX_OK;
 }
 

@@ -941,12 +941,17 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
   }                                                                                                        \
   cudaError_t hx_launch_apply32_p##P(const HxTablesF& T, const HxApplyArgsF& A, int geom, int kind,      \
                                      cudaStream_t s) {                                                     \
+    if (kind >= 3 && geom != HX_KGEOM_STORED) return cudaErrorInvalidValue;                                \
     if (T.q == P + 1)                                                                                      \
-      return kind == 0 ? hx::launch_apply_q<float, P, P + 1>(T, A, geom, s)                                \
-                       : hx::launch_apply32_q<P, P + 1>(T, A, geom, kind == 1, s);                         \
+      return kind == 0   ? hx::launch_apply_q<float, P, P + 1>(T, A, geom, s)                              \
+             : kind == 3 ? hx::launch_apply32_mma<P, P + 1, 1>(T, A, s)                                    \
+             : kind == 4 ? hx::launch_apply32_mma<P, P + 1, 3>(T, A, s)                                    \
+                         : hx::launch_apply32_q<P, P + 1>(T, A, geom, kind == 1, s);                       \
     if (T.q == P + 2)                                                                                      \
-      return kind == 0 ? hx::launch_apply_q<float, P, P + 2>(T, A, geom, s)                                \
-                       : hx::launch_apply32_q<P, P + 2>(T, A, geom, kind == 1, s);                         \
+      return kind == 0   ? hx::launch_apply_q<float, P, P + 2>(T, A, geom, s)                              \
+             : kind == 3 ? hx::launch_apply32_mma<P, P + 2, 1>(T, A, s)                                    \
+             : kind == 4 ? hx::launch_apply32_mma<P, P + 2, 3>(T, A, s)                                    \
+                         : hx::launch_apply32_q<P, P + 2>(T, A, geom, kind == 1, s);                       \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_diag_p##P(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {     \

@@ -41,6 +41,41 @@ def test_fp32_apply_matches_oracle(hx, p, shape, geom, kind):
         assert ms[used] == min(m for m in ms if m >= 0)
 
 
+@pytest.mark.parametrize("p,shape", [(1, (5, 5, 3)), (2, (5, 5, 3)), (3, (5, 5, 3)), (4, (5, 3, 3)), (5, (4, 3, 2)),
+                                     (6, (3, 3, 1)), (7, (2, 2, 2)), (8, (3, 3, 1))])
+@pytest.mark.parametrize("kind,tol", [(3, 3e-2), (4, 1e-4)])
+def test_fp32_tensor_core_apply_matches_oracle(hx, p, shape, kind, tol):
+    """The tensor-core kernels: BF16 operands (unit roundoff 2^-9 ~ 2e-3, six contraction stages
+    with both operands rounded: 3e-2) and the hi/lo BF16 split (dropped lo*lo terms ~ 2^-18
+    each, plus the tensor cores' FP32 accumulation: 1e-4)."""
+    from oracle import fem
+    V, EV, om = case(shape, p)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1.7, 0.45)
+    op.set_f32_kernel(kind)
+    x32 = S.random_vector(om.n_dof, 3032).astype(np.float32)
+    y = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
+    ref = fem.Operator(om, 1.7, 0.45).apply(x32.astype(np.float64), constrained=True)
+    err = rel_err(y, ref)
+    assert err <= tol, err
+    assert op.f32_kernel()[0] == kind
+
+
+@pytest.mark.parametrize("p", [2, 4, 8])
+def test_mixed_solve_tensor_core_bf16x3(hx, p):
+    """The mixed solve with the hi/lo BF16 tensor-core operator still reaches the FP64 1e-10."""
+    from oracle import fem
+    from oracle.solve import jacobi_pcg
+    shape = (4, 4, 4) if p <= 4 else (3, 3, 3)
+    V, EV, om = case(shape, p)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 1.0, 1.0)
+    op.set_f32_kernel(hx.HX_F32_MMA_BF16X3)
+    b = to_dev(S.random_vector(om.n_dof, 5))
+    x, info = op.solve_mixed(b, rtol=1e-10)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    uo, _, _, conv = jacobi_pcg(fem.Operator(om, 1.0, 1.0), b.cpu().numpy(), 1e-12)
+    assert conv and rel_err(x.cpu().numpy(), uo) <= 1e-8
+
+
 def test_fp32_kernel_selection_errors(hx):
     V = S.structured_vertices(2, 2, 2, 0.1, 5)
     mesh = hx.Mesh.structured(2, 2, 2, 3, 5, V)
@@ -48,6 +83,10 @@ def test_fp32_kernel_selection_errors(hx):
     with pytest.raises(hx.HxError) as ei:
         op.set_f32_kernel(hx.HX_F32_DIRECT_STAGED)
     assert ei.value.status == hx.HX_ERR_UNSUPPORTED
+    for kind in (hx.HX_F32_MMA_BF16, hx.HX_F32_MMA_BF16X3):
+        with pytest.raises(hx.HxError) as ei:
+            op.set_f32_kernel(kind)
+        assert ei.value.status == hx.HX_ERR_UNSUPPORTED
     with pytest.raises(hx.HxError) as ei:
         op.set_f32_kernel(7)
     assert ei.value.status == hx.HX_ERR_ARG
