@@ -195,6 +195,27 @@ __device__ __forceinline__ Real point_factors(const Real (&j0)[3], const Real (&
   return det;
 }
 
+// 1 / d in FP64 by Newton-Raphson iteration y <- y (2 - d y) (quadratic convergence) from the
+// hardware's approximate reciprocal: three steps take any start within 2^-10 relative below
+// FP64 rounding, for a fraction of the cost of a correctly rounded division.
+__device__ __forceinline__ double rcp_newton(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+  }
+  return y;
+}
+
+template <typename Real>
+__device__ __forceinline__ void cross3(const Real (&a)[3], const Real (&b)[3], Real (&c)[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
 // ---------------------------------------------------------------------------
 // bulk asynchronous copies (TMA engine) into shared memory, completed on an mbarrier
 // ---------------------------------------------------------------------------
@@ -393,8 +414,10 @@ __global__ void __launch_bounds__(NT, MINB)
   // coefficients are read once per column and each point costs two 3-vector updates
   // (+13-16% on the FP64 on-the-fly apply despite a few spilled registers)
   constexpr bool COLJ = true;
+  // FP64 with on-the-fly geometry: the pointwise stage works with the cofactor rows directly
+  constexpr bool COF = GEOM == HX_KGEOM_ONTHEFLY && sizeof(Real) == 8;
   Real P0[3], R0[3], P1[3], R1[3], J2[3];
-  if (COLJ && GEOM == HX_KGEOM_ONTHEFLY && owner) {
+  if (COLJ && !COF && GEOM == HX_KGEOM_ONTHEFLY && owner) {
     const Real* a = geo + cel * 24;
     const Real x1 = T.xq[c % Q], x2 = T.xq[c / Q];
 #pragma unroll
@@ -452,8 +475,53 @@ __global__ void __launch_bounds__(NT, MINB)
     Real* Xc = Dc + RG;
     Real* Yc = Xc + RG;
     Real w3[Q];
+    if (COF) {
+      // Rows of J^-1 are the cofactor rows c0 = j1 x j2, c1 = j2 x j0, c2 = j0 x j1 over detJ,
+      // so G grad u = (nu w / detJ) sum_i c_i (c_i . t) with t = sum_k c_k du/dxi_k: no 3 x 3
+      // factor matrix is formed.  Along the column j2 is constant and j0, j1 are affine in
+      // z = xi_3 (coefficients once per column); detJ = j2 . c2, and 1/detJ by Newton-Raphson.
+      const Real* ga = geo + cel * 24;
+      const int iq = c % Q, jq = c / Q;
+      const Real x1 = T.xq[iq], x2 = T.xq[jq];
 #pragma unroll
-    for (int kq = 0; kq < Q; ++kq) {
+      for (int d = 0; d < 3; ++d) {
+        const Real* ad = ga + d * 8;
+        P0[d] = ad[1] + ad[4] * x2;
+        R0[d] = ad[5] + ad[7] * x2;
+        P1[d] = ad[2] + ad[4] * x1;
+        R1[d] = ad[6] + ad[7] * x1;
+        J2[d] = ad[3] + ad[5] * x1 + (ad[6] + ad[7] * x1) * x2;
+      }
+      const Real w12 = T.wq[iq] * T.wq[jq];
+#pragma unroll
+      for (int kq = 0; kq < Q; ++kq) {
+        const Real z = T.xq[kq];
+        Real j0[3], j1[3], c0[3], c1[3], c2[3], tt[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          j0[d] = P0[d] + z * R0[d];
+          j1[d] = P1[d] + z * R1[d];
+        }
+        cross3(j1, J2, c0);
+        cross3(J2, j0, c1);
+        cross3(j0, j1, c2);
+        const Real det = J2[0] * c2[0] + J2[1] * c2[1] + J2[2] * c2[2];
+        const Real w = w12 * T.wq[kq];
+        Real nu = nu_r;
+        if (NUF) nu = (e < A.E) ? Real(__ldg(A.nu_q + e * Q3 + kq * Q2 + c)) : Real(0);
+        const Real sc = (e < A.E) ? nu * w * rcp_newton(det) : Real(0);
+        const Real ms = (e < A.E) ? alpha_r * w * det : Real(0);
+        const Real u1 = Xc[kq * SZ], u2 = Yc[kq * SZ], u3 = du[kq];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) tt[d] = c0[d] * u1 + c1[d] * u2 + c2[d] * u3;
+        Dc[kq * SZ] = ms * Dc[kq * SZ];
+        Xc[kq * SZ] = sc * (c0[0] * tt[0] + c0[1] * tt[1] + c0[2] * tt[2]);
+        Yc[kq * SZ] = sc * (c1[0] * tt[0] + c1[1] * tt[1] + c1[2] * tt[2]);
+        w3[kq] = sc * (c2[0] * tt[0] + c2[1] * tt[1] + c2[2] * tt[2]);
+      }
+    }
+#pragma unroll
+    for (int kq = 0; kq < Q && !COF; ++kq) {
       const int pt = kq * Q2 + c;
       Real f[7];
       if (STAGE) {
