@@ -556,7 +556,7 @@ def run_batch(hx, torch, args):
         t_seq, infos_seq = timed(seq, args.batch_reps)
         # lanes: how many chains of solves the graph runs side by side; the best is reported
         by_lanes = {}
-        for lanes in ([0, 8, 2] if len(ops) > 8 else [0, 1]):
+        for lanes in ([0, 8, 2, hx.HX_BATCH_FUSED] if len(ops) > 8 else [0, 1, hx.HX_BATCH_FUSED]):
             batch = hx.Batch(ops, bs, xs, rtol=RTOL, max_it=20000, lanes=lanes)
             batch.solve()
             by_lanes[lanes] = timed(batch.solve, args.batch_reps)
@@ -581,8 +581,10 @@ def run_batch(hx, torch, args):
                      "iterations_total": sum(i["iterations"] for i in infos),
                      "converged": all(i["status"] == 0 for i in infos),
                      "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
-                     "batched_s": t_bat, "sequential_s": t_seq, "speedup": t_seq / t_bat, "lanes": best,
-                     "batched_s_by_lanes": {str(k): v[0] for k, v in by_lanes.items()},
+                     "batched_s": t_bat, "sequential_s": t_seq, "speedup": t_seq / t_bat,
+                     "lanes": "fused" if best == hx.HX_BATCH_FUSED else best,
+                     "batched_s_by_lanes": {("fused" if k == hx.HX_BATCH_FUSED else str(k)): v[0]
+                                            for k, v in by_lanes.items()},
                      "batched_gdofs": dof_applies / t_bat / 1e9, "timing": f"{args.batch_reps} reps after 1 warm-up"}
         del ops, bs, xs
         torch.cuda.empty_cache()

@@ -436,16 +436,32 @@ HX_API hx_status hx_op_gradient(hx_op* op, const double* u, const double* lam, d
  *             after instance i - lanes has finished, so at most `lanes` solves run
  *             side by side (0 or >= n: all instances concurrently).  Small
  *             instances gain from overlap; the many short kernels of multigrid
- *             V-cycles run better in few lanes.  lanes < 0: autotuned — the first
- *             hx_batch_solve times one solve of the whole batch for each of 1, 2,
- *             4, 8, ... and n lanes (CUDA events on the batch's stream), keeps the
- *             fastest graph and then solves as usual; the lane count never changes
- *             the results, only their overlap.  hx_batch_lanes reports the choice.
+ *             V-cycles run better in few lanes.
+ *             lanes = HX_BATCH_FUSED: lock-step mode.  The instances with a diagonal
+ *             preconditioner (Jacobi, collocated mass) iterate together in one
+ *             device-side while loop whose body holds, per CG iteration, one
+ *             element-kernel launch per distinct (order, quadrature, geometry mode)
+ *             walking a work list of (instance, element block) tiles, and one launch
+ *             each for the assembly with (p, Ap), the update and the direction
+ *             walking (instance, vector chunk) tiles, every reduction finished per
+ *             instance; finished instances drop out of the passes, and the loop ends
+ *             when all are done.  Small instances then share the device instead of
+ *             each paying its own launches.  Instances with an LOR preconditioner
+ *             run as branches beside the loop.
+ *             lanes = HX_BATCH_AUTO (or any other negative value): autotuned — the
+ *             first hx_batch_solve times one solve of the whole batch for each of 1,
+ *             2, 4, 8, ... and n lanes and the lock-step mode (CUDA events on the
+ *             batch's stream), keeps the fastest graph and then solves as usual;
+ *             neither lanes nor mode changes the results (each instance's arithmetic,
+ *             reductions included, is that of its solo hx_solve_pcg, bit for bit),
+ *             only their overlap.  hx_batch_lanes reports the choice.
  * The graph captures the operators' coefficients and preconditioners: after
  * hx_op_set_coefficients on an HX_GEOM_ONTHEFLY operator, or hx_op_set_preconditioner,
  * create the batch again.  Synchronous create.
  */
 typedef struct hx_batch hx_batch;
+#define HX_BATCH_AUTO (-1)
+#define HX_BATCH_FUSED (-2)
 HX_API hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, double* const* x, double rtol,
                                  int max_it, int lanes, hx_batch** out);
 
@@ -454,8 +470,9 @@ HX_API hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* 
  * Synchronous. */
 HX_API hx_status hx_batch_solve(hx_batch* batch, void* stream, hx_solve_info* infos);
 
-/* The lane count the next hx_batch_solve runs with (after autotuning, the chosen one; before
- * the first solve of an autotuned batch, n).  0 for a NULL batch. */
+/* The lane count the next hx_batch_solve runs with, or HX_BATCH_FUSED for the lock-step mode
+ * (after autotuning, the chosen one; before the first solve of an autotuned batch, n).  0 for a
+ * NULL batch. */
 HX_API int hx_batch_lanes(const hx_batch* batch);
 
 /* Frees the batch (not its operators or vectors); NULL is ignored. */

@@ -413,8 +413,12 @@ def hx_batch_destroy(batch):
     _lib.hx_batch_destroy(batch)
 
 
+HX_BATCH_AUTO, HX_BATCH_FUSED = -1, -2
+
+
 class Batch:
-    """Owning handle of a batch; keeps its operators and vectors alive."""
+    """Owning handle of a batch; keeps its operators and vectors alive.  lanes: chains of solves
+    (0: all concurrent), HX_BATCH_FUSED (lock-step iterations), HX_BATCH_AUTO (timed choice)."""
 
     def __init__(self, ops, b, x, rtol=1e-10, max_it=10000, lanes=0):
         self.ops, self.b, self.x = list(ops), list(b), list(x)
@@ -425,7 +429,7 @@ class Batch:
 
     @property
     def lanes(self):
-        """Lanes of the next solve (after autotuning: the chosen count)."""
+        """Lanes of the next solve, or HX_BATCH_FUSED (after autotuning: the chosen one)."""
         return hx_batch_lanes(self.handle)
 
     def __del__(self):
@@ -605,4 +609,5 @@ class Operator:
 __all__ = list(SIGNATURES) + ["Mesh", "Operator", "Batch", "HxError", "SolveInfo", "LIB_PATH", "HX_GEOM_STORED",
                               "HX_GEOM_ONTHEFLY", "HX_PREC_JACOBI", "HX_PREC_COLLOCATED_MASS",
                               "HX_PREC_LOR", "HX_PREC_LOR_MC", "HX_PREC_LOR_MG", "HX_F32_AUTO", "HX_F32_COLLOCATED",
-                              "HX_F32_DIRECT_STAGED", "HX_F32_DIRECT", "HX_F32_MMA_BF16", "HX_F32_MMA_BF16X3"]
+                              "HX_F32_DIRECT_STAGED", "HX_F32_DIRECT", "HX_F32_MMA_BF16", "HX_F32_MMA_BF16X3",
+                              "HX_BATCH_AUTO", "HX_BATCH_FUSED"]

@@ -26,75 +26,225 @@ hx_status add_captured_child(cudaGraph_t G, cudaStream_t s, const cudaGraphNode_
   return HX_OK;
 }
 
+// The while-loop node of G (after `dep`) whose body is captured from body(handle).
+hx_status add_while_node(cudaGraph_t G, cudaStream_t cs, cudaGraphNode_t dep,
+                         const std::function<cudaError_t(unsigned long long)>& body, cudaGraphNode_t* loop) {
+  cudaGraphConditionalHandle h = 0;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  np->type = cudaGraphNodeTypeConditional;
+  np->conditional.handle = h;
+  np->conditional.type = cudaGraphCondTypeWhile;
+  np->conditional.size = 1;
+  if (e == cudaSuccess) e = cudaGraphAddNode(loop, G, &dep, nullptr, 1, np);
+  if (e == cudaSuccess) {
+    cudaGraph_t bodyg = np->conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t eb = body((unsigned long long)h);
+      e = cudaStreamEndCapture(cs, &bodyg);
+      if (eb != cudaSuccess) e = eb;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch while node");
+  return HX_OK;
+}
+
+// Instance i's solve before its iterations: r = P b (mean removed for pure Neumann), z, p.
+cudaError_t instance_init(hx_batch* B, int i, double rtol, int max_it, cudaStream_t cs) {
+  hx_op* op = B->ops[i];
+  const HxCgBuffers buf = cg_buffers(op);
+  const double* bi = B->b[i];
+  cudaError_t e = cudaSuccess;
+  if (op->singular) e = hx_launch_cg_mean(buf, bi, cs);
+  if (e == cudaSuccess) e = hx_launch_cg_init(buf, bi, (const double*)nullptr, rtol, max_it, cs);
+  if (e == cudaSuccess) e = precondition_start(op, cs);
+  if (e == cudaSuccess) e = hx_launch_cg_start(buf, cs);
+  if (e == cudaSuccess && op->singular) e = hx_launch_cg_direction(buf, cs);
+  return e;
+}
+
+// Instance i's solve after its iterations: mean-zero closure (pure Neumann), true residual,
+// solution copy.
+cudaError_t instance_tail(hx_batch* B, int i, cudaStream_t cs) {
+  hx_op* op = B->ops[i];
+  const hx_mesh* m = op->mesh;
+  cudaError_t e = cudaSuccess;
+  if (op->singular) {
+    e = hx_launch_sum(m->n_dof, op->m1, op->partial, op->counters, op->vol, cs);
+    if (e == cudaSuccess) e = hx_launch_dot(m->n_dof, op->m1, op->x, op->partial, op->counters, op->vol + 1, cs);
+    if (e == cudaSuccess) e = hx_launch_shift(m->n_dof, op->x, op->vol + 1, op->vol, cs);
+  }
+  if (e == cudaSuccess) e = element_apply(op, op->x, 1, nullptr, cs);
+  if (e == cudaSuccess)
+    e = hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, cs);
+  if (e == cudaSuccess)
+    e = hx_launch_resnorm(m->n_dof, B->b[i], op->Ap, m->dir, op->partial, op->counters, op->scalars, cs,
+                          op->singular ? &op->st->shift : nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->x[i], op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, cs);
+  return e;
+}
+
+// Instance i's whole solve as a branch of G after `dep` (may be null); its tail node out.
+hx_status add_instance_branch(cudaGraph_t G, hx_batch* B, int i, double rtol, int max_it, const cudaGraphNode_t* dep,
+                              cudaGraphNode_t* tail) {
+  cudaStream_t cs = B->stream;
+  hx_op* op = B->ops[i];
+  cudaGraphNode_t init = nullptr, loop = nullptr;
+  hx_status s = add_captured_child(G, cs, dep, dep ? 1 : 0, [&]() { return instance_init(B, i, rtol, max_it, cs); },
+                                   &init);
+  if (s == HX_OK)
+    s = add_while_node(G, cs, init, [&](unsigned long long h) { return cg_iteration(op, cs, h); }, &loop);
+  if (s == HX_OK) s = add_captured_child(G, cs, &loop, 1, [&]() { return instance_tail(B, i, cs); }, tail);
+  return s;
+}
+
+// Lock-step mode: the instances with a diagonal preconditioner iterate together, one loop body
+// per CG iteration for all of them, each pass one launch over a work list (element kernel: one
+// launch per order, quadrature and geometry mode; vector passes: one launch for all).
+bool fusable(const hx_op* op) { return op->prec == HX_PREC_JACOBI || op->prec == HX_PREC_COLLOCATED_MASS; }
+
+hx_status build_fused_tables(hx_batch* B, double rtol, int max_it) {
+  (void)rtol;
+  (void)max_it;
+  hx_batch::Fused& F = B->fused;
+  if (F.built) return HX_OK;
+  std::vector<int> ids;
+  for (int i = 0; i < B->n; ++i)
+    if (fusable(B->ops[i])) ids.push_back(i);
+  F.members = ids;
+  const int nf = (int)ids.size();
+  if (nf == 0) {
+    F.built = true;
+    return HX_OK;
+  }
+  // vector passes: each instance gets the blocks its solo passes use (the reductions finish per
+  // instance over its own blocks, in the same order as in a solo solve)
+  std::vector<HxCgBuffers> bufs(nf);
+  std::vector<HxCgState*> states(nf);
+  std::vector<int> vop, vfirst(nf), vcount(nf);
+  for (int k = 0; k < nf; ++k) {
+    const hx_op* op = B->ops[ids[k]];
+    bufs[k] = cg_buffers(op);
+    bufs[k].cond = 0ull;
+    states[k] = op->st;
+    const long long nb = hx_red_blocks(op->mesh->n_dof);  // the blocks of its solo passes
+    vfirst[k] = (int)vop.size();
+    vcount[k] = (int)nb;
+    for (long long b = 0; b < nb; ++b) vop.push_back(k);
+  }
+  // element kernel: one group per (p, q, geometry mode, nu field)
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+  for (int k = 0; k < nf; ++k) {
+    const hx_op* op = B->ops[ids[k]];
+    groups[std::make_tuple(op->mesh->p, op->mesh->q, op->geom, op->use_field ? 1 : 0)].push_back(k);
+  }
+  static const hx_block_elems_fn nel_fn[] = {nullptr, hx_apply_block_elems_p1, hx_apply_block_elems_p2,
+                                             hx_apply_block_elems_p3, hx_apply_block_elems_p4,
+                                             hx_apply_block_elems_p5, hx_apply_block_elems_p6,
+                                             hx_apply_block_elems_p7, hx_apply_block_elems_p8};
+  std::vector<HxApplyArgs> args;
+  std::vector<int> eop, efirst;
+  F.groups.clear();
+  for (auto& kv : groups) {
+    hx_batch::Group g;
+    g.p = std::get<0>(kv.first);
+    g.geom = std::get<2>(kv.first);
+    g.nuf = std::get<3>(kv.first);
+    g.T = B->ops[ids[kv.second[0]]]->mesh->T;
+    g.args_off = (int)args.size();
+    g.blk_off = (long long)eop.size();
+    const int ne = nel_fn[g.p](std::get<1>(kv.first), g.geom);
+    for (size_t j = 0; j < kv.second.size(); ++j) {
+      const hx_op* op = B->ops[ids[kv.second[j]]];
+      args.push_back(apply_args(op, op->p, 1, &op->st->done));
+      efirst.push_back((int)(eop.size() - g.blk_off));
+      const long long nb = (op->mesh->E + ne - 1) / ne;
+      for (long long b = 0; b < nb; ++b) eop.push_back((int)j);
+    }
+    g.blocks = (long long)eop.size() - g.blk_off;
+    F.groups.push_back(g);
+  }
+  hx_status s;
+  if ((s = dalloc(&F.bufs, bufs.size(), "batch buffers")) || (s = dalloc(&F.states, states.size(), "batch states")) ||
+      (s = dalloc(&F.vop, vop.size(), "batch pass table")) || (s = dalloc(&F.vfirst, vfirst.size(), "batch pass table")) ||
+      (s = dalloc(&F.vcount, vcount.size(), "batch pass table")) || (s = dalloc(&F.args, args.size(), "batch arguments")) ||
+      (s = dalloc(&F.eop, eop.size(), "batch block table")) || (s = dalloc(&F.efirst, efirst.size(), "batch block table")))
+    return s;
+  F.vblocks = (long long)vop.size();
+  HX_TRY(cudaMemcpy(F.bufs, bufs.data(), sizeof(HxCgBuffers) * bufs.size(), cudaMemcpyHostToDevice), "batch tables");
+  HX_TRY(cudaMemcpy(F.states, states.data(), sizeof(HxCgState*) * states.size(), cudaMemcpyHostToDevice),
+         "batch tables");
+  HX_TRY(cudaMemcpy(F.vop, vop.data(), sizeof(int) * vop.size(), cudaMemcpyHostToDevice), "batch tables");
+  HX_TRY(cudaMemcpy(F.vfirst, vfirst.data(), sizeof(int) * vfirst.size(), cudaMemcpyHostToDevice), "batch tables");
+  HX_TRY(cudaMemcpy(F.vcount, vcount.data(), sizeof(int) * vcount.size(), cudaMemcpyHostToDevice), "batch tables");
+  HX_TRY(cudaMemcpy(F.args, args.data(), sizeof(HxApplyArgs) * args.size(), cudaMemcpyHostToDevice), "batch tables");
+  HX_TRY(cudaMemcpy(F.eop, eop.data(), sizeof(int) * eop.size(), cudaMemcpyHostToDevice), "batch tables");
+  HX_TRY(cudaMemcpy(F.efirst, efirst.data(), sizeof(int) * efirst.size(), cudaMemcpyHostToDevice), "batch tables");
+  F.built = true;
+  return HX_OK;
+}
+
+// One lock-step CG iteration of the fused instances (h: the enclosing while loop's handle).
+cudaError_t fused_iteration(hx_batch* B, unsigned long long h) {
+  static const hx_apply_multi_launcher t[] = {nullptr, hx_launch_apply_multi_p1, hx_launch_apply_multi_p2,
+                                              hx_launch_apply_multi_p3, hx_launch_apply_multi_p4,
+                                              hx_launch_apply_multi_p5, hx_launch_apply_multi_p6,
+                                              hx_launch_apply_multi_p7, hx_launch_apply_multi_p8};
+  hx_batch::Fused& F = B->fused;
+  cudaStream_t cs = B->stream;
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < F.groups.size() && e == cudaSuccess; ++k) {
+    const hx_batch::Group& g = F.groups[k];
+    e = t[g.p](g.T, F.args + g.args_off, F.eop + g.blk_off, F.efirst + g.args_off, g.blocks, g.geom, g.nuf, cs);
+  }
+  if (e == cudaSuccess) e = hx_launch_cg_pass_multi(HX_PASS_ASSEMBLE_PAP, F.bufs, F.vop, F.vfirst, F.vcount, F.vblocks, cs);
+  if (e == cudaSuccess) e = hx_launch_cg_pass_multi(HX_PASS_UPDATE, F.bufs, F.vop, F.vfirst, F.vcount, F.vblocks, cs);
+  if (e == cudaSuccess) e = hx_launch_cg_pass_multi(HX_PASS_DIRECTION, F.bufs, F.vop, F.vfirst, F.vcount, F.vblocks, cs);
+  if (e == cudaSuccess) e = hx_launch_batch_condition(F.states, (int)F.members.size(), h, cs);
+  return e;
+}
+
 hx_status build_batch_graph(hx_batch* B, double rtol, int max_it, int lanes) {
   cudaGraph_t G = nullptr;
   HX_TRY(cudaGraphCreate(&G, 0), "batch graph");
   hx_status s = HX_OK;
   cudaStream_t cs = B->stream;
-  // instance i runs after instance i - lanes: `lanes` chains of solves run side by side
-  std::vector<cudaGraphNode_t> tails((size_t)B->n, nullptr);
-  for (int i = 0; i < B->n && s == HX_OK; ++i) {
-    hx_op* op = B->ops[i];
-    const hx_mesh* m = op->mesh;
-    const double* bi = B->b[i];
-    double* xi = B->x[i];
-    const HxCgBuffers buf = cg_buffers(op);
-    cudaGraphNode_t init = nullptr, loop = nullptr, tail = nullptr;
-    // 1. initialization: r = P b (mean removed for pure Neumann), z = D^-1 r, p
-    const cudaGraphNode_t* dep = (i >= lanes) ? &tails[(size_t)(i - lanes)] : nullptr;
-    s = add_captured_child(G, cs, dep, dep ? 1 : 0, [&]() {
-      cudaError_t e = cudaSuccess;
-      if (op->singular) e = hx_launch_cg_mean(buf, bi, cs);
-      if (e == cudaSuccess) e = hx_launch_cg_init(buf, bi, (const double*)nullptr, rtol, max_it, cs);
-      if (e == cudaSuccess) e = precondition_start(op, cs);
-      if (e == cudaSuccess) e = hx_launch_cg_start(buf, cs);
-      if (e == cudaSuccess && op->singular) e = hx_launch_cg_direction(buf, cs);
-      return e;
-    }, &init);
-    if (s) break;
-    // 2. the CG iterations as a device-side while loop
-    cudaGraphConditionalHandle h = 0;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
-    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
-    std::memset(raw, 0, sizeof(raw));
-    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
-    np->type = cudaGraphNodeTypeConditional;
-    np->conditional.handle = h;
-    np->conditional.type = cudaGraphCondTypeWhile;
-    np->conditional.size = 1;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&loop, G, &init, nullptr, 1, np);
-    if (e == cudaSuccess) {
-      cudaGraph_t body = np->conditional.phGraph_out[0];
-      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        cudaError_t eb = cg_iteration(op, cs, (unsigned long long)h);
-        e = cudaStreamEndCapture(cs, &body);
-        if (eb != cudaSuccess) e = eb;
-      }
+  if (lanes == HX_BATCH_FUSED) {
+    s = build_fused_tables(B, rtol, max_it);
+    // instances the lock-step loop cannot take (preconditioners applied outside the CG
+    // kernels) are branches of their own, running beside it
+    for (int i = 0; i < B->n && s == HX_OK; ++i) {
+      if (fusable(B->ops[i])) continue;
+      cudaGraphNode_t tail = nullptr;
+      s = add_instance_branch(G, B, i, rtol, max_it, nullptr, &tail);
     }
-    if (e != cudaSuccess) {
-      s = cuda_fail(e, "batch while node");
-      break;
+    const std::vector<int>& mem = B->fused.members;
+    if (s == HX_OK && !mem.empty()) {
+      cudaGraphNode_t init = nullptr, loop = nullptr, tail = nullptr;
+      s = add_captured_child(G, cs, nullptr, 0, [&]() {
+        cudaError_t e = cudaSuccess;
+        for (size_t k = 0; k < mem.size() && e == cudaSuccess; ++k) e = instance_init(B, mem[k], rtol, max_it, cs);
+        return e;
+      }, &init);
+      if (s == HX_OK) s = add_while_node(G, cs, init, [&](unsigned long long h) { return fused_iteration(B, h); }, &loop);
+      if (s == HX_OK)
+        s = add_captured_child(G, cs, &loop, 1, [&]() {
+          cudaError_t e = cudaSuccess;
+          for (size_t k = 0; k < mem.size() && e == cudaSuccess; ++k) e = instance_tail(B, mem[k], cs);
+          return e;
+        }, &tail);
     }
-    // 3. mean-zero closure (pure Neumann), true residual, solution copy
-    s = add_captured_child(G, cs, &loop, 1, [&]() {
-      cudaError_t e3 = cudaSuccess;
-      if (op->singular) {
-        e3 = hx_launch_sum(m->n_dof, op->m1, op->partial, op->counters, op->vol, cs);
-        if (e3 == cudaSuccess) e3 = hx_launch_dot(m->n_dof, op->m1, op->x, op->partial, op->counters, op->vol + 1, cs);
-        if (e3 == cudaSuccess) e3 = hx_launch_shift(m->n_dof, op->x, op->vol + 1, op->vol, cs);
-      }
-      if (e3 == cudaSuccess) e3 = element_apply(op, op->x, 1, nullptr, cs);
-      if (e3 == cudaSuccess)
-        e3 = hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 1, op->x, 0.0, op->Ap, cs);
-      if (e3 == cudaSuccess)
-        e3 = hx_launch_resnorm(m->n_dof, bi, op->Ap, m->dir, op->partial, op->counters, op->scalars, cs,
-                               op->singular ? &op->st->shift : nullptr);
-      if (e3 == cudaSuccess)
-        e3 = cudaMemcpyAsync(xi, op->x, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice, cs);
-      return e3;
-    }, &tail);
-    tails[(size_t)i] = tail;
+  } else {
+    // instance i runs after instance i - lanes: `lanes` chains of solves run side by side
+    std::vector<cudaGraphNode_t> tails((size_t)B->n, nullptr);
+    for (int i = 0; i < B->n && s == HX_OK; ++i) {
+      const cudaGraphNode_t* dep = (i >= lanes) ? &tails[(size_t)(i - lanes)] : nullptr;
+      s = add_instance_branch(G, B, i, rtol, max_it, dep, &tails[(size_t)i]);
+    }
   }
   if (s == HX_OK) {
     cudaError_t e = cudaGraphInstantiate(&B->exec, G, 0);
@@ -111,6 +261,7 @@ hx_status tune_lanes(hx_batch* B) {
   std::vector<int> cand;
   for (int L = 1; L < B->n; L *= 2) cand.push_back(L);
   cand.push_back(B->n);
+  cand.push_back(HX_BATCH_FUSED);
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   hx_status s = HX_OK;
   cudaError_t e = cudaEventCreate(&t0);
@@ -169,8 +320,8 @@ hx_status hx_batch_create(int n, hx_op* const* ops, const double* const* b, doub
   B->x.assign(x, x + n);
   B->rtol = rtol;
   B->max_it = max_it;
-  B->tune = lanes < 0;
-  B->lanes = (lanes <= 0 || lanes > n) ? n : lanes;
+  B->tune = lanes < 0 && lanes != HX_BATCH_FUSED;
+  B->lanes = lanes == HX_BATCH_FUSED ? HX_BATCH_FUSED : (lanes <= 0 || lanes > n) ? n : lanes;
   hx_status s = HX_OK;
   for (int i = 0; i < n && s == HX_OK; ++i) {
     s = ensure_solver(ops[i]);
@@ -243,6 +394,15 @@ void hx_batch_destroy(hx_batch* B) {
   if (B->stream) cudaStreamDestroy(B->stream);
   if (B->st_host) cudaFreeHost(B->st_host);
   if (B->rn2_host) cudaFreeHost(B->rn2_host);
+  hx_batch::Fused& F = B->fused;
+  dfree(F.bufs);
+  dfree(F.states);
+  dfree(F.vop);
+  dfree(F.vfirst);
+  dfree(F.vcount);
+  dfree(F.args);
+  dfree(F.eop);
+  dfree(F.efirst);
   delete B;
 }
 

@@ -151,8 +151,26 @@ struct hx_batch {
   double* rn2_host = nullptr;    // pinned, n true-residual norms
   double rtol = 0.0;             // stopping rule the graph was built with
   int max_it = 0;
-  int lanes = 0;                 // lanes of the current graph
+  int lanes = 0;                 // lanes of the current graph (HX_BATCH_FUSED: lock-step mode)
   bool tune = false;             // pick the lanes by timing at the first solve
+  // lock-step mode: element-kernel launches per (order, quadrature, geometry mode, nu field)
+  struct Group {
+    int p = 0, geom = 0, nuf = 0;
+    HxTables T;
+    int args_off = 0;                // the group's operators in Fused::args (and Fused::efirst)
+    long long blk_off = 0, blocks = 0;  // the group's blocks in Fused::eop
+  };
+  struct Fused {
+    bool built = false;
+    std::vector<int> members;        // batch indices of the lock-step instances
+    std::vector<Group> groups;
+    HxCgBuffers* bufs = nullptr;     // per member: CG buffers (no loop handle)
+    HxCgState** states = nullptr;    // per member: CG state
+    int *vop = nullptr, *vfirst = nullptr, *vcount = nullptr;  // vector passes: block -> member
+    long long vblocks = 0;
+    HxApplyArgs* args = nullptr;     // per member, grouped: element-kernel arguments
+    int *eop = nullptr, *efirst = nullptr;  // element blocks -> member within the group
+  } fused;
 };
 
 namespace hxc {

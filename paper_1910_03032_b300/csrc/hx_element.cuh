@@ -319,9 +319,9 @@ __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Re
 // ---------------------------------------------------------------------------
 // the operator kernel
 // ---------------------------------------------------------------------------
-template <typename Real, int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
-__global__ void __launch_bounds__(NT, MINB)
-    apply_kernel(const __grid_constant__ HxTablesT<Real> T, const HxApplyArgsT<Real> A) {
+// The element work of block `blk` (elements blk NE .. blk NE + NE - 1) of one operator.
+template <typename Real, int P, int Q, int NE, int NT, int GEOM, bool NUF>
+__device__ __forceinline__ void apply_body(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, long long blk) {
   using Lt = Layout<Q, Real>;
   constexpr int N = P + 1, N3 = N * N * N, Q2 = Q * Q, Q3 = Q2 * Q;
   constexpr int SY = Lt::SY, SZ = Lt::SZ, RG = Lt::RG, R3 = Lt::R3;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(NT, MINB)
   Real* geo = smem + NE * R3;  // on-the-fly: NE x 24 map coefficients
   Real* sf = smem + ((NE * R3 + 3) & ~3);  // staged factors (16-byte aligned)
   __shared__ int wait_failed;          // some thread's first wait for the factor copy gave up
-  const long long e0 = (long long)blockIdx.x * NE;
+  const long long e0 = blk * NE;
   const int tid = threadIdx.x;
   // the copy starts at the 16-byte boundary at or below element e0's first factor
   const int foff = STAGE ? (int)(((e0 * A.fstride * (long long)sizeof(Real)) & 15) / (long long)sizeof(Real)) : 0;
@@ -617,6 +617,23 @@ __global__ void __launch_bounds__(NT, MINB)
   // no copy may still be writing this block's shared memory when it exits (every owner's
   // first wait saw the copy complete, so this returns at once)
   if (STAGE && tid == 0) mbar_wait_bounded(&fbar, HX_WAIT_LIMIT_EXIT);
+}
+
+template <typename Real, int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
+__global__ void __launch_bounds__(NT, MINB)
+    apply_kernel(const __grid_constant__ HxTablesT<Real> T, const HxApplyArgsT<Real> A) {
+  apply_body<Real, P, Q, NE, NT, GEOM, NUF>(T, A, blockIdx.x);
+}
+
+// Several operators of one order at once (the lock-step iterations of a batch): block b works
+// on block b - blk_first[o] of operator o = blk_op[b], with that operator's arguments.
+template <typename Real, int P, int Q, int NE, int NT, int MINB, int GEOM, bool NUF>
+__global__ void __launch_bounds__(NT, MINB)
+    apply_multi_kernel(const __grid_constant__ HxTablesT<Real> T, const HxApplyArgsT<Real>* __restrict__ args,
+                       const int* __restrict__ blk_op, const int* __restrict__ blk_first) {
+  const int o = __ldg(blk_op + blockIdx.x);
+  const HxApplyArgsT<Real> A = args[o];
+  apply_body<Real, P, Q, NE, NT, GEOM, NUF>(T, A, (long long)blockIdx.x - __ldg(blk_first + o));
 }
 
 // Load vector: bE = (B x B x B)^T (w detJ f) per element.
@@ -943,6 +960,27 @@ cudaError_t launch_apply_impl(const HxTablesT<Real>& T, const HxApplyArgsT<Real>
   return cudaGetLastError();
 }
 
+template <int P, int Q, int GEOM, bool NUF>
+cudaError_t launch_apply_multi_impl(const HxTables& T, const HxApplyArgs* args, const int* blk_op, const int* blk_first,
+                                    long long blocks, cudaStream_t s) {
+  using C = ApplyConfig<P, Q, double, GEOM>;
+  constexpr int NE = C::NE, NT = C::NT, MINB = C::MINB;
+  const size_t shmem = sizeof(double) * ((size_t)NE * Layout<Q>::R3 + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+  auto k = apply_multi_kernel<double, P, Q, NE, NT, MINB, GEOM, NUF>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+  if (err != cudaSuccess || blocks == 0) return err;
+  k<<<(unsigned)blocks, NT, shmem, s>>>(T, args, blk_op, blk_first);
+  return cudaGetLastError();
+}
+
+template <int P, int Q>
+cudaError_t launch_apply_multi_q(const HxTables& T, const HxApplyArgs* args, const int* blk_op, const int* blk_first,
+                                 long long blocks, int geom, int nuf, cudaStream_t s) {
+  if (geom == HX_KGEOM_STORED) return launch_apply_multi_impl<P, Q, HX_KGEOM_STORED, false>(T, args, blk_op, blk_first, blocks, s);
+  if (nuf) return launch_apply_multi_impl<P, Q, HX_KGEOM_ONTHEFLY, true>(T, args, blk_op, blk_first, blocks, s);
+  return launch_apply_multi_impl<P, Q, HX_KGEOM_ONTHEFLY, false>(T, args, blk_op, blk_first, blocks, s);
+}
+
 template <typename Real, int P, int Q>
 cudaError_t launch_apply_q(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A, int geom, cudaStream_t s) {
   if (geom == HX_KGEOM_STORED) return launch_apply_impl<Real, P, Q, HX_KGEOM_STORED, false>(T, A, s);
@@ -1031,6 +1069,20 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
     if (T.q == P + 1) return hx::launch_diag_q<float, P, P + 1>(T, A, geom, s);                                  \
     if (T.q == P + 2) return hx::launch_diag_q<float, P, P + 2>(T, A, geom, s);                                  \
     return cudaErrorInvalidValue;                                                                          \
+  }                                                                                                        \
+  cudaError_t hx_launch_apply_multi_p##P(const HxTables& T, const HxApplyArgs* args, const int* blk_op,   \
+                                         const int* blk_first, long long blocks, int geom, int nuf,       \
+                                         cudaStream_t s) {                                                 \
+    if (T.q == P + 1) return hx::launch_apply_multi_q<P, P + 1>(T, args, blk_op, blk_first, blocks, geom, nuf, s); \
+    if (T.q == P + 2) return hx::launch_apply_multi_q<P, P + 2>(T, args, blk_op, blk_first, blocks, geom, nuf, s); \
+    return cudaErrorInvalidValue;                                                                          \
+  }                                                                                                        \
+  int hx_apply_block_elems_p##P(int q, int geom) {                                                         \
+    if (q == P + 1)                                                                                        \
+      return geom == HX_KGEOM_STORED ? hx::ApplyConfig<P, P + 1, double, HX_KGEOM_STORED>::NE              \
+                                     : hx::ApplyConfig<P, P + 1, double, HX_KGEOM_ONTHEFLY>::NE;           \
+    return geom == HX_KGEOM_STORED ? hx::ApplyConfig<P, P + 2, double, HX_KGEOM_STORED>::NE                \
+                                   : hx::ApplyConfig<P, P + 2, double, HX_KGEOM_ONTHEFLY>::NE;             \
   }                                                                                                        \
   cudaError_t hx_launch_grad_p##P(const HxTables& T, const HxGradArgs& A, cudaStream_t s) {               \
     if (T.q == P + 1) return hx::launch_grad_q<P, P + 1>(T, A, s);                                        \

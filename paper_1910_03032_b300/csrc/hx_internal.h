@@ -78,6 +78,11 @@ typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cuda
 // kind: HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED or HX_F32_DIRECT (include/hx.h)
 typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, int kind, cudaStream_t);
 typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cudaStream_t);
+// the FP64 element kernel over several operators of one order: blocks -> (operator, block) by table
+typedef cudaError_t (*hx_apply_multi_launcher)(const HxTables&, const HxApplyArgs*, const int* blk_op,
+                                               const int* blk_first, long long blocks, int geom, int nuf,
+                                               cudaStream_t);
+typedef int (*hx_block_elems_fn)(int q, int geom);
 
 #define HX_DECLARE_ORDER(P)                                                                        \
   cudaError_t hx_launch_apply_p##P(const HxTables&, const HxApplyArgs&, int, cudaStream_t);       \
@@ -85,7 +90,10 @@ typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cuda
   cudaError_t hx_launch_diag32_p##P(const HxTablesF&, const HxDiagArgsF&, int, cudaStream_t);     \
   cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);              \
   cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, int, cudaStream_t); \
-  cudaError_t hx_launch_grad_p##P(const HxTables&, const HxGradArgs&, cudaStream_t);
+  cudaError_t hx_launch_grad_p##P(const HxTables&, const HxGradArgs&, cudaStream_t);                     \
+  cudaError_t hx_launch_apply_multi_p##P(const HxTables&, const HxApplyArgs*, const int*, const int*,     \
+                                         long long, int, int, cudaStream_t);                              \
+  int hx_apply_block_elems_p##P(int q, int geom);
 HX_DECLARE_ORDER(1)
 HX_DECLARE_ORDER(2)
 HX_DECLARE_ORDER(3)
@@ -155,6 +163,13 @@ struct HxCgState {
 #define HX_RED_BLOCKS 1184  // 8 x 148 SMs: fixed grid of every reduction kernel
 #define HX_RED_VALUES 4     // partial sums per block at most (partial buffers hold HX_RED_VALUES x HX_RED_BLOCKS)
 #define HX_RED_THREADS 256
+// Blocks of a CG pass over n DoFs: about 4 entries per thread, at least 1, at most
+// HX_RED_BLOCKS.  A solve's reductions sum over the same blocks whether its passes run alone or
+// among the lock-step passes of a batch, so both give bit-identical results.
+inline long long hx_red_blocks(long long n) {
+  const long long b = (n + 4LL * HX_RED_THREADS - 1) / (4LL * HX_RED_THREADS);
+  return b < 1 ? 1 : b > HX_RED_BLOCKS ? HX_RED_BLOCKS : b;
+}
 
 template <typename Real>
 struct HxCgBuffersT {
@@ -300,6 +315,13 @@ cudaError_t hx_launch_dot(long long n, const double* a, const double* c, double*
                           double* out, cudaStream_t s);
 cudaError_t hx_launch_resnorm(long long n, const double* b, const double* Ax, const unsigned char* dir, double* partial,
                               unsigned int* counter, double* out, cudaStream_t s, const double* shift = nullptr);
+// lock-step CG passes over several operators (batches): block b works on share
+// b - blk_first[o] of the blk_count[o] blocks of operator o = blk_op[b] (blk_count[o] <= HX_RED_BLOCKS)
+enum { HX_PASS_ASSEMBLE_PAP = 0, HX_PASS_UPDATE = 1, HX_PASS_DIRECTION = 2 };
+cudaError_t hx_launch_cg_pass_multi(int pass, const HxCgBuffers* bufs, const int* blk_op, const int* blk_first,
+                                    const int* blk_count, long long blocks, cudaStream_t s);
+// sets the while-loop condition `cond`: some operator unfinished and within its cap of bodies
+cudaError_t hx_launch_batch_condition(HxCgState* const* states, int n, unsigned long long cond, cudaStream_t s);
 // null-space (pure Neumann) helpers
 template <typename Real>
 cudaError_t hx_launch_cg_mean(const HxCgBuffersT<Real>& b, const Real* v, cudaStream_t s);

@@ -35,14 +35,16 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Last-block completion: every block writes NV partial sums to partial[v * G + block];
 // the block that finishes last reduces them in a fixed order into out[v].
 // Returns true in the last block (all threads), with out[] written by thread 0.
+// (bid, G): the block's index among the G blocks that reduce together (a launch's whole grid, or
+// one operator's share of a launch over several).
 template <int NV>
-__device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsigned int* counter, double (&out)[NV]) {
+__device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsigned int* counter, double (&out)[NV],
+                                  int bid, int G) {
   __shared__ double red[32];
   __shared__ bool is_last;
-  const int G = gridDim.x;
   for (int k = 0; k < NV; ++k) {
     const double s = block_sum<HX_RED_THREADS>(v[k], red);
-    if (threadIdx.x == 0) partial[k * G + blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[k * G + bid] = s;
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -60,6 +62,11 @@ __device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsign
   }
   if (threadIdx.x == 0) *counter = 0u;
   return true;
+}
+
+template <int NV>
+__device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsigned int* counter, double (&out)[NV]) {
+  return last_block_reduce<NV>(v, partial, counter, out, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -237,6 +244,9 @@ __device__ __forceinline__ Real gather_sum_grid(long long g, const HxGridAsm& G,
 
 #define HX_GRID_STRIDE(g, n) \
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (n); g += (long long)gridDim.x * blockDim.x)
+// the same over a virtual grid of nb blocks, this one being block bid
+#define HX_VGRID_STRIDE(g, n, bid, nb) \
+  for (long long g = (bid) * (long long)blockDim.x + threadIdx.x; g < (n); g += (long long)(nb) * blockDim.x)
 
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const HxGridAsm ga, const int* __restrict__ off,
@@ -351,17 +361,17 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_mean_kernel(HxCgBuffersT<Re
 
 // Ap = assemble(yE) with Dirichlet rows Ap = p; pAp = (p, Ap); alpha = rz / pAp.
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuffersT<Real> B) {
+__device__ __forceinline__ void cg_assemble_pap_body(const HxCgBuffersT<Real>& B, int bid, int nb) {
   if (*(volatile int*)&B.st->done) return;
   double acc[1] = {0.0};
-  HX_GRID_STRIDE(g, B.n) {
+  HX_VGRID_STRIDE(g, B.n, bid, nb) {
     const Real pg = B.p[g];
     const Real ap = B.dir[g] ? pg : (B.ga.p ? gather_sum_grid(g, B.ga, B.yE) : gather_sum(g, B.off, B.idx, B.yE));
     B.Ap[g] = ap;
     acc[0] += (double)pg * (double)ap;
   }
   double out[1];
-  if (last_block_reduce<1>(acc, B.partial, &B.st->count[2], out) && threadIdx.x == 0) {
+  if (last_block_reduce<1>(acc, B.partial, &B.st->count[2], out, bid, nb) && threadIdx.x == 0) {
     HxCgState* s = B.st;
     if (!(out[0] > 0.0) || !isfinite(out[0])) {
       s->status = -6;  // HX_ERR_BREAKDOWN
@@ -372,14 +382,19 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuf
   }
 }
 
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuffersT<Real> B) {
+  cg_assemble_pap_body(B, blockIdx.x, gridDim.x);
+}
+
 // x += alpha p, r -= alpha Ap, z = D^-1 r; rr = (r, r), rz' = (r, z); convergence test.
 // Null-space mode: rz' = (r, z - mean z) and the mean is kept for the direction pass.
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<Real> B) {
+__device__ __forceinline__ void cg_update_body(const HxCgBuffersT<Real>& B, int bid, int nb) {
   if (*(volatile int*)&B.st->done) return;
   const Real a = Real(B.st->alpha);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  HX_GRID_STRIDE(g, B.n) {
+  HX_VGRID_STRIDE(g, B.n, bid, nb) {
     const Real pg = B.p[g];
     B.x[g] += a * pg;
     const Real r = B.r[g] - a * B.Ap[g];
@@ -393,7 +408,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<
     }
   }
   double out[4];
-  if (last_block_reduce<4>(acc, B.partial, &B.st->count[3], out) && threadIdx.x == 0) {
+  if (last_block_reduce<4>(acc, B.partial, &B.st->count[3], out, bid, nb) && threadIdx.x == 0) {
     HxCgState* s = B.st;
     s->iter += 1;
     s->rr = out[0];
@@ -415,6 +430,11 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<
       s->rz = rz;
     }
   }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<Real> B) {
+  cg_update_body(B, blockIdx.x, gridDim.x);
 }
 
 // Preconditioner given as a vector z = M^-1 r (computed between the update and the direction
@@ -447,7 +467,22 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_rz_kernel(HxCgBuffersT<Real
   }
 }
 
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
 // p = D^-1 r + beta p.
+template <typename Real>
+__device__ __forceinline__ void cg_direction_body(const HxCgBuffersT<Real>& B, int bid, int nb) {
+  if (*(volatile int*)&B.st->done) return;
+  const Real beta = Real(B.st->beta), zm = Real(B.st->zmean);
+  // every rounding spelled out (a product rounded on its own, then one fused multiply-add), so
+  // that the solo and the lock-step kernels, which both inline this, round alike
+  HX_VGRID_STRIDE(g, B.n, bid, nb) {
+    const Real z = B.z ? B.z[g] : mul_rn(B.dinv[g], B.r[g]);
+    B.p[g] = fma(beta, B.p[g], z - zm);
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffersT<Real> B) {
   if (B.cond != 0ull && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -458,9 +493,60 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffer
     const bool stop = *(volatile int*)&s->done || s->loops > s->max_it + 1;
     cudaGraphSetConditional((cudaGraphConditionalHandle)B.cond, stop ? 0u : 1u);
   }
-  if (*(volatile int*)&B.st->done) return;
-  const Real beta = Real(B.st->beta), zm = Real(B.st->zmean);
-  HX_GRID_STRIDE(g, B.n) { B.p[g] = ((B.z ? B.z[g] : B.dinv[g] * B.r[g]) - zm) + beta * B.p[g]; }
+  cg_direction_body(B, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// lock-step CG iterations of several operators (a batch): one launch per pass over all of them.
+// Block b works on share b - blk_first[o] of the blk_count[o] blocks given to operator
+// o = blk_op[b], with that operator's buffers (the reductions finish per operator).
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_multi_kernel(const HxCgBuffersT<Real>* bufs,
+                                                                                const int* __restrict__ blk_op,
+                                                                                const int* __restrict__ blk_first,
+                                                                                const int* __restrict__ blk_count) {
+  const int o = __ldg(blk_op + blockIdx.x);
+  const HxCgBuffersT<Real> B = bufs[o];
+  cg_assemble_pap_body(B, blockIdx.x - __ldg(blk_first + o), __ldg(blk_count + o));
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_multi_kernel(const HxCgBuffersT<Real>* bufs,
+                                                                          const int* __restrict__ blk_op,
+                                                                          const int* __restrict__ blk_first,
+                                                                          const int* __restrict__ blk_count) {
+  const int o = __ldg(blk_op + blockIdx.x);
+  const HxCgBuffersT<Real> B = bufs[o];
+  cg_update_body(B, blockIdx.x - __ldg(blk_first + o), __ldg(blk_count + o));
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_multi_kernel(const HxCgBuffersT<Real>* bufs,
+                                                                             const int* __restrict__ blk_op,
+                                                                             const int* __restrict__ blk_first,
+                                                                             const int* __restrict__ blk_count) {
+  const int o = __ldg(blk_op + blockIdx.x);
+  const HxCgBuffersT<Real> B = bufs[o];
+  cg_direction_body(B, blockIdx.x - __ldg(blk_first + o), __ldg(blk_count + o));
+}
+
+// Last kernel of the lock-step while-loop body: every unfinished operator counts one more body;
+// the loop continues while one of them runs and has not used up its cap of max_it + 1 bodies.
+__global__ void __launch_bounds__(HX_RED_THREADS) batch_condition_kernel(HxCgState* const* states, int n,
+                                                                          unsigned long long cond) {
+  __shared__ int live;
+  if (threadIdx.x == 0) live = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    HxCgState* s = states[i];
+    if (!*(volatile int*)&s->done) {
+      s->loops += 1;
+      if (s->loops <= s->max_it + 1) atomicOr(&live, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, live ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,42 +729,42 @@ cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned
 template <typename Real>
 cudaError_t hx_launch_cg_init(const HxCgBuffersT<Real>& b, const Real* bvec, const Real* x0, double rtol, int max_it,
                               cudaStream_t s) {
-  cg_init_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b, bvec, x0, rtol, max_it);
+  cg_init_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b, bvec, x0, rtol, max_it);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_residual(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_residual_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  cg_residual_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_start(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_start_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  cg_start_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_assemble_pap_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  cg_assemble_pap_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_update(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_update_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  cg_update_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_rz(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_rz_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  cg_rz_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_direction(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_direction_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b);
+  cg_direction_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t hx_launch_cg_mean(const HxCgBuffersT<Real>& b, const Real* v, cudaStream_t s) {
-  cg_mean_kernel<Real><<<HX_RED_BLOCKS, HX_RED_THREADS, 0, s>>>(b, v);
+  cg_mean_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b, v);
   return cudaGetLastError();
 }
 cudaError_t hx_launch_sum(long long n, const double* v, double* partial, unsigned int* counter, double* out,
@@ -701,6 +787,23 @@ cudaError_t hx_launch_shift(long long n, double* x, const double* num, const dou
   template cudaError_t hx_launch_cg_mean<R>(const HxCgBuffersT<R>&, const R*, cudaStream_t);
 HX_CG_INSTANTIATE(double)
 HX_CG_INSTANTIATE(float)
+
+cudaError_t hx_launch_cg_pass_multi(int pass, const HxCgBuffers* bufs, const int* blk_op, const int* blk_first,
+                                    const int* blk_count, long long blocks, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (pass == HX_PASS_ASSEMBLE_PAP)
+    cg_assemble_pap_multi_kernel<double><<<(unsigned)blocks, HX_RED_THREADS, 0, s>>>(bufs, blk_op, blk_first, blk_count);
+  else if (pass == HX_PASS_UPDATE)
+    cg_update_multi_kernel<double><<<(unsigned)blocks, HX_RED_THREADS, 0, s>>>(bufs, blk_op, blk_first, blk_count);
+  else
+    cg_direction_multi_kernel<double><<<(unsigned)blocks, HX_RED_THREADS, 0, s>>>(bufs, blk_op, blk_first, blk_count);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_batch_condition(HxCgState* const* states, int n, unsigned long long cond, cudaStream_t s) {
+  batch_condition_kernel<<<1, HX_RED_THREADS, 0, s>>>(states, n, cond);
+  return cudaGetLastError();
+}
 
 cudaError_t hx_launch_ir_residual(long long n, const double* b, const double* Ax, const unsigned char* dir, double* r,
                                   double* partial, unsigned int* counter, double* rn2, cudaStream_t s,

@@ -47,11 +47,12 @@ def test_batch_matches_oracle_and_individual_solves():
         xs.append(torch.full_like(b, float("nan")))
         refs.append((x_ref, info))
         oracle.append(oracle_solution(N, p, a, nu, faces, 100 + k, bh))
-    # all concurrent, one chain, chains of several solves, and autotuned (-1: timed at the
-    # first solve over 1, 2, 4 and 6 lanes; the results cannot depend on the choice)
-    for lanes in (0, 1, 2, 4, -1):
+    # all concurrent, one chain, chains of several solves, lock-step iterations (-2) and
+    # autotuned (-1: timed at the first solve over 1, 2, 4 and 6 lanes and the lock-step mode;
+    # the results cannot depend on the choice)
+    for lanes in (0, 1, 2, 4, hx.HX_BATCH_FUSED, hx.HX_BATCH_AUTO):
         batch = hx.Batch(ops, bs, xs, rtol=1e-10, lanes=lanes)
-        assert batch.lanes == (len(ops) if lanes <= 0 else lanes)
+        assert batch.lanes == (lanes if lanes == hx.HX_BATCH_FUSED else len(ops) if lanes <= 0 else lanes)
         for rep in range(2):  # the bound graph is reusable
             for x in xs:
                 x.fill_(float("nan"))
@@ -62,9 +63,36 @@ def test_batch_matches_oracle_and_individual_solves():
                 xb = x.cpu().numpy()
                 assert np.array_equal(xb, x_ref.cpu().numpy())
                 assert rel_err(xb, xo) <= 1e-8
-            if lanes < 0:
-                assert batch.lanes in (1, 2, 4, len(ops))
+            if lanes == hx.HX_BATCH_AUTO:
+                assert batch.lanes in (1, 2, 4, len(ops), hx.HX_BATCH_FUSED)
         del batch
+
+
+def test_fused_batch_with_mixed_preconditioners_and_failures():
+    """Lock-step mode beside LOR-preconditioned branches; an instance that fails its cap stops
+    alone while the others finish; the loop ends when every instance is done."""
+    hx = require_gpu()
+    specs = [(3, 2, 1.0, 1.0, hx.HX_PREC_JACOBI, 10000), (2, 4, 0.0, 1.0, hx.HX_PREC_LOR_MG, 10000),
+             (4, 3, 5.0, 0.1, hx.HX_PREC_COLLOCATED_MASS, 10000), (2, 6, 1.0, 1.0, hx.HX_PREC_JACOBI, 10000)]
+    ops, bs, xs, refs = [], [], [], []
+    for k, (N, p, a, nu, prec, _) in enumerate(specs):
+        V = S.structured_vertices(N, N, N, 0.1, 300 + k)
+        op = hx.Operator(hx.Mesh.box(N, N, N, p, p + 2, V, dirichlet_faces=63), a, nu)
+        op.set_preconditioner(prec, 1)
+        b = to_dev(S.random_vector(op.n_dof, 400 + k))
+        refs.append(op.solve(b, rtol=1e-10))
+        ops.append(op)
+        bs.append(b)
+        xs.append(torch.full_like(b, float("nan")))
+    batch = hx.Batch(ops, bs, xs, rtol=1e-10, lanes=hx.HX_BATCH_FUSED)
+    infos = batch.solve()
+    for (xr, ir), x, i in zip(refs, xs, infos):
+        assert i["status"] == 0 and i["iterations"] == ir["iterations"]
+        assert torch.equal(x, xr)
+    # a cap of 3 iterations: every instance stops with NOT_CONVERGED after 3 iterations
+    capped = hx.Batch(ops, bs, xs, rtol=1e-10, max_it=3, lanes=hx.HX_BATCH_FUSED)
+    infos = capped.solve(raise_on_fail=False)
+    assert all(i["status"] == hx.HX_ERR_NOT_CONVERGED and i["iterations"] == 3 for i in infos)
 
 
 def test_batch_reports_failures():
