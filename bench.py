@@ -68,13 +68,13 @@ HBM_GBS = _measured_hbm_gbs()
 # 565 G DFMA/s at ~1.94 GHz: 1.97 per clock per SM) x 148 SMs x 2032 MHz x 2 flops.
 FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch, keyed by
-# (p, N, geom): the 32^3 capture of the current kernel (496.3 MB read + 28.4 MB written)
+# (p, N, geom): the 32^3 capture of the current kernel (493.9 MB read + 28.8 MB written)
 # scaled by the element count (27x at 96^3); traffic grows in proportion to the elements.
-NCU_TRAFFIC = {(4, 96, "stored"): (496.308736e6 + 28.430848e6) * 27}
+NCU_TRAFFIC = {(4, 96, "stored"): (493.932288e6 + 28.763392e6) * 27}
 # sm__pipe_fp64_cycles_active (% of peak sustained) of the same capture: the FP64 pipe's
 # own utilization, which the algorithmic-flop fraction overstates (the even-odd folding
 # executes fewer flops than the algorithmic count)
-NCU_FP64_PIPE = {(4, 96, "stored"): 0.830}
+NCU_FP64_PIPE = {(4, 96, "stored"): 0.831}
 # FP32 element kernels of the mixed-precision solve (include/hx.h HX_F32_*)
 F32_KERNELS = {0: "collocated", 1: "direct_staged", 2: "direct", 3: "mma_bf16", 4: "mma_bf16x3"}
 
