@@ -480,7 +480,7 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
     torch.cuda.synchronize()
     t_mix = reduce_max(e0.elapsed_time(e1) / 1e3, world) / args.steps
     err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
-    kind, tune_ms = op.f32_kernel()
+    kind, block_elems, tune_ms = op.f32_kernel()
     t32 = time_applies_f32(op, torch, b.float())
     n = p + 1
     geo = 7 * 4 * q ** 3 * E if args.geom == "stored" else 24 * 8 * E
@@ -489,7 +489,7 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
             "inner_iterations": info["iterations"], "inner_rtol": args.inner_rtol,
             "rel_residual_fp64": info["rel_residual"], "rel_diff_vs_fp64_solution": err,
             "apply_f32_gdofs": n_dof / t32 / 1e9, "apply_f32_ms": 1e3 * t32,
-            "f32_kernel": F32_KERNELS.get(kind, kind),
+            "f32_kernel": F32_KERNELS.get(kind, kind), "f32_block_elems": block_elems,
             "f32_autotune_ms": {F32_KERNELS[k]: v for k, v in enumerate(tune_ms) if v >= 0},
             "roofline_f32": {"bound": "hbm", "achieved": bytes32 / t32 / 1e9, "peak": HBM_GBS, "unit": "GB/s",
                              "frac": bytes32 / t32 / 1e9 / HBM_GBS, "alg_bytes_per_launch": bytes32,
@@ -832,7 +832,7 @@ def run_sweep(hx, torch, args, peaks):
 
         t_mix, infom = timed(mixed_step, args.sweep_reps)
         diff = float(torch.linalg.norm(xm - x) / torch.linalg.norm(x))
-        kind, tune_ms = op.f32_kernel()
+        kind, block_elems, tune_ms = op.f32_kernel()
         del op, x, xm
         torch.cuda.empty_cache()
         otf = hx.Operator(mesh, ALPHA, NU, geom_mode=hx.HX_GEOM_ONTHEFLY)
@@ -845,7 +845,7 @@ def run_sweep(hx, torch, args, peaks):
             "apply_fp64_frac_of_probe": flops / t_app / 1e12 / peaks["fp64_tflops"],
             "apply_f32_ms": 1e3 * t32, "apply_f32_gdofs": n_dof / t32 / 1e9,
             "apply_f32_hbm_frac": bytes32 / t32 / 1e9 / HBM_GBS,
-            "f32_kernel": F32_KERNELS.get(kind, kind),
+            "f32_kernel": F32_KERNELS.get(kind, kind), "f32_block_elems": block_elems,
             "f32_autotune_ms": {F32_KERNELS[k]: v for k, v in enumerate(tune_ms) if v >= 0},
             "apply_onthefly_gdofs": n_dof / t_otf / 1e9, "onthefly_vs_stored": t_app / t_otf,
             "fp64_step_s": t_fp64, "fp64_iterations": info["iterations"],

@@ -276,17 +276,20 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
  *   HX_F32_MMA_BF16X3     the same with each operand split into a high and a low BF16 part and
  *                         three products accumulated (hi*hi + hi*lo + lo*hi, ~16 significant
  *                         bits, ~1e-4 relative); stored factors only
- *   HX_F32_AUTO           (default) the fastest of the FP32-accurate candidates
- *                         (HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED, HX_F32_DIRECT) for this order,
- *                         quadrature,
- *                         geometry mode and size class (log2 of the element count), timed once
- *                         per process by the operator's first FP32 set-up (one warm-up and three
+ *   HX_F32_AUTO           (default) the fastest of the FP32-accurate candidates -- kernel form
+ *                         (HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED, HX_F32_DIRECT) and, for the
+ *                         direct forms with stored factors, tile shape (half, the default or
+ *                         twice the elements per block, where the block stays within 1024
+ *                         threads and the shared memory) -- for this order, quadrature, geometry
+ *                         mode and size class (log2 of the element count), timed once per
+ *                         process by the operator's first FP32 set-up (one warm-up and three
  *                         timed launches of each candidate, CUDA events) and cached
- * hx_op_set_f32_kernel selects one (HX_ERR_ARG for an unknown kind, HX_ERR_UNSUPPORTED for
- * a stored-factor kind with on-the-fly geometry); it takes effect at the next FP32 set-up.
- * hx_op_f32_kernel reports the kernel in use (*kind = -1 before the first FP32 set-up) and,
- * when ms is not NULL, the autotuner's average time per launch of each candidate in ms
- * (ms[kind], -1 where not timed).  Host-side only.
+ * hx_op_set_f32_kernel selects one kind with its default tile (HX_ERR_ARG for an unknown kind,
+ * HX_ERR_UNSUPPORTED for a stored-factor kind with on-the-fly geometry); it takes effect at the
+ * next FP32 set-up.  hx_op_f32_kernel reports the kernel in use (*kind = -1 before the first
+ * FP32 set-up), when block_elems is not NULL its elements per block (-1 for the kinds with a
+ * fixed block), and when ms is not NULL the autotuner's average time per launch of each kind's
+ * fastest tile in ms (ms[kind] for kinds 0..2, -1 where not timed).  Host-side only.
  */
 #define HX_F32_AUTO (-1)
 #define HX_F32_COLLOCATED 0
@@ -295,7 +298,7 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
 #define HX_F32_MMA_BF16 3
 #define HX_F32_MMA_BF16X3 4
 HX_API hx_status hx_op_set_f32_kernel(hx_op* op, int kind);
-HX_API hx_status hx_op_f32_kernel(const hx_op* op, int* kind, float* ms /* 3 entries or NULL */);
+HX_API hx_status hx_op_f32_kernel(const hx_op* op, int* kind, int* block_elems, float* ms /* 3 entries or NULL */);
 
 /*
  * Failure-detection hook (the paper has no counterpart).  For p <= 4 with stored

@@ -76,7 +76,7 @@ SIGNATURES = {
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
     "hx_op_set_wait_limit": (_I, [_P, _I]),
     "hx_op_set_f32_kernel": (_I, [_P, _I]),
-    "hx_op_f32_kernel": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "hx_op_f32_kernel": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
     "hx_op_collocated_mass": (_I, [_P, _P, _P]),
     "hx_op_set_preconditioner": (_I, [_P, ctypes.c_int, ctypes.c_int, _P]),
@@ -336,11 +336,12 @@ def hx_op_set_f32_kernel(op, kind):
 
 
 def hx_op_f32_kernel(op):
-    """(kind in use or -1, [autotuner ms per launch of each candidate, -1 where not timed])"""
-    k = _I(0)
+    """(kind in use or -1, elements per block or -1, [autotuner ms per launch of each kind's fastest
+    tile, -1 where not timed])"""
+    k, ne = _I(0), _I(0)
     ms = (ctypes.c_float * 3)()
-    _check(_lib.hx_op_f32_kernel(op, ctypes.byref(k), ms))
-    return k.value, list(ms)
+    _check(_lib.hx_op_f32_kernel(op, ctypes.byref(k), ctypes.byref(ne), ms))
+    return k.value, ne.value, list(ms)
 
 
 def hx_op_set_wait_limit(op, attempts):

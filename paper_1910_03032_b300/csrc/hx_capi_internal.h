@@ -103,6 +103,7 @@ struct hx_op {
   int wait_limit = HX_WAIT_LIMIT_DEFAULT;  // attempts of the FP32 kernel's first wait for its factors
   int f32_request = HX_F32_AUTO;  // FP32 element kernel asked for (hx_op_set_f32_kernel)
   int f32_kind = -1;              // FP32 element kernel in use (-1: not chosen yet)
+  int f32_tile = 0;               // its tile variant (-1, 0, +1: half, default, twice the elements per block)
   float f32_ms[3] = {-1.0f, -1.0f, -1.0f};  // autotuner: average time of each candidate (ms)
   float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
   double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual

@@ -34,7 +34,7 @@ cudaError_t element_apply32(const hx_op* op, const float* x, const int* done, cu
                                           hx_launch_apply32_p4, hx_launch_apply32_p5, hx_launch_apply32_p6,
                                           hx_launch_apply32_p7, hx_launch_apply32_p8};
   const HxApplyArgsF a = apply_args32(op, x, done);
-  return t[op->mesh->p](op->mesh->T32, a, op->geom, op->f32_kind, s);
+  return t[op->mesh->p](op->mesh->T32, a, op->geom, op->f32_kind, op->f32_tile, s);
 }
 
 // Autotuned choice of the FP32 element kernel, shared by the operators of one process with the
@@ -46,18 +46,20 @@ struct F32Key {
   }
 };
 std::mutex g_f32_mutex;
-std::map<F32Key, int> g_f32_choice;
+std::map<F32Key, std::pair<int, int>> g_f32_choice;  // (kind, tile)
 
-// The FP32 element kernel this operator runs: the caller's choice (hx_op_set_f32_kernel), else the
-// fastest candidate for this order, quadrature and geometry mode, timed once per process and
-// size class on this operator (one warm-up and three timed element-kernel launches each, CUDA
-// events on the solver stream).  The candidates compute the same operator; they differ in how
-// the contractions are organized (collocated derivative or B/D-direct) and in whether the stored
-// factors arrive by bulk copies.
+// The FP32 element kernel this operator runs: the caller's choice (hx_op_set_f32_kernel, default
+// tile), else the fastest candidate -- kernel form and tile shape (elements per block) -- for this
+// order, quadrature and geometry mode, timed once per process and size class on this operator
+// (one warm-up and three timed element-kernel launches each, CUDA events on the solver stream).
+// The candidates compute the same operator; they differ in how the contractions are organized
+// (collocated derivative or B/D-direct), in whether the stored factors arrive by bulk copies,
+// and in how many elements a block holds.
 hx_status tune_f32(hx_op* op) {
   if (op->f32_kind >= 0) return HX_OK;
   if (op->f32_request >= 0) {
     op->f32_kind = op->f32_request;
+    op->f32_tile = 0;
     return HX_OK;
   }
   const hx_mesh* m = op->mesh;
@@ -68,34 +70,46 @@ hx_status tune_f32(hx_op* op) {
     std::lock_guard<std::mutex> lock(g_f32_mutex);
     auto it = g_f32_choice.find(key);
     if (it != g_f32_choice.end()) {
-      op->f32_kind = it->second;
+      op->f32_kind = it->second.first;
+      op->f32_tile = it->second.second;
       return HX_OK;
     }
   }
   cudaStream_t st = op->stream;
-  int cand[3], nc = 0;
-  cand[nc++] = HX_F32_COLLOCATED;
-  if (op->geom == HX_GEOM_STORED) cand[nc++] = HX_F32_DIRECT_STAGED;
-  cand[nc++] = HX_F32_DIRECT;
+  std::vector<std::pair<int, int>> cand;
+  cand.push_back({HX_F32_COLLOCATED, 0});
+  const int tiles = op->geom == HX_GEOM_STORED ? 1 : 0;  // tile variants only with stored factors
+  for (int tl = -tiles; tl <= tiles; ++tl) {
+    if (op->geom == HX_GEOM_STORED) cand.push_back({HX_F32_DIRECT_STAGED, tl});
+    cand.push_back({HX_F32_DIRECT, tl});
+  }
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   if (e == cudaSuccess) e = cudaMemsetAsync(op->p32, 0, sizeof(float) * m->n_dof, st);
-  int best = cand[0];
+  std::pair<int, int> best = cand[0];
   float best_ms = -1.0f;
   for (int i = 0; i < 3; ++i) op->f32_ms[i] = -1.0f;
-  for (int k = 0; k < nc && e == cudaSuccess; ++k) {
-    op->f32_kind = cand[k];
-    e = element_apply32(op, op->p32, nullptr, st);
-    if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+  for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
+    op->f32_kind = cand[k].first;
+    op->f32_tile = cand[k].second;
+    // a tile variant that does not exist for this order (too many threads or too much shared
+    // memory) is refused by its launcher before anything is enqueued: skip it
+    if (element_apply32(op, op->p32, nullptr, st) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    e = cudaEventRecord(t0, st);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = element_apply32(op, op->p32, nullptr, st);
     if (e == cudaSuccess) e = cudaEventRecord(t1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     float ms = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
     op->launches += 4;
-    op->f32_ms[cand[k]] = ms / 3.0f;
-    if (e == cudaSuccess && (best_ms < 0.0f || ms < best_ms)) {
+    if (e != cudaSuccess) break;
+    float& km = op->f32_ms[cand[k].first];
+    if (km < 0.0f || ms / 3.0f < km) km = ms / 3.0f;  // per kind: its fastest tile
+    if (best_ms < 0.0f || ms < best_ms) {
       best_ms = ms;
       best = cand[k];
     }
@@ -106,7 +120,8 @@ hx_status tune_f32(hx_op* op) {
     op->f32_kind = -1;
     return cuda_fail(e, "FP32 kernel timing");
   }
-  op->f32_kind = best;
+  op->f32_kind = best.first;
+  op->f32_tile = best.second;
   std::lock_guard<std::mutex> lock(g_f32_mutex);
   g_f32_choice[key] = best;
   return HX_OK;
@@ -390,9 +405,17 @@ hx_status hx_op_set_f32_kernel(hx_op* op, int kind) {
   return HX_OK;
 }
 
-hx_status hx_op_f32_kernel(const hx_op* op, int* kind, float* ms) {
+hx_status hx_op_f32_kernel(const hx_op* op, int* kind, int* block_elems, float* ms) {
   if (!op || !kind) return fail(HX_ERR_ARG, "NULL argument");
   *kind = op->f32_kind;
+  if (block_elems) {
+    static const hx_block_elems_fn t[] = {nullptr, hx_apply32_block_elems_p1, hx_apply32_block_elems_p2,
+                                          hx_apply32_block_elems_p3, hx_apply32_block_elems_p4,
+                                          hx_apply32_block_elems_p5, hx_apply32_block_elems_p6,
+                                          hx_apply32_block_elems_p7, hx_apply32_block_elems_p8};
+    const bool direct = op->f32_kind == HX_F32_DIRECT_STAGED || op->f32_kind == HX_F32_DIRECT;
+    *block_elems = direct ? t[op->mesh->p](op->mesh->q, op->f32_tile) : -1;
+  }
   if (ms)
     for (int i = 0; i < 3; ++i) ms[i] = op->f32_ms[i];  // the autotuner's candidates (kinds 0..2)
   return HX_OK;

@@ -1046,18 +1046,18 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_apply32_p##P(const HxTablesF& T, const HxApplyArgsF& A, int geom, int kind,      \
-                                     cudaStream_t s) {                                                     \
+                                     int tile, cudaStream_t s) {                                           \
     if (kind >= 3 && geom != HX_KGEOM_STORED) return cudaErrorInvalidValue;                                \
     if (T.q == P + 1)                                                                                      \
       return kind == 0   ? hx::launch_apply_q<float, P, P + 1>(T, A, geom, s)                              \
              : kind == 3 ? hx::launch_apply32_mma<P, P + 1, 1>(T, A, s)                                    \
              : kind == 4 ? hx::launch_apply32_mma<P, P + 1, 3>(T, A, s)                                    \
-                         : hx::launch_apply32_q<P, P + 1>(T, A, geom, kind == 1, s);                       \
+                         : hx::launch_apply32_q<P, P + 1>(T, A, geom, kind == 1, tile, s);                 \
     if (T.q == P + 2)                                                                                      \
       return kind == 0   ? hx::launch_apply_q<float, P, P + 2>(T, A, geom, s)                              \
              : kind == 3 ? hx::launch_apply32_mma<P, P + 2, 1>(T, A, s)                                    \
              : kind == 4 ? hx::launch_apply32_mma<P, P + 2, 3>(T, A, s)                                    \
-                         : hx::launch_apply32_q<P, P + 2>(T, A, geom, kind == 1, s);                       \
+                         : hx::launch_apply32_q<P, P + 2>(T, A, geom, kind == 1, tile, s);                 \
     return cudaErrorInvalidValue;                                                                          \
   }                                                                                                        \
   cudaError_t hx_launch_diag_p##P(const HxTables& T, const HxDiagArgs& A, int geom, cudaStream_t s) {     \
@@ -1076,6 +1076,9 @@ cudaError_t launch_load_q(const HxTables& T, const HxLoadArgs& A, cudaStream_t s
     if (T.q == P + 1) return hx::launch_apply_multi_q<P, P + 1>(T, args, blk_op, blk_first, blocks, geom, nuf, s); \
     if (T.q == P + 2) return hx::launch_apply_multi_q<P, P + 2>(T, args, blk_op, blk_first, blocks, geom, nuf, s); \
     return cudaErrorInvalidValue;                                                                          \
+  }                                                                                                        \
+  int hx_apply32_block_elems_p##P(int q, int tile) {                                                      \
+    return q == P + 1 ? hx::ne32_of_tile<P + 1>(tile) : hx::ne32_of_tile<P + 2>(tile);                    \
   }                                                                                                        \
   int hx_apply_block_elems_p##P(int q, int geom) {                                                         \
     if (q == P + 1)                                                                                        \

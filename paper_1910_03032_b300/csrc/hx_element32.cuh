@@ -368,35 +368,64 @@ constexpr int ne32() {
   return (Q * Q * 8 <= 256) ? 8 : (Q * Q * 4 <= 256) ? 4 : 2;
 }
 
-template <int P, int Q, int GEOM, bool NUF, bool STAGE>
-cudaError_t launch_apply32_impl(const HxTablesF& T, const HxApplyArgsF& A, cudaStream_t s) {
-  constexpr int NE = ne32<Q>();
-  using L = Layout32<P, Q, NE>;
-  constexpr int NT = ((NE * Q * Q + 31) / 32) * 32;
-  constexpr int RB = GEOM == HX_KGEOM_ONTHEFLY ? 96 : 64;  // registers per thread budgeted
-  constexpr int MINB = 65536 / (NT * RB) < 1 ? 1 : 65536 / (NT * RB) > 16 ? 16 : 65536 / (NT * RB);
-  // the bulk copies of staged factors move whole padded (16-byte) element ranges
-  if (STAGE && A.fstride != L::FE32) return cudaErrorInvalidValue;
-  const size_t shmem =
-      sizeof(float) * ((STAGE ? (size_t)NE * L::FE : 0) + (size_t)L::INT + (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
-  auto k = apply32_kernel<P, Q, NE, NT, MINB, GEOM, NUF, STAGE>;
-  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-  if (err != cudaSuccess) return err;
-  const long long blocks = (A.E + NE - 1) / NE;
-  if (blocks == 0) return cudaSuccess;
-  k<<<(unsigned)blocks, NT, shmem, s>>>(T, A);
-  return cudaGetLastError();
+// Elements per block of the tile variant `shift` (the default ne32 scaled by 2^shift), or 0 when
+// that variant does not exist (NE outside 1..8, or more than 1024 threads).
+template <int Q>
+constexpr int ne32_tile(int shift) {
+  const int ne = shift < 0 ? ne32<Q>() / 2 : shift > 0 ? ne32<Q>() * 2 : ne32<Q>();
+  return (ne < 1 || ne > 8 || ((ne * Q * Q + 31) / 32) * 32 > 1024) ? 0 : ne;
 }
 
-// stage: stored factors arrive by bulk copies (else they are read from global memory)
-template <int P, int Q>
-cudaError_t launch_apply32_q(const HxTablesF& T, const HxApplyArgsF& A, int geom, bool stage, cudaStream_t s) {
-  if (geom == HX_KGEOM_STORED) {
-    if (stage) return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, true>(T, A, s);
-    return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, false>(T, A, s);
+template <int P, int Q, int GEOM, bool NUF, bool STAGE, int NE>
+cudaError_t launch_apply32_impl(const HxTablesF& T, const HxApplyArgsF& A, cudaStream_t s) {
+  if constexpr (NE == 0) {
+    return cudaErrorInvalidValue;  // no such tile variant
+  } else {
+    using L = Layout32<P, Q, NE>;
+    constexpr int NT = ((NE * Q * Q + 31) / 32) * 32;
+    constexpr int RB = GEOM == HX_KGEOM_ONTHEFLY ? 96 : 64;  // registers per thread budgeted
+    constexpr int MINB = 65536 / (NT * RB) < 1 ? 1 : 65536 / (NT * RB) > 16 ? 16 : 65536 / (NT * RB);
+    // the bulk copies of staged factors move whole padded (16-byte) element ranges
+    if (STAGE && A.fstride != L::FE32) return cudaErrorInvalidValue;
+    const size_t shmem = sizeof(float) * ((STAGE ? (size_t)NE * L::FE : 0) + (size_t)L::INT +
+                                          (GEOM == HX_KGEOM_ONTHEFLY ? NE * 24 : 0));
+    if (shmem > 227 * 1024) return cudaErrorInvalidValue;
+    auto k = apply32_kernel<P, Q, NE, NT, MINB, GEOM, NUF, STAGE>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    if (err != cudaSuccess) return err;
+    const long long blocks = (A.E + NE - 1) / NE;
+    if (blocks == 0) return cudaSuccess;
+    k<<<(unsigned)blocks, NT, shmem, s>>>(T, A);
+    return cudaGetLastError();
   }
-  if (A.nu_q) return launch_apply32_impl<P, Q, HX_KGEOM_ONTHEFLY, true, false>(T, A, s);
-  return launch_apply32_impl<P, Q, HX_KGEOM_ONTHEFLY, false, false>(T, A, s);
+}
+
+// stage: stored factors arrive by bulk copies (else they are read from global memory);
+// tile: -1, 0, +1 for half, the default and twice the elements per block (stored factors; the
+// on-the-fly forms have the default only)
+template <int P, int Q>
+cudaError_t launch_apply32_q(const HxTablesF& T, const HxApplyArgsF& A, int geom, bool stage, int tile,
+                             cudaStream_t s) {
+  constexpr int NM = ne32_tile<Q>(-1), N0 = ne32_tile<Q>(0), NP = ne32_tile<Q>(1);
+  if (geom == HX_KGEOM_STORED) {
+    if (stage) {
+      if (tile < 0) return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, true, NM>(T, A, s);
+      if (tile > 0) return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, true, NP>(T, A, s);
+      return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, true, N0>(T, A, s);
+    }
+    if (tile < 0) return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, false, NM>(T, A, s);
+    if (tile > 0) return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, false, NP>(T, A, s);
+    return launch_apply32_impl<P, Q, HX_KGEOM_STORED, false, false, N0>(T, A, s);
+  }
+  if (tile != 0) return cudaErrorInvalidValue;
+  if (A.nu_q) return launch_apply32_impl<P, Q, HX_KGEOM_ONTHEFLY, true, false, N0>(T, A, s);
+  return launch_apply32_impl<P, Q, HX_KGEOM_ONTHEFLY, false, false, N0>(T, A, s);
+}
+
+// elements per block of the direct FP32 kernel's tile variant (0: none)
+template <int Q>
+int ne32_of_tile(int tile) {
+  return ne32_tile<Q>(tile);
 }
 
 }  // namespace hx

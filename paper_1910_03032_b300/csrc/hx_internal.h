@@ -75,8 +75,10 @@ typedef cudaError_t (*hx_apply_launcher)(const HxTables&, const HxApplyArgs&, in
 typedef cudaError_t (*hx_diag_launcher)(const HxTables&, const HxDiagArgs&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_diag32_launcher)(const HxTablesF&, const HxDiagArgsF&, int geom, cudaStream_t);
 typedef cudaError_t (*hx_load_launcher)(const HxTables&, const HxLoadArgs&, cudaStream_t);
-// kind: HX_F32_COLLOCATED, HX_F32_DIRECT_STAGED or HX_F32_DIRECT (include/hx.h)
-typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, int kind, cudaStream_t);
+// kind: HX_F32_* (include/hx.h); tile: -1, 0, +1 (half, default, twice the elements per block of
+// the direct kinds with stored factors)
+typedef cudaError_t (*hx_apply32_launcher)(const HxTablesF&, const HxApplyArgsF&, int geom, int kind, int tile,
+                                           cudaStream_t);
 typedef cudaError_t (*hx_grad_launcher)(const HxTables&, const HxGradArgs&, cudaStream_t);
 // the FP64 element kernel over several operators of one order: blocks -> (operator, block) by table
 typedef cudaError_t (*hx_apply_multi_launcher)(const HxTables&, const HxApplyArgs*, const int* blk_op,
@@ -89,7 +91,8 @@ typedef int (*hx_block_elems_fn)(int q, int geom);
   cudaError_t hx_launch_diag_p##P(const HxTables&, const HxDiagArgs&, int, cudaStream_t);         \
   cudaError_t hx_launch_diag32_p##P(const HxTablesF&, const HxDiagArgsF&, int, cudaStream_t);     \
   cudaError_t hx_launch_load_p##P(const HxTables&, const HxLoadArgs&, cudaStream_t);              \
-  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, int, cudaStream_t); \
+  cudaError_t hx_launch_apply32_p##P(const HxTablesF&, const HxApplyArgsF&, int, int, int, cudaStream_t); \
+  int hx_apply32_block_elems_p##P(int q, int tile);                                               \
   cudaError_t hx_launch_grad_p##P(const HxTables&, const HxGradArgs&, cudaStream_t);                     \
   cudaError_t hx_launch_apply_multi_p##P(const HxTables&, const HxApplyArgs*, const int*, const int*,     \
                                          long long, int, int, cudaStream_t);                              \

@@ -35,8 +35,9 @@ def test_fp32_apply_matches_oracle(hx, p, shape, geom, kind):
     y = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
     ref = fem.Operator(om, 1.7, 0.45).apply(x32.astype(np.float64), constrained=True)
     assert rel_err(y, ref) <= 2e-5, rel_err(y, ref)
-    used, ms = op.f32_kernel()
+    used, ne, ms = op.f32_kernel()
     assert used == kind if kind >= 0 else used in ((0, 1, 2) if geom == 0 else (0, 2))
+    assert (ne in (1, 2, 4, 8)) if used in (1, 2) else ne == -1
     if kind < 0 and used >= 0 and ms[used] >= 0:  # tuned here (not taken from the process cache)
         assert ms[used] == min(m for m in ms if m >= 0)
 
