@@ -440,20 +440,22 @@ def run_hx(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def time_applies_f32(op, torch, x32, reps=20, warm=3):
-    """Average device time of the FP32 apply (element kernel + assembly) with CUDA events."""
-    y = torch.empty_like(x32)
+def time_applies_f32(op, torch, x32, reps=20, warm=3, group=5):
+    """Average device time of the FP32 apply (element kernel + assembly) with CUDA events: groups
+    of `group` back-to-back applies between two events, so that the host's launch latency before
+    the first kernel of a group is spread over the group (an apply takes only ~1 ms)."""
     s = torch.cuda.current_stream()
     for _ in range(warm):
         op.apply_f32(x32)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
-    for _ in range(reps):
+    for _ in range(max(1, reps // group)):
         e0.record(s)
-        hx_apply = op.apply_f32(x32)
+        for _ in range(group):
+            op.apply_f32(x32)
         e1.record(s)
         e1.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
+        times.append(e0.elapsed_time(e1) / 1e3 / group)
     return float(np.mean(times))
 
 

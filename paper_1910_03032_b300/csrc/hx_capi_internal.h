@@ -72,6 +72,7 @@ struct hx_mesh {
   long long n_dirichlet = 0;     // Dirichlet DoFs (0: no boundary condition fixes the constants)
   long long grid[3] = {0, 0, 0}; // structured meshes: the logical (pN+1)-node grid of the DoFs
   HxGridAsm ga = {};  // box meshes: the grid the assembly indexes by arithmetic (ga.p = 0: none)
+  HxELayout lay = {}; // layout of this mesh's E-vectors (line layout with ga, else element-major)
 };
 
 struct hx_op {

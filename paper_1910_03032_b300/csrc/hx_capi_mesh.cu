@@ -194,6 +194,7 @@ hx_status hx_mesh_create_box(int nx, int ny, int nz, int p, int q, const double*
     (*out)->grid[1] = gy;
     (*out)->grid[2] = gz;
     (*out)->ga = hx_grid_asm(p, nx, ny, nz, (int)gx, (int)gy);
+    (*out)->lay = hx_elayout_rows(nx);
   }
   return s;
 }

@@ -16,6 +16,7 @@ HxApplyArgsF apply_args32(const hx_op* op, const float* x, const int* done) {
   a.R = m->R;
   a.x = x;
   a.yE = op->yE32;
+  a.lay = m->lay;
   a.factors = op->factors32;
   a.fstride = hx_f32_factor_stride(m->q);
   a.X8 = m->X8;
@@ -203,6 +204,7 @@ hx_status ensure_mixed(hx_op* op) {
       d.alpha = op->alpha;
       d.nu = op->nu;
       d.dE = op->yE32;
+      d.lay = m->lay;
       HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
       HX_TRY(hx_launch_assemble32(n, m->ga, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
              "FP32 diagonal assembly");

@@ -13,6 +13,7 @@ HxApplyArgs apply_args(const hx_op* op, const double* x, int constrained, const 
   a.R = m->R;
   a.x = x;
   a.yE = op->yE;
+  a.lay = m->lay;
   a.factors = op->factors;
   a.fstride = 7LL * m->q * m->q * m->q;
   a.X8 = m->X8;
@@ -157,6 +158,7 @@ hx_status ensure_diag(hx_op* op, cudaStream_t s, int* nl) {
   d.alpha = op->alpha;
   d.nu = op->nu;
   d.dE = op->yE;
+  d.lay = m->lay;
   HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
   HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
          "diagonal assembly");
@@ -174,7 +176,7 @@ hx_status refresh_dinv(hx_op* op, cudaStream_t s, int* nl) {
   }
   if (op->prec == HX_PREC_COLLOCATED_MASS) {
     if (!(op->alpha > 0.0)) return fail(HX_ERR_ARG, "the collocated mass preconditioner needs alpha > 0");
-    HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
+    HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, m->lay, s), "collocated mass");
     HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->pdiag, s),
            "collocated mass assembly");
     *nl += 2;
@@ -284,6 +286,7 @@ hx_status hx_op_create(hx_mesh* m, double alpha, double nu, const double* nu_q, 
       la.X8 = m->X8;
       la.fq = nullptr;
       la.yE = op->yE;
+      la.lay = m->lay;
       e = load_launcher(m->p)(m->T, la, s);
       if (e == cudaSuccess) e = hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->m1, s);
       if (e != cudaSuccess) { st = cuda_fail(e, "mass row sums"); break; }
@@ -369,6 +372,7 @@ hx_status hx_op_load_vector(hx_op* op, const double* f_q, double* b, void* strea
   a.X8 = m->X8;
   a.fq = f_q;
   a.yE = op->yE;
+  a.lay = m->lay;
   HX_TRY(load_launcher(m->p)(m->T, a, s), "load kernel");
   HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, b, s), "assembly");
   op->launches += 2;

@@ -40,7 +40,7 @@ hx_status mg_values(hx_op* op, cudaStream_t s, int* nl) {
   if (op->has_field) return fail(HX_ERR_UNSUPPORTED, "the LOR preconditioner takes a constant nu only");
   const hx_mesh* m = op->mesh;
   const int nx = (int)((m->grid[0] - 1) / m->p), ny = (int)((m->grid[1] - 1) / m->p);
-  HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
+  HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, m->lay, s), "collocated mass");
   HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->mg_mc, s),
          "collocated mass assembly");
   HX_TRY(hx_mg_fine(m->T, nx, ny, m->X8, op->alpha, op->nu, 1, op->mg_mc, op->mg.levels[0], s), "fine LOR stencil");
@@ -213,7 +213,7 @@ hx_status hx_op_collocated_mass(hx_op* op, double* diag, void* stream) {
   if (!op || !diag) return fail(HX_ERR_ARG, "NULL argument");
   const hx_mesh* m = op->mesh;
   cudaStream_t s = (cudaStream_t)stream;
-  HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, s), "collocated mass");
+  HX_TRY(hx_launch_cmass(m->T, m->E, m->X8, op->alpha, op->yE, m->lay, s), "collocated mass");
   HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, diag, s),
          "collocated mass assembly");
   op->launches += 2;

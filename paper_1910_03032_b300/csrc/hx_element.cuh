@@ -289,12 +289,16 @@ struct Layout {
 // stages shared by the apply and load-vector kernels (region D of each element)
 // ---------------------------------------------------------------------------
 // After the z-direction transpose has left [kz][jq][iq] in region D: B^T along
-// y, then B^T along x written straight to the E-vector.
+// y, then B^T along x into region X (free by now), and from there to the E-vector in the
+// order of its layout, so that consecutive threads write consecutive words (whole element
+// blocks for element-major E-vectors, the same x-line of the block's elements side by side
+// for the line layout).
 template <int N, int Q, int NE, int NT, typename Real>
 __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Real* smem, long long e0, long long E,
-                                                    Real* __restrict__ yE) {
+                                                    Real* __restrict__ yE, const HxELayout& lay) {
   using Lt = Layout<Q, Real>;
-  constexpr int N3 = N * N * N, SY = Lt::SY, SZ = Lt::SZ, R3 = Lt::R3;
+  constexpr int N3 = N * N * N, SY = Lt::SY, SZ = Lt::SZ, R3 = Lt::R3, RG = Lt::RG;
+  static_assert(RG >= N3, "an element's result fits in its region X");
   for (int t = threadIdx.x; t < NE * N * Q; t += NT) {
     const int el = t / (N * Q), r = t - el * (N * Q);
     const int kz = r / Q, iq = r - kz * Q;
@@ -308,11 +312,24 @@ __device__ __forceinline__ void transpose_y_x_store(const HxTablesT<Real>& T, Re
   for (int t = threadIdx.x; t < NE * N * N; t += NT) {
     const int el = t / (N * N), r = t - el * (N * N);
     const int kz = r / N, j = r - kz * N;
-    const long long e = e0 + el;
     Real vin[Q], vout[N];
     load_line<Q>(smem + el * R3 + kz * SZ + j * SY, 1, vin);
     eo_apply<Q, N, 1>(T.Bte, T.Bto, vin, vout);
-    if (e < E) store_line<N>(yE + e * N3 + r * N, 1, vout);
+    store_line<N>(smem + el * R3 + RG + r * N, 1, vout);
+  }
+  __syncthreads();
+  const int nel = (E - e0) < NE ? (int)(E - e0) : NE;
+  if (lay.nx == 0) {
+    Real* out = yE + e0 * N3;  // the block's elements are one contiguous range
+    for (int t = threadIdx.x; t < nel * N3; t += NT) {
+      const int el = t / N3, l = t - el * N3;
+      out[t] = smem[el * R3 + RG + l];
+    }
+  } else {
+    for (int t = threadIdx.x; t < NE * N3; t += NT) {
+      const int i = t % N, u = t / N, el = u % NE, r = u / NE;
+      if (el < nel) yE[hx_eline(lay, e0 + el, r, N) + i] = smem[el * R3 + RG + r * N + i];
+    }
   }
 }
 
@@ -613,7 +630,7 @@ __device__ __forceinline__ void apply_body(const HxTablesT<Real>& T, const HxApp
     store_line<N>(Dc, SZ, out);
   }
   __syncthreads();
-  transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
+  transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE, A.lay);
   // no copy may still be writing this block's shared memory when it exits (every owner's
   // first wait saw the copy complete, so this returns at once)
   if (STAGE && tid == 0) mbar_wait_bounded(&fbar, HX_WAIT_LIMIT_EXIT);
@@ -674,7 +691,7 @@ __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTabl
     store_line<N>(smem + cel * R3 + jq * SY + iq, SZ, out);
   }
   __syncthreads();
-  transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE);
+  transpose_y_x_store<N, Q, NE, NT>(T, smem, e0, A.E, A.yE, A.lay);
 }
 
 // Adjoint gradients at every quadrature point (not part of the paper's method):
@@ -908,7 +925,7 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
       s += bb * (src[0] + src[1 * st] + src[4 * st]) + dd * src[6 * st] + Real(2) * bd * (src[3 * st] + src[5 * st]) +
            Real(2) * bb * src[2 * st];
     }
-    if (e < A.E) A.dE[e * N3 + l] = s;
+    if (e < A.E) A.dE[hx_eline(A.lay, e, l / N, N) + l % N] = s;
   }
 }
 

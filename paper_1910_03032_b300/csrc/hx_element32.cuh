@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     eo_apply_sym_anti<Q, N>(T.Bte, T.Bto, T.Dnte, T.Dnto, pp, rr, out);
     if (el < nel) {
-      float* yl = A.yE + (e0 + el) * N3 + r * N;
+      float* yl = A.yE + hx_eline(A.lay, e0 + el, r, N);
 #pragma unroll
       for (int i = 0; i < N; ++i) yl[i] = out[i];
     }

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(NT, 1)
         mma_acc(cy, ar, tD[nt]);
         scatter_c(ra, nt, lane, ROWS, N, cy, [&](int row, int i, float val) {
           const int el = row % NE, r = row / NE;
-          if (el < nel) A.yE[(e0 + el) * N3 + r * N + i] = val;
+          if (el < nel) A.yE[hx_eline(A.lay, e0 + el, r, N) + i] = val;
         });
       }
     }

@@ -7,6 +7,23 @@
 
 #include "hx_tables.h"
 
+// Layout of an E-vector (n^3 values per element, local node l = i + n j + n^2 k, x-line r = j + n k).
+// nx = 0: element-major, entry l of element e at e n^3 + l.  nx > 0 (box meshes, elements numbered
+// x fastest in rows of nx): the x-lines of one row of elements lie side by side, line r of element
+// e at ((e / nx) n^2 + r) (nx n) + (e mod nx) n, so that the entries a DoF-grid x-line gathers form
+// one contiguous range (the two entries of a node between elements are neighbours).
+struct HxELayout {
+  int nx;
+  unsigned m;  // e / nx = (e m) >> s for 0 <= e < 2^31
+  int s;
+};
+// first entry of x-line r of element e
+__host__ __device__ __forceinline__ long long hx_eline(const HxELayout& L, long long e, int r, int n) {
+  if (L.nx == 0) return (e * n * n + r) * n;
+  const long long row = (long long)(((unsigned long long)(unsigned)e * L.m) >> L.s);
+  return (row * n * n + r) * ((long long)L.nx * n) + (e - row * L.nx) * n;
+}
+
 // Arguments of the element-operator kernel (gather -> contractions ->
 // pointwise -> transposed contractions -> E-vector), in scalar type T
 // (double: the operator; float: the inner solver of the mixed-precision refinement).
@@ -15,7 +32,8 @@ struct HxApplyArgsT {
   long long E;            // number of elements
   const int* R;           // [E][n^3] restriction; g >= 0 free DoF, -(g+1) Dirichlet DoF
   const T* x;             // L-vector input
-  T* yE;                  // [E][n^3] E-vector output
+  T* yE;                  // E-vector output (E n^3 values)
+  HxELayout lay;          // its layout
   const T* factors;       // stored geometry: [E][fstride], 7 planes of q^3 (m, G00, G01, G02, G11, G12, G22)
   long long fstride;      // element stride of `factors` (7 q^3, or the padded FP32 stride)
   const double* X8;       // [E][8][3] element corner coordinates (on-the-fly geometry)
@@ -44,7 +62,8 @@ struct HxDiagArgsT {
   const double* X8;
   const double* nu_q;
   double alpha, nu;
-  T* dE;                  // [E][n^3] element diagonals
+  T* dE;                  // element diagonals (an E-vector)
+  HxELayout lay;          // its layout
 };
 typedef HxDiagArgsT<double> HxDiagArgs;
 typedef HxDiagArgsT<float> HxDiagArgsF;
@@ -55,6 +74,7 @@ struct HxLoadArgs {
   const double* X8;
   const double* fq;       // [E][q^3] source values at the quadrature points (null: f = 1)
   double* yE;
+  HxELayout lay;
 };
 
 // Arguments of the adjoint-gradient kernel: per-point dL/dnu and dL/df from u and lam.
@@ -116,12 +136,13 @@ cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int*
 // Logical grid of a box mesh (elements nx x ny x nz numbered x fastest, DoFs on the
 // (p nx + 1) x (p ny + 1) x (p nz + 1) node grid, lexicographic local nodes): the assembly then
 // finds a DoF's element entries by index arithmetic instead of reading the transpose map, in the
-// same (increasing E-vector position) order.  p = 0: no such grid, the map is read.
+// map's order (increasing element index).  The E-vectors it reads are in the line layout with
+// rows of nx elements (HxELayout).  p = 0: no such grid; element-major E-vectors, the map is read.
 struct HxGridAsm {
   int p, nx, ny, nz, gx, gy;
-  // n / d = (n m) >> s for 0 <= n < 2^31 (d = gx, gy, p): multiply-shift instead of division
-  unsigned mgx, mgy, mp;
-  int sgx, sgy, sp;
+  // n / d = (n m) >> s for 0 <= n < 2^31 (d = gx, gy, p, nx): multiply-shift instead of division
+  unsigned mgx, mgy, mp, mnx;
+  int sgx, sgy, sp, snx;
 };
 // Multiplier and shift of the division by d (1 <= d < 2^31) for dividends below 2^31:
 // s = 31 + ceil(log2 d), m = floor(2^s / d) + 1 (Granlund and Montgomery, "Division by invariant
@@ -132,11 +153,18 @@ inline void hx_fastdiv_init(int d, unsigned* m, int* s) {
   *s = 31 + l;
   *m = (unsigned)((1ULL << *s) / (unsigned long long)d + 1ULL);
 }
+// the line layout of the E-vectors of a box mesh with rows of nx elements
+inline HxELayout hx_elayout_rows(int nx) {
+  HxELayout L = {nx, 0u, 0};
+  hx_fastdiv_init(nx, &L.m, &L.s);
+  return L;
+}
 inline HxGridAsm hx_grid_asm(int p, int nx, int ny, int nz, int gx, int gy) {
-  HxGridAsm g = {p, nx, ny, nz, gx, gy, 0, 0, 0, 0, 0, 0};
+  HxGridAsm g = {p, nx, ny, nz, gx, gy, 0, 0, 0, 0, 0, 0, 0, 0};
   hx_fastdiv_init(gx, &g.mgx, &g.sgx);
   hx_fastdiv_init(gy, &g.mgy, &g.sgy);
   hx_fastdiv_init(p, &g.mp, &g.sp);
+  hx_fastdiv_init(nx, &g.mnx, &g.snx);
   return g;
 }
 // y[g] = sum_{k in off[g]..off[g+1]} yE[idx[k]]; with `constrained`, Dirichlet rows
@@ -163,7 +191,11 @@ struct HxCgState {
   unsigned int count[4];  // last-block counters, one per reduction kernel
 };
 
-#define HX_RED_BLOCKS 1184  // 8 x 148 SMs: fixed grid of every reduction kernel
+// Grid of the reduction kernels: one wave of HX_RED_MINB blocks of HX_RED_THREADS on each of the
+// 148 SMs (the kernels are compiled for that residency), so that no partly filled second wave
+// stretches these memory-bound passes.
+#define HX_RED_MINB 6
+#define HX_RED_BLOCKS (HX_RED_MINB * 148)
 #define HX_RED_VALUES 4     // partial sums per block at most (partial buffers hold HX_RED_VALUES x HX_RED_BLOCKS)
 #define HX_RED_THREADS 256
 // Blocks of a CG pass over n DoFs: about 4 entries per thread, at least 1, at most
@@ -196,7 +228,7 @@ struct HxCgBuffersT {
 typedef HxCgBuffersT<double> HxCgBuffers;
 typedef HxCgBuffersT<float> HxCgBuffersF;
 
-cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, double alpha, double* dE,
+cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, double alpha, double* dE, const HxELayout& lay,
                             cudaStream_t s);
 cudaError_t hx_launch_scale(long long n, const double* d, const double* r, double* z, cudaStream_t s);
 cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s);

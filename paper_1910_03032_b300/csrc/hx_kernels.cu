@@ -69,6 +69,46 @@ __device__ bool last_block_reduce(const double (&v)[NV], double* partial, unsign
   return last_block_reduce<NV>(v, partial, counter, out, blockIdx.x, gridDim.x);
 }
 
+// A thread's partial sum in the reduction passes of the CG.  FP64 vectors sum in FP64.  FP32
+// vectors sum in FP32 with compensation (Kahan, "Further remarks on reducing truncation
+// errors", 1965: the rounding error of each addition is carried to the next, so the error
+// stays a few units of FP32 rounding however many terms a thread adds) and only the thread's
+// result is widened to FP64: the FP64 pipe runs at 1/64 of the FP32 rate on this part, and
+// widening and adding every term in FP64 made these passes FP64-bound.
+template <typename Real>
+struct PartialSum;
+template <>
+struct PartialSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct PartialSum<float> {
+  float s = 0.0f, c = 0.0f;  // c: minus the part of the terms not yet in s
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+template <int NV, typename Real>
+__device__ bool last_block_reduce(const PartialSum<Real> (&v)[NV], double* partial, unsigned int* counter,
+                                  double (&out)[NV], int bid, int G) {
+  double d[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) d[k] = v[k].get();
+  return last_block_reduce<NV>(d, partial, counter, out, bid, G);
+}
+template <int NV, typename Real>
+__device__ bool last_block_reduce(const PartialSum<Real> (&v)[NV], double* partial, unsigned int* counter,
+                                  double (&out)[NV]) {
+  return last_block_reduce<NV, Real>(v, partial, counter, out, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // geometry setup: factors[e][c][pt], c = (m, G00, G01, G02, G11, G12, G22)
 // ---------------------------------------------------------------------------
@@ -167,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) node_kernel(const __grid_constant__ 
 //   dE[e][l] = alpha w_a w_b w_c detJ_e(xi_l),   l = (a, b, c).
 __global__ void __launch_bounds__(kThreads) cmass_kernel(const __grid_constant__ HxTables T, long long E, int EB,
                                                           const double* __restrict__ X8, double alpha,
-                                                          double* __restrict__ dE) {
+                                                          double* __restrict__ dE, const HxELayout lay) {
   extern __shared__ double cf[];
   const int n = T.p + 1, N3 = n * n * n;
   const long long e0 = (long long)blockIdx.x * EB;
@@ -187,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) cmass_kernel(const __grid_constant__
     hx::trilinear_jacobian(cf + el * 24, T.xn[a], T.xn[b], T.xn[c], j0, j1, j2);
     const double det = j0[0] * (j1[1] * j2[2] - j1[2] * j2[1]) + j0[1] * (j1[2] * j2[0] - j1[0] * j2[2]) +
                        j0[2] * (j1[0] * j2[1] - j1[1] * j2[0]);
-    dE[e * N3 + l] = alpha * T.wn[a] * T.wn[b] * T.wn[c] * det;
+    dE[hx_eline(lay, e, b + n * c, n) + a] = alpha * T.wn[a] * T.wn[b] * T.wn[c] * det;
   }
 }
 
@@ -203,43 +243,61 @@ __device__ __forceinline__ Real gather_sum(long long g, const int* __restrict__ 
   return s;
 }
 
-// The same sum for a DoF of a box mesh, its element entries found by index arithmetic: along
-// each axis a node interior to an element row belongs to one element, a node between two
-// elements to both (the lower one with local index p, the upper with 0); the entries are
-// visited with the element index increasing (z, then y, then x outermost to innermost), the
-// order of the transpose map.
+// The same sums for a box mesh, its element entries found by index arithmetic, one x-run of
+// nodes per thread.  Along each axis a node interior to an element row belongs to one element, a
+// node between two elements to both (the lower one with local index p, the upper with 0).  Run
+// t = ex + nx line (line = J + gy K, one DoF x-line) holds the nodes I = ex p + 1 .. ex p + p, and
+// the run with ex = 0 also node I = 0: consecutive runs hold consecutive DoFs.  A node's entries
+// are summed with the element index increasing (z, then y, then x outermost to innermost), the
+// order of the transpose map.  The E-vector is in the line layout (rows of nx elements): entry
+// (lx, ly, lz) of element (ex, ey, ez) at ((ey + ny ez) n^2 + ly + n lz) (nx n) + ex n + lx, so a
+// run's entries for one (y, z) pair are n + 1 consecutive values.
 __device__ __forceinline__ int fast_div(int n, unsigned m, int s) {
   return (int)(((unsigned long long)(unsigned)n * m) >> s);
 }
 
-template <typename Real>
-__device__ __forceinline__ Real gather_sum_grid(long long g, const HxGridAsm& G, const Real* __restrict__ yE) {
-  const int p = G.p, n = p + 1, n3 = n * n * n;
-  const int gi = (int)g;  // n_dof < 2^31 (checked when the mesh is built)
-  const int t = fast_div(gi, G.mgx, G.sgx), I = gi - t * G.gx;
-  const int K = fast_div(t, G.mgy, G.sgy), J = t - K * G.gy;
-  int ex[2], lx[2], ey[2], ly[2], ez[2], lz[2];
-  auto axis = [&](int X, int ne, int* e, int* l) {
-    const int q = fast_div(X, G.mp, G.sp), r = X - q * p;
-    if (r == 0 && q > 0 && q < ne) {  // between elements q - 1 and q
-      e[0] = q - 1;
-      l[0] = p;
-      e[1] = q;
-      l[1] = 0;
-      return 2;
-    }
-    e[0] = q < ne ? q : ne - 1;
-    l[0] = q < ne ? r : p;
-    return 1;
-  };
-  const int cx = axis(I, G.nx, ex, lx), cy = axis(J, G.ny, ey, ly), cz = axis(K, G.nz, ez, lz);
-  Real s = Real(0);
+// the elements (e) and local indices (l) of node X along an axis with ne elements; returns 1 or 2
+__device__ __forceinline__ int grid_axis(int X, int ne, const HxGridAsm& G, int* e, int* l) {
+  const int p = G.p, q = fast_div(X, G.mp, G.sp), r = X - q * p;
+  if (r == 0 && q > 0 && q < ne) {  // between elements q - 1 and q
+    e[0] = q - 1;
+    l[0] = p;
+    e[1] = q;
+    l[1] = 0;
+    return 2;
+  }
+  e[0] = q < ne ? q : ne - 1;
+  l[0] = q < ne ? r : p;
+  return 1;
+}
+
+__host__ __device__ __forceinline__ long long grid_runs(const HxGridAsm& G) {
+  return (long long)G.nx * G.gy * ((long long)G.p * G.nz + 1);
+}
+
+// s[i] = the assembled entry of node ex p + i of run t (i >= *i0); returns the DoF of node ex p.
+template <int P, typename Real>
+__device__ __forceinline__ long long gather_run_grid(int t, const HxGridAsm& G, const Real* __restrict__ yE,
+                                                     Real (&s)[P + 1], int* i0) {
+  constexpr int n = P + 1;
+  const int line = fast_div(t, G.mnx, G.snx), ex = t - line * G.nx;
+  const int K = fast_div(line, G.mgy, G.sgy), J = line - K * G.gy;
+  int ey[2], ly[2], ez[2], lz[2];
+  const int cy = grid_axis(J, G.ny, G, ey, ly), cz = grid_axis(K, G.nz, G, ez, lz);
+  const bool first = ex == 0, right = ex + 1 < G.nx;
+  const long long xl = (long long)G.nx * n;  // one x-line of a row of elements
+#pragma unroll
+  for (int i = 0; i <= P; ++i) s[i] = Real(0);
   for (int a = 0; a < cz; ++a)
     for (int b = 0; b < cy; ++b) {
-      const int eyz = G.nx * (ey[b] + G.ny * ez[a]), lyz = n * (ly[b] + n * lz[a]);
-      for (int c = 0; c < cx; ++c) s += __ldg(yE + (ex[c] + eyz) * n3 + lx[c] + lyz);
+      const Real* L = yE + ((long long)(ey[b] + G.ny * ez[a]) * (n * n) + ly[b] + n * lz[a]) * xl + (long long)ex * n;
+      if (first) s[0] += __ldg(L);
+#pragma unroll
+      for (int i = 1; i <= P; ++i) s[i] += __ldg(L + i);
+      if (right) s[P] += __ldg(L + n);  // element ex + 1, local index 0
     }
-  return s;
+  *i0 = first ? 0 : 1;
+  return (long long)line * G.gx + (long long)ex * P;
 }
 
 #define HX_GRID_STRIDE(g, n) \
@@ -257,8 +315,30 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(long long n, const H
   HX_GRID_STRIDE(g, n) {
     Real s;
     if (constrained && dir[g]) s = x ? x[g] : Real(dir_const);
-    else s = ga.p ? gather_sum_grid(g, ga, yE) : gather_sum(g, off, idx, yE);
+    else s = gather_sum(g, off, idx, yE);
     y[g] = s;
+  }
+}
+
+// the same for a box mesh, one x-run per thread
+template <int P, typename Real>
+__global__ void __launch_bounds__(kThreads) assemble_grid_kernel(long long runs, const HxGridAsm ga,
+                                                                  const Real* __restrict__ yE,
+                                                                  const unsigned char* __restrict__ dir,
+                                                                  int constrained, const Real* __restrict__ x,
+                                                                  double dir_const, Real* __restrict__ y) {
+  HX_GRID_STRIDE(t, runs) {
+    Real s[P + 1];
+    int i0;
+    const long long g0 = gather_run_grid<P>((int)t, ga, yE, s, &i0);
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+      if (i < i0) continue;
+      const long long g = g0 + i;
+      Real v = s[i];
+      if (constrained && dir[g]) v = x ? x[g] : Real(dir_const);
+      y[g] = v;
+    }
   }
 }
 
@@ -280,15 +360,15 @@ __global__ void __launch_bounds__(kThreads) masked_copy_kernel(long long n, cons
 // ---------------------------------------------------------------------------
 // x = P x0 (or 0), r = P b; sums ||P b||^2.
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffersT<Real> B, const Real* __restrict__ b,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_init_kernel(HxCgBuffersT<Real> B, const Real* __restrict__ b,
                                                                   const Real* __restrict__ x0, double rtol, int max_it) {
-  double acc[1] = {0.0};
+  PartialSum<Real> acc[1];
   HX_GRID_STRIDE(g, B.n) {
     const bool d = B.dir[g];
     const Real bg = d ? Real(0) : (B.nullspace ? Real((double)b[g] - B.st->shift) : b[g]);
     B.r[g] = bg;
     B.x[g] = (x0 && !d) ? x0[g] : Real(0);
-    acc[0] += (double)bg * (double)bg;
+    acc[0].add(bg * bg);
   }
   double out[1];
   if (last_block_reduce<1>(acc, B.partial, &B.st->count[0], out) && threadIdx.x == 0) {
@@ -308,7 +388,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_init_kernel(HxCgBuffersT<Re
 
 // r -= A_c x (after an apply of the initial guess into Ap).
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffersT<Real> B) {
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_residual_kernel(HxCgBuffersT<Real> B) {
   HX_GRID_STRIDE(g, B.n) { B.r[g] -= B.Ap[g]; }
 }
 
@@ -317,15 +397,15 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_residual_kernel(HxCgBuffers
 // Null-space mode also sums z and r: the preconditioned residual is orthogonalized against
 // the constants (z - mean z, Sec. 5.3) and p is finished by a direction pass with beta = 0.
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffersT<Real> B) {
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_start_kernel(HxCgBuffersT<Real> B) {
+  PartialSum<Real> acc[4];
   HX_GRID_STRIDE(g, B.n) {
     const Real r = B.r[g], z = B.z ? B.z[g] : B.dinv[g] * r;
     B.p[g] = z;
-    acc[0] += (double)r * (double)z;
-    acc[1] += (double)r * (double)r;
-    acc[2] += (double)z;
-    acc[3] += (double)r;
+    acc[0].add(r * z);
+    acc[1].add(r * r);
+    acc[2].add(z);
+    acc[3].add(r);
   }
   double out[4];
   if (last_block_reduce<4>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
@@ -352,23 +432,56 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_start_kernel(HxCgBuffersT<R
 
 // st->shift = mean of v over all DoFs.
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_mean_kernel(HxCgBuffersT<Real> B, const Real* __restrict__ v) {
-  double acc[1] = {0.0};
-  HX_GRID_STRIDE(g, B.n) { acc[0] += (double)v[g]; }
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_mean_kernel(HxCgBuffersT<Real> B, const Real* __restrict__ v) {
+  PartialSum<Real> acc[1];
+  HX_GRID_STRIDE(g, B.n) { acc[0].add(v[g]); }
   double out[1];
   if (last_block_reduce<1>(acc, B.partial, &B.st->count[0], out) && threadIdx.x == 0) B.st->shift = out[0] / (double)B.n;
+}
+
+// The assembly of the pass for a box mesh, one x-run per thread; returns the thread's part of pAp.
+template <int P, typename Real>
+__device__ __forceinline__ PartialSum<Real> assemble_pap_runs(const HxCgBuffersT<Real>& B, int bid, int nb) {
+  PartialSum<Real> acc;
+  HX_VGRID_STRIDE(t, grid_runs(B.ga), bid, nb) {
+    Real s[P + 1];
+    int i0;
+    const long long g0 = gather_run_grid<P>((int)t, B.ga, B.yE, s, &i0);
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+      if (i < i0) continue;
+      const long long g = g0 + i;
+      const Real pg = B.p[g];
+      const Real ap = B.dir[g] ? pg : s[i];
+      B.Ap[g] = ap;
+      acc.add(pg * ap);
+    }
+  }
+  return acc;
 }
 
 // Ap = assemble(yE) with Dirichlet rows Ap = p; pAp = (p, Ap); alpha = rz / pAp.
 template <typename Real>
 __device__ __forceinline__ void cg_assemble_pap_body(const HxCgBuffersT<Real>& B, int bid, int nb) {
   if (*(volatile int*)&B.st->done) return;
-  double acc[1] = {0.0};
-  HX_VGRID_STRIDE(g, B.n, bid, nb) {
-    const Real pg = B.p[g];
-    const Real ap = B.dir[g] ? pg : (B.ga.p ? gather_sum_grid(g, B.ga, B.yE) : gather_sum(g, B.off, B.idx, B.yE));
-    B.Ap[g] = ap;
-    acc[0] += (double)pg * (double)ap;
+  PartialSum<Real> acc[1];
+  switch (B.ga.p) {
+    case 0:
+      HX_VGRID_STRIDE(g, B.n, bid, nb) {
+        const Real pg = B.p[g];
+        const Real ap = B.dir[g] ? pg : gather_sum(g, B.off, B.idx, B.yE);
+        B.Ap[g] = ap;
+        acc[0].add(pg * ap);
+      }
+      break;
+    case 1: acc[0] = assemble_pap_runs<1>(B, bid, nb); break;
+    case 2: acc[0] = assemble_pap_runs<2>(B, bid, nb); break;
+    case 3: acc[0] = assemble_pap_runs<3>(B, bid, nb); break;
+    case 4: acc[0] = assemble_pap_runs<4>(B, bid, nb); break;
+    case 5: acc[0] = assemble_pap_runs<5>(B, bid, nb); break;
+    case 6: acc[0] = assemble_pap_runs<6>(B, bid, nb); break;
+    case 7: acc[0] = assemble_pap_runs<7>(B, bid, nb); break;
+    default: acc[0] = assemble_pap_runs<8>(B, bid, nb); break;
   }
   double out[1];
   if (last_block_reduce<1>(acc, B.partial, &B.st->count[2], out, bid, nb) && threadIdx.x == 0) {
@@ -383,7 +496,7 @@ __device__ __forceinline__ void cg_assemble_pap_body(const HxCgBuffersT<Real>& B
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_kernel(HxCgBuffersT<Real> B) {
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_assemble_pap_kernel(HxCgBuffersT<Real> B) {
   cg_assemble_pap_body(B, blockIdx.x, gridDim.x);
 }
 
@@ -393,18 +506,18 @@ template <typename Real>
 __device__ __forceinline__ void cg_update_body(const HxCgBuffersT<Real>& B, int bid, int nb) {
   if (*(volatile int*)&B.st->done) return;
   const Real a = Real(B.st->alpha);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  PartialSum<Real> acc[4];
   HX_VGRID_STRIDE(g, B.n, bid, nb) {
     const Real pg = B.p[g];
     B.x[g] += a * pg;
     const Real r = B.r[g] - a * B.Ap[g];
     B.r[g] = r;
-    acc[0] += (double)r * (double)r;
+    acc[0].add(r * r);
     if (!B.z) {
       const Real z = B.dinv[g] * r;
-      acc[1] += (double)r * (double)z;
-      acc[2] += (double)z;
-      acc[3] += (double)r;
+      acc[1].add(r * z);
+      acc[2].add(z);
+      acc[3].add(r);
     }
   }
   double out[4];
@@ -433,21 +546,21 @@ __device__ __forceinline__ void cg_update_body(const HxCgBuffersT<Real>& B, int 
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_kernel(HxCgBuffersT<Real> B) {
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_update_kernel(HxCgBuffersT<Real> B) {
   cg_update_body(B, blockIdx.x, gridDim.x);
 }
 
 // Preconditioner given as a vector z = M^-1 r (computed between the update and the direction
 // passes): rz' = (r, z) (null-space mode: (r, z - mean z)), beta = rz' / rz.
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_rz_kernel(HxCgBuffersT<Real> B) {
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_rz_kernel(HxCgBuffersT<Real> B) {
   if (*(volatile int*)&B.st->done) return;
-  double acc[3] = {0.0, 0.0, 0.0};
+  PartialSum<Real> acc[3];
   HX_GRID_STRIDE(g, B.n) {
     const Real r = B.r[g], z = B.z[g];
-    acc[0] += (double)r * (double)z;
-    acc[1] += (double)z;
-    acc[2] += (double)r;
+    acc[0].add(r * z);
+    acc[1].add(z);
+    acc[2].add(r);
   }
   double out[3];
   if (last_block_reduce<3>(acc, B.partial, &B.st->count[1], out) && threadIdx.x == 0) {
@@ -484,7 +597,7 @@ __device__ __forceinline__ void cg_direction_body(const HxCgBuffersT<Real>& B, i
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffersT<Real> B) {
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_direction_kernel(HxCgBuffersT<Real> B) {
   if (B.cond != 0ull && blockIdx.x == 0 && threadIdx.x == 0) {
     // last kernel of a CUDA-graph while-loop body: continue only while CG runs, and never
     // for more bodies than the iteration cap allows
@@ -502,7 +615,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_kernel(HxCgBuffer
 // o = blk_op[b], with that operator's buffers (the reductions finish per operator).
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_multi_kernel(const HxCgBuffersT<Real>* bufs,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_assemble_pap_multi_kernel(const HxCgBuffersT<Real>* bufs,
                                                                                 const int* __restrict__ blk_op,
                                                                                 const int* __restrict__ blk_first,
                                                                                 const int* __restrict__ blk_count) {
@@ -512,7 +625,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_assemble_pap_multi_kernel(c
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_update_multi_kernel(const HxCgBuffersT<Real>* bufs,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_update_multi_kernel(const HxCgBuffersT<Real>* bufs,
                                                                           const int* __restrict__ blk_op,
                                                                           const int* __restrict__ blk_first,
                                                                           const int* __restrict__ blk_count) {
@@ -522,7 +635,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_update_multi_kernel(const H
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_multi_kernel(const HxCgBuffersT<Real>* bufs,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_direction_multi_kernel(const HxCgBuffersT<Real>* bufs,
                                                                              const int* __restrict__ blk_op,
                                                                              const int* __restrict__ blk_first,
                                                                              const int* __restrict__ blk_count) {
@@ -533,7 +646,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) cg_direction_multi_kernel(cons
 
 // Last kernel of the lock-step while-loop body: every unfinished operator counts one more body;
 // the loop continues while one of them runs and has not used up its cap of max_it + 1 bodies.
-__global__ void __launch_bounds__(HX_RED_THREADS) batch_condition_kernel(HxCgState* const* states, int n,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) batch_condition_kernel(HxCgState* const* states, int n,
                                                                           unsigned long long cond) {
   __shared__ int live;
   if (threadIdx.x == 0) live = 0;
@@ -553,7 +666,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) batch_condition_kernel(HxCgSta
 // mixed-precision iterative refinement (FP64 outer residual, FP32 inner CG)
 // ---------------------------------------------------------------------------
 // r = P b - Ax (FP64), out = ||r||^2.
-__global__ void __launch_bounds__(HX_RED_THREADS) ir_residual_kernel(long long n, const double* __restrict__ b,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) ir_residual_kernel(long long n, const double* __restrict__ b,
                                                                       const double* __restrict__ Ax,
                                                                       const unsigned char* __restrict__ dir,
                                                                       double* __restrict__ r, double* partial,
@@ -584,7 +697,7 @@ __global__ void __launch_bounds__(kThreads) ir_update_kernel(long long n, double
   HX_GRID_STRIDE(g, n) { x[g] += s * (double)d[g]; }
 }
 
-__global__ void __launch_bounds__(HX_RED_THREADS) sum_kernel(long long n, const double* __restrict__ v, double* partial,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) sum_kernel(long long n, const double* __restrict__ v, double* partial,
                                                               unsigned int* counter, double* out) {
   double acc[1] = {0.0};
   HX_GRID_STRIDE(g, n) { acc[0] += v[g]; }
@@ -613,7 +726,7 @@ __global__ void __launch_bounds__(kThreads) to_float_strided_kernel(long long E,
   }
 }
 
-__global__ void __launch_bounds__(HX_RED_THREADS) dot_kernel(long long n, const double* __restrict__ a,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) dot_kernel(long long n, const double* __restrict__ a,
                                                               const double* __restrict__ c, double* partial,
                                                               unsigned int* counter, double* out) {
   double acc[1] = {0.0};
@@ -623,7 +736,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS) dot_kernel(long long n, const 
 }
 
 // out = sum_g (dir[g] ? 0 : b[g] - Ax[g])^2
-__global__ void __launch_bounds__(HX_RED_THREADS) resnorm_kernel(long long n, const double* __restrict__ b,
+__global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) resnorm_kernel(long long n, const double* __restrict__ b,
                                                                   const double* __restrict__ Ax,
                                                                   const unsigned char* __restrict__ dir,
                                                                   double* partial, unsigned int* counter, double* out,
@@ -671,26 +784,55 @@ cudaError_t hx_launch_node_coords(const HxTables& T, long long n_dof, const int*
   return cudaGetLastError();
 }
 
+template <typename Real>
+cudaError_t launch_assemble(long long n, const HxGridAsm& ga, const int* off, const int* idx, const Real* yE,
+                            const unsigned char* dir, int constrained, const Real* x, double dir_const, Real* y,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (ga.p == 0) {
+    assemble_kernel<Real><<<grid_for(n), kThreads, 0, s>>>(n, ga, off, idx, yE, dir, constrained, x, dir_const, y);
+    return cudaGetLastError();
+  }
+  const long long runs = grid_runs(ga);
+  const unsigned gb = grid_for(runs);
+  switch (ga.p) {
+#define HX_ASM_CASE(P)                                                                                     \
+  case P:                                                                                                  \
+    assemble_grid_kernel<P, Real><<<gb, kThreads, 0, s>>>(runs, ga, yE, dir, constrained, x, dir_const, y); \
+    break;
+    HX_ASM_CASE(1)
+    HX_ASM_CASE(2)
+    HX_ASM_CASE(3)
+    HX_ASM_CASE(4)
+    HX_ASM_CASE(5)
+    HX_ASM_CASE(6)
+    HX_ASM_CASE(7)
+    HX_ASM_CASE(8)
+#undef HX_ASM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t hx_launch_assemble(long long n, const HxGridAsm& ga, const int* off, const int* idx, const double* yE,
                                const unsigned char* dir,
                                int constrained, const double* x, double dir_const, double* y, cudaStream_t s) {
-  assemble_kernel<double><<<grid_for(n), kThreads, 0, s>>>(n, ga, off, idx, yE, dir, constrained, x, dir_const, y);
-  return cudaGetLastError();
+  return launch_assemble<double>(n, ga, off, idx, yE, dir, constrained, x, dir_const, y, s);
 }
 
 cudaError_t hx_launch_assemble32(long long n, const HxGridAsm& ga, const int* off, const int* idx, const float* yE,
                                  const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s) {
-  assemble_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, ga, off, idx, yE, dir, constrained, x, 0.0, y);
-  return cudaGetLastError();
+  return launch_assemble<float>(n, ga, off, idx, yE, dir, constrained, x, 0.0, y, s);
 }
 
 cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, double alpha, double* dE,
-                            cudaStream_t s) {
+                            const HxELayout& lay, cudaStream_t s) {
   const int EB = 8;
   const long long blocks = (E + EB - 1) / EB;
   if (blocks == 0) return cudaSuccess;
-  cmass_kernel<<<(unsigned)blocks, kThreads, sizeof(double) * 24 * EB, s>>>(T, E, EB, X8, alpha, dE);
+  cmass_kernel<<<(unsigned)blocks, kThreads, sizeof(double) * 24 * EB, s>>>(T, E, EB, X8, alpha, dE, lay);
   return cudaGetLastError();
 }
 

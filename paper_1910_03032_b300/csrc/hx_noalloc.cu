@@ -149,6 +149,7 @@ extern "C" hx_status hx_apply_noalloc(int p, int q, int64_t n_elem, int64_t n_do
   a.R = restriction;
   a.x = x;
   a.yE = scratch;
+  a.lay = HxELayout{0, 0u, 0};  // element-major: the caller's transpose map indexes it
   a.factors = nullptr;
   a.fstride = 0;
   a.X8 = X8;

@@ -102,9 +102,11 @@ def test_apply_is_bitwise_reproducible(hx):
 @pytest.mark.parametrize("p,q,shape", [(1, 3, (3, 2, 2)), (2, 4, (4, 3, 5)), (3, 4, (3, 3, 2)), (4, 6, (5, 4, 3)),
                                        (5, 7, (2, 3, 2)), (8, 10, (2, 2, 3)), (3, 5, (1, 1, 1)), (2, 3, (7, 1, 1))])
 def test_box_mesh_assembly_equals_transpose_map(hx, p, q, shape):
-    """A box mesh assembles by index arithmetic, a general mesh through its transpose map: the
-    same mesh built both ways gives bit-identical FP64 and FP32 applies, diagonals and solves
-    (the arithmetic visits a DoF's element entries in the map's order)."""
+    """A box mesh assembles by index arithmetic (one x-run of nodes per thread, E-vectors in the
+    line layout), a general mesh through its transpose map: the same mesh built both ways gives
+    bit-identical FP64 and FP32 applies (the arithmetic visits a DoF's element entries in the
+    map's order).  The solves agree to rounding: the CG inner products are summed run by run on
+    the box mesh and DoF by DoF on the general one."""
     V, EV, om = case(shape, p, q=q)
     box = hx.Mesh.structured(*shape, p, q, V)
     gen = hx.Mesh.general(p, q, V, EV, om.n_dof, om.restriction, om.dirichlet.astype(np.uint8))
@@ -115,8 +117,12 @@ def test_box_mesh_assembly_equals_transpose_map(hx, p, q, shape):
         assert torch.equal(a, b)
     a, b = (o.apply_f32(x.float()) for o in ops)
     assert torch.equal(a, b)
+    for constrained in (False, True):
+        a, b = (o.diagonal(constrained) for o in ops)
+        assert torch.equal(a, b)
     (xa, ia), (xb, ib) = (o.solve(x, rtol=1e-10) for o in ops)
-    assert ia["iterations"] == ib["iterations"] and torch.equal(xa, xb)
+    assert abs(ia["iterations"] - ib["iterations"]) <= 1
+    assert float((xa - xb).norm() / xb.norm()) < 1e-8
 
 
 def test_general_mesh_with_permuted_numbering(hx):
