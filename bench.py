@@ -487,6 +487,14 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
     n = p + 1
     geo = 7 * 4 * q ** 3 * E if args.geom == "stored" else 24 * 8 * E
     bytes32 = 8 * n_dof + 4 * n ** 3 * E + geo
+    # the element kernel alone (its launches timed with CUDA events by the autotuner on this
+    # operator): x in, restriction and factors in, E-vector out
+    k_ms = tune_ms[kind] if 0 <= kind < len(tune_ms) and tune_ms[kind] > 0 else None
+    kbytes = 4 * n_dof + 8 * n ** 3 * E + geo
+    kernel_only = None if k_ms is None else {
+        "ms": k_ms, "alg_bytes_per_launch": kbytes, "achieved": kbytes / (k_ms * 1e-3) / 1e9,
+        "frac": kbytes / (k_ms * 1e-3) / 1e9 / HBM_GBS,
+        "timing": "mean of 3 back-to-back launches after 1 warm-up, CUDA events (the FP32 kernel autotuner)"}
     return {"solve_time_s": t_mix, "speedup_vs_fp64": t_fp64 / t_mix, "refinements": info["refinements"],
             "inner_iterations": info["iterations"], "inner_rtol": args.inner_rtol,
             "rel_residual_fp64": info["rel_residual"], "rel_diff_vs_fp64_solution": err,
@@ -496,7 +504,8 @@ def measure_mixed(hx, torch, op, b, x64, args, t_fp64, world):
             "roofline_f32": {"bound": "hbm", "achieved": bytes32 / t32 / 1e9, "peak": HBM_GBS, "unit": "GB/s",
                              "frac": bytes32 / t32 / 1e9 / HBM_GBS, "alg_bytes_per_launch": bytes32,
                              "kernel": f"FP32 element kernel ({F32_KERNELS.get(kind, kind)}, P={p}, Q={q}) "
-                                       "+ assembly, timed together"}}
+                                       "+ assembly, timed together",
+                             "element_kernel_only": kernel_only}}
 
 
 def batch_specs(seed=4444, n=64):

@@ -814,13 +814,17 @@ __global__ void __launch_bounds__(NT) grad_kernel(const __grid_constant__ HxTabl
 // Diagonal of the element matrices, sum-factorized:
 // diag[k][j][i] = sum_{c,b,a} m (BB_ai BB_bj BB_ck) + G00 DD_ai BB_bj BB_ck + G11 BB_ai DD_bj BB_ck
 //   + G22 BB_ai BB_bj DD_ck + 2 G01 BD_ai BD_bj BB_ck + 2 G02 BD_ai BB_bj BD_ck + 2 G12 BB_ai BD_bj BD_ck
-// with BB = B.B, DD = D.D, BD = B.D (entrywise) and factors at point (a, b, c).
+// with BB = B.B, DD = D.D, BD = B.D (entrywise) and factors at point (a, b, c).  Terms that meet
+// the same tables in the remaining directions are summed as soon as they do: after the
+// a-contraction six sums remain (m and G00 share BB_bj BB_ck), after the b-contraction three
+// (one per table along c), so the b and c stages contract 6 and 3 arrays instead of 7.
 template <typename Real, int P, int Q, int NE, int NT, int GEOM, bool NUF>
 __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTablesT<Real> T, const HxDiagArgsT<Real> A) {
   constexpr int N = P + 1, N3 = N * N * N, Q3 = Q * Q * Q;
-  constexpr int F1 = 7 * Q * Q * N, F2 = 7 * Q * N * N;
-  constexpr int FA = (7 * Q3 > F2) ? 7 * Q3 : F2;  // factors, later reused by stage-2 output
-  constexpr int PER = FA + F1;
+  constexpr int X1 = Q * Q * N;                       // one stage-1 array [c][b][i]
+  constexpr int Y1 = Q * N * N;                       // one stage-2 array [c][j][i]
+  constexpr int FA = (7 * Q3 > 3 * Y1) ? 7 * Q3 : 3 * Y1;  // factors, later reused by stage-2 output
+  constexpr int PER = FA + 6 * X1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* smem = reinterpret_cast<Real*>(smem_raw);
   Real* tab = smem + NE * PER;  // BB, DD, BD tables: 3 q n
@@ -867,48 +871,46 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
   const Real* BB = tab;
   const Real* DD = tab + Q * N;
   const Real* BD = tab + 2 * Q * N;
-  // stage 1: contract a -> T1[f][c][b][i]
-  for (int t = tid; t < NE * Q * Q; t += NT) {
-    const int el = t / (Q * Q), cb = t - el * (Q * Q);
+  // stage 1: contract a -> X[s][c][b][i], s = (m + G00, G11, G22, G12 | BB_a or DD_a; G01, G02 | BD_a)
+  for (int t = tid; t < NE * Q * Q * N; t += NT) {
+    const int el = t / (Q * Q * N), r = t - el * (Q * Q * N);
+    const int cb = r / N, i = r - cb * N;
     const Real* F = smem + el * PER + cb * Q;
-    Real* T1 = smem + el * PER + FA + cb * N;
-    for (int i = 0; i < N; ++i) {
-      Real s[7] = {0, 0, 0, 0, 0, 0, 0};
-      for (int a = 0; a < Q; ++a) {
-        const Real bb = BB[a * N + i], dd = DD[a * N + i], bd = BD[a * N + i];
-        s[0] += bb * F[0 * Q3 + a];
-        s[1] += dd * F[1 * Q3 + a];
-        s[2] += bd * F[2 * Q3 + a];
-        s[3] += bd * F[3 * Q3 + a];
-        s[4] += bb * F[4 * Q3 + a];
-        s[5] += bb * F[5 * Q3 + a];
-        s[6] += bb * F[6 * Q3 + a];
-      }
-      for (int f = 0; f < 7; ++f) T1[f * Q * Q * N + i] = s[f];
+    Real s[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const Real bb = BB[a * N + i], dd = DD[a * N + i], bd = BD[a * N + i];
+      s[0] += bb * F[0 * Q3 + a] + dd * F[1 * Q3 + a];
+      s[1] += bb * F[4 * Q3 + a];
+      s[2] += bb * F[6 * Q3 + a];
+      s[3] += bb * F[5 * Q3 + a];
+      s[4] += bd * F[2 * Q3 + a];
+      s[5] += bd * F[3 * Q3 + a];
     }
+    Real* X = smem + el * PER + FA + cb * N + i;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) X[f * X1] = s[f];
   }
   __syncthreads();
-  // stage 2: contract b -> T2[f][c][j][i] (reuses the factor space)
-  for (int t = tid; t < NE * Q * N; t += NT) {
-    const int el = t / (Q * N), r = t - el * (Q * N);
-    const int c = r / N, i = r - c * N;
-    const Real* T1 = smem + el * PER + FA + c * Q * N + i;
-    Real* T2 = smem + el * PER + c * N * N + i;
-    for (int j = 0; j < N; ++j) {
-      Real s[7] = {0, 0, 0, 0, 0, 0, 0};
-      for (int b = 0; b < Q; ++b) {
-        const Real bb = BB[b * N + j], dd = DD[b * N + j], bd = BD[b * N + j];
-        const Real* src = T1 + b * N;
-        s[0] += bb * src[0 * Q * Q * N];
-        s[1] += bb * src[1 * Q * Q * N];
-        s[2] += bd * src[2 * Q * Q * N];
-        s[3] += bb * src[3 * Q * Q * N];
-        s[4] += dd * src[4 * Q * Q * N];
-        s[5] += bd * src[5 * Q * Q * N];
-        s[6] += bb * src[6 * Q * Q * N];
-      }
-      for (int f = 0; f < 7; ++f) T2[f * Q * N * N + j * N] = s[f];
+  // stage 2: contract b -> Y[s][c][j][i] (reusing the factor space), s = (BB_c, DD_c, 2 BD_c terms)
+  for (int t = tid; t < NE * Q * N * N; t += NT) {
+    const int el = t / (Q * N * N), r = t - el * (Q * N * N);
+    const int c = r / (N * N), ji = r - c * (N * N);
+    const int j = ji / N, i = ji - j * N;
+    const Real* X = smem + el * PER + FA + c * Q * N + i;
+    Real s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const Real bb = BB[b * N + j], dd = DD[b * N + j], bd = BD[b * N + j];
+      const Real* src = X + b * N;
+      s0 += bb * src[0 * X1] + dd * src[1 * X1] + Real(2) * bd * src[4 * X1];
+      s1 += bb * src[2 * X1];
+      s2 += bd * src[3 * X1] + bb * src[5 * X1];
     }
+    Real* Y = smem + el * PER + c * N * N + ji;
+    Y[0 * Y1] = s0;
+    Y[1 * Y1] = s1;
+    Y[2 * Y1] = s2;
   }
   __syncthreads();
   // stage 3: contract c -> element diagonal
@@ -916,14 +918,12 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
     const int el = t / N3, l = t - el * N3;
     const int k = l / (N * N), ji = l - k * N * N;
     const long long e = e0 + el;
-    const Real* T2 = smem + el * PER + ji;
+    const Real* Y = smem + el * PER + ji;
     Real s = Real(0);
+#pragma unroll
     for (int c = 0; c < Q; ++c) {
-      const Real bb = BB[c * N + k], dd = DD[c * N + k], bd = BD[c * N + k];
-      const Real* src = T2 + c * N * N;
-      const int st = Q * N * N;
-      s += bb * (src[0] + src[1 * st] + src[4 * st]) + dd * src[6 * st] + Real(2) * bd * (src[3 * st] + src[5 * st]) +
-           Real(2) * bb * src[2 * st];
+      const Real* src = Y + c * N * N;
+      s += BB[c * N + k] * src[0] + DD[c * N + k] * src[Y1] + Real(2) * BD[c * N + k] * src[2 * Y1];
     }
     if (e < A.E) A.dE[hx_eline(A.lay, e, l / N, N) + l % N] = s;
   }
@@ -1008,9 +1008,9 @@ cudaError_t launch_apply_q(const HxTablesT<Real>& T, const HxApplyArgsT<Real>& A
 template <typename Real, int P, int Q, int GEOM, bool NUF>
 cudaError_t launch_diag_impl(const HxTablesT<Real>& T, const HxDiagArgsT<Real>& A, cudaStream_t s) {
   constexpr int N = P + 1, NE = Config<P, Q>::NE_DIAG, NT = 128;
-  constexpr int F1 = 7 * Q * Q * N, F2 = 7 * Q * N * N;
-  constexpr int FA = (7 * Q * Q * Q > F2) ? 7 * Q * Q * Q : F2;
-  const size_t shmem = sizeof(Real) * (size_t)(NE * (FA + F1) + 3 * Q * N + NE * 24);
+  constexpr int Y3 = 3 * Q * N * N;
+  constexpr int FA = (7 * Q * Q * Q > Y3) ? 7 * Q * Q * Q : Y3;
+  const size_t shmem = sizeof(Real) * (size_t)(NE * (FA + 6 * Q * Q * N) + 3 * Q * N + NE * 24);
   auto k = diag_kernel<Real, P, Q, NE, NT, GEOM, NUF>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
   if (err != cudaSuccess) return err;
