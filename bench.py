@@ -64,17 +64,19 @@ def _measured_hbm_gbs(fallback=6400.0):
 
 
 HBM_GBS = _measured_hbm_gbs()
-# FP64 peak of the B300: 2 DFMA per clock per SM (a throughput probe measured
-# 565 G DFMA/s at ~1.94 GHz: 1.97 per clock per SM) x 148 SMs x 2032 MHz x 2 flops.
+# FP64 peak of the B300 from the unit count: 2 DFMA per clock per SM x 148 SMs x 2032 MHz x
+# 2 flops (the library's FMA-rate probe reaches 506 G DFMA/s = 1.68 per clock per SM; every
+# default run measures it again and reports the fraction of both).
 FP64_PEAK_TFLOPS = 148 * 2.032e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one element-kernel launch, keyed by
-# (p, N, geom): the 32^3 capture of the current kernel (493.9 MB read + 28.8 MB written)
-# scaled by the element count (27x at 96^3); traffic grows in proportion to the elements.
-NCU_TRAFFIC = {(4, 96, "stored"): (493.932288e6 + 28.763392e6) * 27}
+# (p, N, geom): the 32^3 capture of the current kernel (16 elements per block, line-layout
+# E-vector; 457.9 MB read + 28.7 MB written) scaled by the element count (27x at 96^3);
+# traffic grows in proportion to the elements.
+NCU_TRAFFIC = {(4, 96, "stored"): (457.918976e6 + 28.729088e6) * 27}
 # sm__pipe_fp64_cycles_active (% of peak sustained) of the same capture: the FP64 pipe's
 # own utilization, which the algorithmic-flop fraction overstates (the even-odd folding
 # executes fewer flops than the algorithmic count)
-NCU_FP64_PIPE = {(4, 96, "stored"): 0.831}
+NCU_FP64_PIPE = {(4, 96, "stored"): 0.828}
 # FP32 element kernels of the mixed-precision solve (include/hx.h HX_F32_*)
 F32_KERNELS = {0: "collocated", 1: "direct_staged", 2: "direct", 3: "mma_bf16", 4: "mma_bf16x3"}
 

@@ -465,10 +465,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_mean_kernel(Hx
 template <int P, typename Real>
 __device__ __forceinline__ PartialSum<Real> assemble_pap_runs(const HxCgBuffersT<Real>& B, int bid, int nb) {
   PartialSum<Real> acc;
-  HX_VGRID_STRIDE(t, grid_runs(B.ga), bid, nb) {
-    Real s[P + 1];
-    int i0;
-    const long long g0 = gather_run_grid<P>((int)t, B.ga, B.yE, s, &i0);
+  auto finish = [&](long long g0, const Real(&s)[P + 1], int i0) {
 #pragma unroll
     for (int i = 0; i <= P; ++i) {
       if (i < i0) continue;
@@ -478,16 +475,25 @@ __device__ __forceinline__ PartialSum<Real> assemble_pap_runs(const HxCgBuffersT
       B.Ap[g] = ap;
       acc.add(pg * ap);
     }
+  };
+  HX_VGRID_STRIDE(t, grid_runs(B.ga), bid, nb) {
+    Real s[P + 1];
+    int i0;
+    const long long g0 = gather_run_grid<P>((int)t, B.ga, B.yE, s, &i0);
+    finish(g0, s, i0);
   }
   return acc;
 }
 
 // Ap = assemble(yE) with Dirichlet rows Ap = p; pAp = (p, Ap); alpha = rz / pAp.
-template <typename Real>
+// PG > 0: a box mesh of order PG (compile-time, so each order gets its own registers);
+// PG = 0: the order read from the buffers (the lock-step kernels over several operators).
+template <int PG, typename Real>
 __device__ __forceinline__ void cg_assemble_pap_body(const HxCgBuffersT<Real>& B, int bid, int nb) {
   if (*(volatile int*)&B.st->done) return;
   PartialSum<Real> acc[1];
-  switch (B.ga.p) {
+  if constexpr (PG > 0) acc[0] = assemble_pap_runs<PG>(B, bid, nb);
+  else switch (B.ga.p) {
     case 0:
       HX_VGRID_STRIDE(g, B.n, bid, nb) {
         const Real pg = B.p[g];
@@ -517,9 +523,9 @@ __device__ __forceinline__ void cg_assemble_pap_body(const HxCgBuffersT<Real>& B
   }
 }
 
-template <typename Real>
+template <int PG, typename Real>
 __global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_assemble_pap_kernel(HxCgBuffersT<Real> B) {
-  cg_assemble_pap_body(B, blockIdx.x, gridDim.x);
+  cg_assemble_pap_body<PG>(B, blockIdx.x, gridDim.x);
 }
 
 // x += alpha p, r -= alpha Ap, z = D^-1 r; rr = (r, r), rz' = (r, z); convergence test.
@@ -687,7 +693,7 @@ __global__ void __launch_bounds__(HX_RED_THREADS, HX_RED_MINB) cg_assemble_pap_m
                                                                                 const int* __restrict__ blk_count) {
   const int o = __ldg(blk_op + blockIdx.x);
   const HxCgBuffersT<Real> B = bufs[o];
-  cg_assemble_pap_body(B, blockIdx.x - __ldg(blk_first + o), __ldg(blk_count + o));
+  cg_assemble_pap_body<0>(B, blockIdx.x - __ldg(blk_first + o), __ldg(blk_count + o));
 }
 
 template <typename Real>
@@ -952,7 +958,18 @@ cudaError_t hx_launch_cg_start(const HxCgBuffersT<Real>& b, cudaStream_t s) {
 }
 template <typename Real>
 cudaError_t hx_launch_cg_assemble_pap(const HxCgBuffersT<Real>& b, cudaStream_t s) {
-  cg_assemble_pap_kernel<Real><<<(unsigned)hx_red_blocks(b.n), HX_RED_THREADS, 0, s>>>(b);
+  const unsigned nb = (unsigned)hx_red_blocks(b.n);
+  switch (b.ga.p) {
+    case 1: cg_assemble_pap_kernel<1, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 2: cg_assemble_pap_kernel<2, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 3: cg_assemble_pap_kernel<3, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 4: cg_assemble_pap_kernel<4, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 5: cg_assemble_pap_kernel<5, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 6: cg_assemble_pap_kernel<6, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 7: cg_assemble_pap_kernel<7, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    case 8: cg_assemble_pap_kernel<8, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+    default: cg_assemble_pap_kernel<0, Real><<<nb, HX_RED_THREADS, 0, s>>>(b); break;
+  }
   return cudaGetLastError();
 }
 template <typename Real>
