@@ -146,6 +146,33 @@ __device__ __forceinline__ void trilinear_coeffs(const double* __restrict__ X8, 
   }
 }
 
+// The same coefficients for the NE elements of a block, one (element, coefficient) pair per
+// thread: the FP64 additions then run as warp instructions with all lanes busy (computed by one
+// thread per element they cost as many FP64 warp instructions per element as there are
+// additions, which made the FP32 kernels with recomputed geometry FP64-pipe bound).  Each
+// coefficient sums its 8 corner terms in corner order, like trilinear_coeffs: the results
+// are the same bits.  Call from all threads; a barrier must follow before geo is read.
+template <typename Real>
+__device__ __forceinline__ void trilinear_coeffs_block(const double* __restrict__ X8, long long e0, long long E,
+                                                       int ne, Real* geo) {
+  for (int t = threadIdx.x; t < ne * 24; t += blockDim.x) {
+    const int el = t / 24, k = t - el * 24, d = k >> 3, m = k & 7;
+    // axes of monomial m = (1, xi1, xi2, xi3, xi1 xi2, xi1 xi3, xi2 xi3, xi1 xi2 xi3) as bits
+    const int axes = (0x76534210 >> (4 * m)) & 7;
+    const long long e = e0 + el;
+    double s = 0.0;
+    if (e < E) {
+      const double* X = X8 + e * 24 + d;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const double x = __ldg(X + c * 3);
+        s += (__popc(axes & ~c) & 1) ? -x : x;  // sign: -1 per axis of the monomial where corner c sits at -1
+      }
+    }
+    geo[el * 24 + k] = Real(0.125 * s);
+  }
+}
+
 // Columns j0 = dx/dxi1, j1 = dx/dxi2, j2 = dx/dxi3 at (x1, x2, x3).
 template <typename Real>
 __device__ __forceinline__ void trilinear_jacobian(const Real* cf, Real x1, Real x2, Real x3, Real (&j0)[3],
@@ -379,12 +406,7 @@ __device__ __forceinline__ void apply_body(const HxTablesT<Real>& T, const HxApp
     for (long long off = (long long)tid * 128; off < bytes; off += (long long)NT * 128)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
   } else {
-    for (int el = tid; el < NE; el += NT) {
-      const long long e = e0 + el;
-      double X8[24];  // corner coordinates stay FP64 until the map coefficients are formed
-      for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
-      trilinear_coeffs(X8, geo + el * 24);
-    }
+    trilinear_coeffs_block(A.X8, e0, A.E, NE, geo);  // corner coordinates stay FP64 until here
   }
   // 1. gather x_E = R x (Dirichlet DoFs read as zero for A_c) and B along x: [k][j][i] -> [k][j][iq]
   for (int t = tid; t < NE * N * N; t += NT) {
@@ -663,12 +685,7 @@ __global__ void __launch_bounds__(NT) load_kernel(const __grid_constant__ HxTabl
   double* geo = smem + NE * R3;
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
-  for (int el = tid; el < NE; el += NT) {
-    const long long e = e0 + el;
-    double X8[24];
-    for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
-    trilinear_coeffs(X8, geo + el * 24);
-  }
+  trilinear_coeffs_block(A.X8, e0, A.E, NE, geo);
   __syncthreads();
   if (tid < NE * Q2) {
     const int cel = tid / Q2, c = tid - cel * Q2;
@@ -711,12 +728,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(const __grid_constant__ HxTabl
   double* geo = smem + NE * R6;
   const long long e0 = (long long)blockIdx.x * NE;
   const int tid = threadIdx.x;
-  for (int el = tid; el < NE; el += NT) {
-    const long long e = e0 + el;
-    double X8[24];
-    for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
-    trilinear_coeffs(X8, geo + el * 24);
-  }
+  trilinear_coeffs_block(A.X8, e0, A.E, NE, geo);
   // 1. gather (Dirichlet entries as zero) and B along x, for u (v = 0) and lam (v = 1)
   for (int t = tid; t < 2 * NE * N * N; t += NT) {
     const int v = t / (NE * N * N), tt = t - v * NE * N * N;
@@ -837,12 +849,7 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
     tab[2 * Q * N + t] = T.B[t] * T.D[t];
   }
   if (GEOM == HX_KGEOM_ONTHEFLY) {
-    for (int el = tid; el < NE; el += NT) {
-      const long long e = e0 + el;
-      double X8[24];
-      for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
-      trilinear_coeffs(X8, geo + el * 24);
-    }
+    trilinear_coeffs_block(A.X8, e0, A.E, NE, geo);
     __syncthreads();
   }
   // factors into shared memory: F[f][c][b][a]

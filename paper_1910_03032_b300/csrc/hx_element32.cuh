@@ -134,12 +134,7 @@ __global__ void __launch_bounds__(NT, MINB)
     for (long long off = (long long)tid * 128; off < bytes; off += (long long)NT * 128)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
   } else if (GEOM == HX_KGEOM_ONTHEFLY) {
-    for (int el = tid; el < NE; el += NT) {
-      const long long e = e0 + el;
-      double X8[24];  // corner coordinates stay FP64 until the map coefficients are formed
-      for (int c = 0; c < 24; ++c) X8[c] = (e < A.E) ? A.X8[e * 24 + c] : 0.0;
-      trilinear_coeffs(X8, geo + el * 24);
-    }
+    trilinear_coeffs_block(A.X8, e0, A.E, NE, geo);  // corner coordinates stay FP64 until here
   }
   __syncthreads();  // the barriers are initialized before anyone waits on them
   // 1. gather x_E = R x (Dirichlet DoFs read as zero for A_c) line by line, and contract the
@@ -287,9 +282,9 @@ __global__ void __launch_bounds__(NT, MINB)
             j2[dd] = J2[dd];
           }
           const float w = w12 * T.wq[kq];
-          float nu = float(A.nu);
+          float nu = A.nu;
           if (NUF) nu = live ? float(__ldg(A.nu_q + e * Q3 + kq * Q2 + c)) : 0.0f;
-          point_factors(j0, j1, j2, float(A.alpha) * w, nu * w, f);
+          point_factors(j0, j1, j2, A.alpha * w, nu * w, f);
         }
         if (!live) {
 #pragma unroll

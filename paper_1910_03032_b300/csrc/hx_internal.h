@@ -38,7 +38,8 @@ struct HxApplyArgsT {
   long long fstride;      // element stride of `factors` (7 q^3, or the padded FP32 stride)
   const double* X8;       // [E][8][3] element corner coordinates (on-the-fly geometry)
   const double* nu_q;     // [E][q^3] per-point viscosity or null (on-the-fly geometry)
-  double alpha, nu;       // Helmholtz coefficients (on-the-fly geometry)
+  T alpha, nu;            // Helmholtz coefficients (on-the-fly geometry), in the kernel's type:
+                          // an FP64 value converted per point costs an FP64-pipe instruction
   int constrained;        // 1: Dirichlet DoFs of x read as zero
   const int* done;        // optional device flag: kernel returns at once when *done != 0
   int* err;               // optional device flag, set to 1 when a bounded wait gives up
@@ -61,7 +62,7 @@ struct HxDiagArgsT {
   long long fstride;      // element stride of `factors`
   const double* X8;
   const double* nu_q;
-  double alpha, nu;
+  T alpha, nu;
   T* dE;                  // element diagonals (an E-vector)
   HxELayout lay;          // its layout
 };

@@ -144,12 +144,7 @@ __global__ void __launch_bounds__(kThreads) geometry_kernel(const __grid_constan
   extern __shared__ double cf[];  // EB x 24
   const int q = T.q, Q2 = q * q, Q3 = Q2 * q;
   const long long e0 = (long long)blockIdx.x * EB;
-  for (int el = threadIdx.x; el < EB; el += blockDim.x) {
-    const long long e = e0 + el;
-    double x8[24];
-    for (int c = 0; c < 24; ++c) x8[c] = (e < E) ? X8[e * 24 + c] : 0.0;
-    hx::trilinear_coeffs(x8, cf + el * 24);
-  }
+  hx::trilinear_coeffs_block(X8, e0, E, EB, cf);
   __syncthreads();
   int nbad = 0;
   for (int t = threadIdx.x; t < EB * Q2; t += blockDim.x) {
@@ -191,12 +186,7 @@ __global__ void __launch_bounds__(kThreads) qpoint_kernel(const __grid_constant_
   extern __shared__ double cf[];
   const int q = T.q, Q3 = q * q * q;
   const long long e0 = (long long)blockIdx.x * EB;
-  for (int el = threadIdx.x; el < EB; el += blockDim.x) {
-    const long long e = e0 + el;
-    double x8[24];
-    for (int c = 0; c < 24; ++c) x8[c] = (e < E) ? X8[e * 24 + c] : 0.0;
-    hx::trilinear_coeffs(x8, cf + el * 24);
-  }
+  hx::trilinear_coeffs_block(X8, e0, E, EB, cf);
   __syncthreads();
   for (int t = threadIdx.x; t < EB * Q3 * 3; t += blockDim.x) {
     const int el = t / (Q3 * 3), r = t - el * Q3 * 3;
@@ -233,12 +223,7 @@ __global__ void __launch_bounds__(kThreads) cmass_kernel(const __grid_constant__
   extern __shared__ double cf[];
   const int n = T.p + 1, N3 = n * n * n;
   const long long e0 = (long long)blockIdx.x * EB;
-  for (int el = threadIdx.x; el < EB; el += blockDim.x) {
-    const long long e = e0 + el;
-    double x8[24];
-    for (int c = 0; c < 24; ++c) x8[c] = (e < E) ? X8[e * 24 + c] : 0.0;
-    hx::trilinear_coeffs(x8, cf + el * 24);
-  }
+  hx::trilinear_coeffs_block(X8, e0, E, EB, cf);
   __syncthreads();
   for (int t = threadIdx.x; t < EB * N3; t += blockDim.x) {
     const int el = t / N3, l = t - el * N3;
