@@ -125,6 +125,17 @@ struct hx_op {
   bool diag_stale = true;
   bool dinv_stale = true;
   bool has_field = false;       // the coefficients include a per-point nu field
+  // Constant-coefficient updates of stored factors: m is linear in alpha and G in nu, so a new
+  // (alpha, nu), both nonzero, rescales the factors in place (rescales: in-place updates since
+  // the geometry kernel last ran, bounded so that rounding cannot build up), and the diagonal is
+  // alpha / alpha_d dm + nu / nu_d dk from its mass and stiffness parts dmk = [dm; dk], computed
+  // once per geometry at (alpha_d, nu_d).
+  double alpha_f = 0, nu_f = 0;  // the coefficients the stored factors hold
+  bool factors_ok = false;       // stored factors computed without a nu field
+  int rescales = 0;
+  double* dmk = nullptr;         // [2][n_dof]
+  double alpha_d = 0, nu_d = 0;
+  bool dmk_ok = false;
   // low-order refined operator (Sec. 5.2) and its Chebyshev-Jacobi inverse (HX_PREC_LOR)
   HxLorMatrix lor = {};
   long long lor_nnz = 0;
@@ -203,6 +214,7 @@ int iteration_launches(const hx_op* op);
 cudaError_t precondition_start(const hx_op* op, cudaStream_t s);
 bool build_while_graph(cudaStream_t s, const std::function<cudaError_t(unsigned long long)>& body,
                        cudaGraphExec_t* out);
+constexpr int kMaxRescales = 64;  // in-place factor rescales before the geometry is recomputed
 constexpr int kChunk = 16;  // CG iterations per launch of the fallback (non-conditional) path
 
 }  // namespace hxc

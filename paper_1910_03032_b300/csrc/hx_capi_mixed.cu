@@ -205,6 +205,7 @@ hx_status ensure_mixed(hx_op* op) {
       d.nu = op->nu;
       d.dE = op->yE32;
       d.lay = m->lay;
+      d.parts = 3;
       HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
       HX_TRY(hx_launch_assemble32(n, m->ga, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
              "FP32 diagonal assembly");

@@ -84,6 +84,7 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->nu_q);
   dfree(op->yE);
   dfree(op->diag);
+  dfree(op->dmk);
   dfree(op->x);
   dfree(op->r);
   dfree(op->p);
@@ -159,10 +160,35 @@ hx_status ensure_diag(hx_op* op, cudaStream_t s, int* nl) {
   d.nu = op->nu;
   d.dE = op->yE;
   d.lay = m->lay;
-  HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
-  HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
-         "diagonal assembly");
-  *nl += 2;
+  d.parts = 3;
+  // stored factors of constant coefficients: the diagonal from its mass and stiffness parts
+  const bool split = op->geom == HX_GEOM_STORED && op->factors_ok && op->alpha_f != 0.0 && op->nu_f != 0.0;
+  if (split) {
+    if (!op->dmk_ok) {
+      hx_status st;
+      if (!op->dmk && (st = dalloc(&op->dmk, 2 * (size_t)m->n_dof, "diagonal parts"))) return st;
+      for (int part = 0; part < 2; ++part) {
+        d.parts = 1 + part;
+        HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
+        HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0,
+                                  op->dmk + part * m->n_dof, s),
+               "diagonal assembly");
+      }
+      *nl += 4;
+      op->alpha_d = op->alpha_f;
+      op->nu_d = op->nu_f;
+      op->dmk_ok = true;
+    }
+    HX_TRY(hx_launch_axpby(m->n_dof, op->alpha / op->alpha_d, op->dmk, op->nu / op->nu_d, op->dmk + m->n_dof, op->diag,
+                           s),
+           "diagonal from its parts");
+    *nl += 1;
+  } else {
+    HX_TRY(diag_launcher(m->p)(m->T, d, op->geom, s), "diagonal kernel");
+    HX_TRY(hx_launch_assemble(m->n_dof, m->ga, m->off, m->idx, op->yE, m->dir, 0, nullptr, 0.0, op->diag, s),
+           "diagonal assembly");
+    *nl += 2;
+  }
   op->diag_stale = false;
   return HX_OK;
 }
@@ -213,7 +239,21 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
   // alpha = 0 with nothing fixed on the boundary: K alone, singular on the constants
   op->singular = (alpha == 0.0 && m->n_dirichlet == 0);
   if (op->geom == HX_GEOM_STORED) {
-    HX_TRY(hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s), "geometry kernel");
+    // constant coefficients, both nonzero before and after: the factors scale in place (a
+    // bounded number of times in a row, then the geometry kernel recomputes them)
+    if (!nu_q && op->factors_ok && op->alpha_f != 0.0 && op->nu_f != 0.0 && alpha != 0.0 && nu != 0.0 &&
+        op->rescales < kMaxRescales) {
+      HX_TRY(hx_launch_scale_factors(m->E, (int)Q3, alpha / op->alpha_f, nu / op->nu_f, op->factors, s),
+             "factor rescale");
+      ++op->rescales;
+    } else {
+      HX_TRY(hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s), "geometry kernel");
+      op->rescales = 0;
+      op->dmk_ok = false;
+    }
+    op->alpha_f = alpha;
+    op->nu_f = nu;
+    op->factors_ok = nu_q == nullptr;
     ++nl;
   } else {
     op->use_field = nu_q != nullptr;

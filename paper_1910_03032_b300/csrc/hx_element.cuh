@@ -871,6 +871,11 @@ __global__ void __launch_bounds__(NT) diag_kernel(const __grid_constant__ HxTabl
         point_factors(j0, j1, j2, alpha_r * w, nu * w, f);
       }
     }
+    if (!(A.parts & 1)) f[0] = Real(0);  // the mass part left out
+    if (!(A.parts & 2)) {               // the stiffness part left out
+#pragma unroll
+      for (int c = 1; c < 7; ++c) f[c] = Real(0);
+    }
 #pragma unroll
     for (int c = 0; c < 7; ++c) smem[el * PER + c * Q3 + pt] = f[c];
   }

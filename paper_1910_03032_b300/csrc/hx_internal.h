@@ -65,6 +65,7 @@ struct HxDiagArgsT {
   T alpha, nu;
   T* dE;                  // element diagonals (an E-vector)
   HxELayout lay;          // its layout
+  int parts;              // terms summed: 1 the mass part (m), 2 the stiffness part (G), 3 both
 };
 typedef HxDiagArgsT<double> HxDiagArgs;
 typedef HxDiagArgsT<float> HxDiagArgsF;
@@ -233,6 +234,11 @@ cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, do
                             cudaStream_t s);
 cudaError_t hx_launch_scale(long long n, const double* d, const double* r, double* z, cudaStream_t s);
 cudaError_t hx_launch_dinv(long long n, const double* diag, const unsigned char* dir, double* dinv, cudaStream_t s);
+// Stored factors [E][7][q^3] after a change of constant coefficients: m *= ra, G *= rk.
+cudaError_t hx_launch_scale_factors(long long E, int Q3, double ra, double rk, double* factors, cudaStream_t s);
+// out = ra a + rk b
+cudaError_t hx_launch_axpby(long long n, double ra, const double* a, double rk, const double* b, double* out,
+                            cudaStream_t s);
 cudaError_t hx_launch_dinv32(long long n, const float* diag, const unsigned char* dir, float* dinv, cudaStream_t s);
 cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
                                   double value, double* dst, cudaStream_t s);

@@ -163,17 +163,45 @@ __global__ void __launch_bounds__(kThreads) geometry_kernel(const __grid_constan
       R1[d] = ad[6] + ad[7] * x1;
       j2[d] = ad[3] + ad[5] * x1 + (ad[6] + ad[7] * x1) * x2;
     }
+    // The rows of detJ J^-1 are the cross products c0 = j1 x j2, c1 = j2 x j0, c2 = j0 x j1
+    // (G = nu w c c^T / detJ).  With j0 = P0 + z R0, j1 = P1 + z R1 and j2 fixed along the
+    // column, c0 and c1 are affine in z, c2 and detJ = j0 . c0 quadratic: their coefficients are
+    // formed once per column, and each point evaluates them (12 + 2 FMAs instead of two
+    // Jacobian columns, nine cross-product entries and a dot product), with 1/detJ by the
+    // Newton-Raphson reciprocal instead of a division.
+    double A0[3], B0[3], A1[3], B1[3], C0[3], C1[3], C2[3], U[3], V[3];
+    hx::cross3(P1, j2, A0);
+    hx::cross3(R1, j2, B0);
+    hx::cross3(j2, P0, A1);
+    hx::cross3(j2, R0, B1);
+    hx::cross3(P0, P1, C0);
+    hx::cross3(P0, R1, U);
+    hx::cross3(R0, P1, V);
+    hx::cross3(R0, R1, C2);
+    for (int d = 0; d < 3; ++d) C1[d] = U[d] + V[d];
+    const double d0 = P0[0] * A0[0] + P0[1] * A0[1] + P0[2] * A0[2];
+    const double d1 = P0[0] * B0[0] + P0[1] * B0[1] + P0[2] * B0[2] + R0[0] * A0[0] + R0[1] * A0[1] + R0[2] * A0[2];
+    const double d2 = R0[0] * B0[0] + R0[1] * B0[1] + R0[2] * B0[2];
     for (int kq = 0; kq < q; ++kq) {
       const double z = T.xq[kq];
-      double j0[3], j1[3], f[7];
+      double c0[3], c1[3], c2[3], f[7];
       for (int d = 0; d < 3; ++d) {
-        j0[d] = P0[d] + z * R0[d];
-        j1[d] = P1[d] + z * R1[d];
+        c0[d] = A0[d] + z * B0[d];
+        c1[d] = A1[d] + z * B1[d];
+        c2[d] = C0[d] + z * (C1[d] + z * C2[d]);
       }
+      const double det = d0 + z * (d1 + z * d2);
       const int pt = kq * Q2 + col;
       const double w = w12 * T.wq[kq];
       const double nuv = nu_q ? nu_q[e * Q3 + pt] : nu;
-      const double det = hx::point_factors(j0, j1, j2, alpha * w, nuv * w, f);
+      const double s = nuv * w * hx::rcp_newton(det);
+      f[0] = alpha * w * det;
+      f[1] = s * (c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
+      f[2] = s * (c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2]);
+      f[3] = s * (c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2]);
+      f[4] = s * (c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2]);
+      f[5] = s * (c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2]);
+      f[6] = s * (c2[0] * c2[0] + c2[1] * c2[1] + c2[2] * c2[2]);
       if (!(det > 0.0)) ++nbad;
       for (int c = 0; c < 7; ++c) factors[(e * 7 + c) * Q3 + pt] = f[c];
     }
@@ -882,6 +910,41 @@ cudaError_t hx_launch_assemble32(long long n, const HxGridAsm& ga, const int* of
                                  const unsigned char* dir,
                                  int constrained, const float* x, float* y, cudaStream_t s) {
   return launch_assemble<float>(n, ga, off, idx, yE, dir, constrained, x, 0.0, y, s);
+}
+
+// Stored factors after a change of constant coefficients (one warp per (element, component)
+// row of q^3 points, so that the loads and stores are coalesced): m *= ra, G *= rk.
+__global__ void __launch_bounds__(kThreads) scale_factors_kernel(long long rows, int Q3, double ra, double rk,
+                                                                  double* __restrict__ f) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < rows; row += warps) {
+    const double r = (row % 7 == 0) ? ra : rk;
+    double* p = f + row * Q3;
+    for (int i = lane; i < Q3; i += 32) p[i] *= r;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) axpby_kernel(long long n, double ra, const double* __restrict__ a,
+                                                          double rk, const double* __restrict__ b,
+                                                          double* __restrict__ out) {
+  HX_GRID_STRIDE(g, n) { out[g] = ra * a[g] + rk * b[g]; }
+}
+
+cudaError_t hx_launch_scale_factors(long long E, int Q3, double ra, double rk, double* factors, cudaStream_t s) {
+  const long long rows = 7 * E;
+  if (rows == 0) return cudaSuccess;
+  long long b = (rows * 32 + kThreads - 1) / kThreads;
+  if (b > 148LL * 16) b = 148LL * 16;
+  scale_factors_kernel<<<(unsigned)b, kThreads, 0, s>>>(rows, Q3, ra, rk, factors);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_axpby(long long n, double ra, const double* a, double rk, const double* b, double* out,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  axpby_kernel<<<grid_for(n), kThreads, 0, s>>>(n, ra, a, rk, b, out);
+  return cudaGetLastError();
 }
 
 cudaError_t hx_launch_cmass(const HxTables& T, long long E, const double* X8, double alpha, double* dE,

@@ -271,3 +271,30 @@ def test_unstructured_mesh(hx, p):
     u, info = op.solve(to_dev(b), rtol=1e-10)
     assert info["status"] == 0 and info["true_rel_residual"] <= 1.01e-10
     assert rel_err(u.cpu().numpy(), jacobi_pcg(oop, b, 1e-12)[0]) <= 1e-8
+
+
+@pytest.mark.parametrize("p", [2, 5])
+def test_coefficient_updates_rescale_and_recompute(hx, p):
+    """New constant coefficients (both nonzero) rescale the stored factors in place and combine
+    the diagonal from its mass and stiffness parts; a zero coefficient, a nu field or more than
+    64 updates in a row recompute them.  Every state matches the oracle of its coefficients."""
+    from oracle import fem
+    shape = (3, 2, 4)
+    V, EV, om = case(shape, p)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, p + 2, V), 3.0, 0.25)
+    x = S.random_vector(om.n_dof, 77)
+    for step, (alpha, nu) in enumerate([(7.0, 0.5), (0.0, 2.0), (5.0, 2.0), (5.0, 0.125)] + [(1.5, 0.75)] * 66):
+        op.set_coefficients(alpha, nu)
+        if step < 4 or step in (66, 67, 69):  # before, at and after the recomputation cap
+            oop = fem.Operator(om, alpha, nu)
+            for constrained in (False, True):
+                _assert_close(op.apply(to_dev(x), constrained=constrained).cpu().numpy(),
+                              oop.apply(x, constrained=constrained))
+                _assert_close(op.diagonal(constrained).cpu().numpy(), oop.diagonal(constrained))
+    # a nu field replaces the constant, and a constant afterwards recomputes the factors
+    mesh = op.mesh
+    nu_q = torch.full((mesh.n_elem, (p + 2) ** 3), 0.3, dtype=torch.float64, device="cuda")
+    op.set_coefficients(2.0, 0.0, nu_q=nu_q)
+    _assert_close(op.apply(to_dev(x)).cpu().numpy(), fem.Operator(om, 2.0, 0.3).apply(x))
+    op.set_coefficients(4.0, 0.6)
+    _assert_close(op.diagonal(True).cpu().numpy(), fem.Operator(om, 4.0, 0.6).diagonal(True))
