@@ -136,6 +136,9 @@ struct hx_op {
   double* dmk = nullptr;         // [2][n_dof]
   double alpha_d = 0, nu_d = 0;
   bool dmk_ok = false;
+  float* dmk32 = nullptr;        // the same for the FP32 operator of the mixed-precision solver
+  double alpha_d32 = 0, nu_d32 = 0;
+  bool dmk32_ok = false;
   // low-order refined operator (Sec. 5.2) and its Chebyshev-Jacobi inverse (HX_PREC_LOR)
   HxLorMatrix lor = {};
   long long lor_nnz = 0;

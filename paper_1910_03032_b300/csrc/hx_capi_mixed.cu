@@ -206,11 +206,34 @@ hx_status ensure_mixed(hx_op* op) {
       d.dE = op->yE32;
       d.lay = m->lay;
       d.parts = 3;
-      HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
-      HX_TRY(hx_launch_assemble32(n, m->ga, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
-             "FP32 diagonal assembly");
+      // stored factors of constant coefficients: from its mass and stiffness parts, as in FP64
+      const bool split = op->geom == HX_GEOM_STORED && op->factors_ok && op->alpha_f != 0.0 && op->nu_f != 0.0;
+      if (split) {
+        if (!op->dmk32_ok) {
+          if (!op->dmk32 && (s = dalloc(&op->dmk32, 2 * (size_t)n, "FP32 diagonal parts"))) return s;
+          for (int part = 0; part < 2; ++part) {
+            d.parts = 1 + part;
+            HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
+            HX_TRY(hx_launch_assemble32(n, m->ga, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->dmk32 + part * n,
+                                        op->stream),
+                   "FP32 diagonal assembly");
+          }
+          op->launches += 4;
+          op->alpha_d32 = op->alpha_f;
+          op->nu_d32 = op->nu_f;
+          op->dmk32_ok = true;
+        }
+        HX_TRY(hx_launch_axpby32(n, (float)(op->alpha / op->alpha_d32), op->dmk32, (float)(op->nu / op->nu_d32),
+                                 op->dmk32 + n, op->Ap32, op->stream),
+               "FP32 diagonal from its parts");
+      } else {
+        HX_TRY(t[m->p](m->T32, d, op->geom, op->stream), "FP32 diagonal kernel");
+        HX_TRY(hx_launch_assemble32(n, m->ga, m->off, m->idx, op->yE32, m->dir, 0, nullptr, op->Ap32, op->stream),
+               "FP32 diagonal assembly");
+        op->launches += 1;
+      }
       HX_TRY(hx_launch_dinv32(n, op->Ap32, m->dir, op->dinv32, op->stream), "FP32 dinv");
-      op->launches += 3;
+      op->launches += 2;
     } else {
       if ((s = ensure_dinv(op, op->stream))) return s;
       HX_TRY(hx_launch_to_float(n, op->dinv, op->dinv32, op->stream), "FP32 dinv");

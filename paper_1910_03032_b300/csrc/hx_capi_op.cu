@@ -85,6 +85,7 @@ void hx_op_destroy(hx_op* op) {
   dfree(op->yE);
   dfree(op->diag);
   dfree(op->dmk);
+  dfree(op->dmk32);
   dfree(op->x);
   dfree(op->r);
   dfree(op->p);
@@ -250,6 +251,7 @@ hx_status setup_coefficients(hx_op* op, double alpha, double nu, const double* n
       HX_TRY(hx_launch_geometry(m->T, m->E, m->X8, nu_q, alpha, nu, op->factors, bad, s), "geometry kernel");
       op->rescales = 0;
       op->dmk_ok = false;
+      op->dmk32_ok = false;
     }
     op->alpha_f = alpha;
     op->nu_f = nu;

@@ -239,6 +239,8 @@ cudaError_t hx_launch_scale_factors(long long E, int Q3, double ra, double rk, d
 // out = ra a + rk b
 cudaError_t hx_launch_axpby(long long n, double ra, const double* a, double rk, const double* b, double* out,
                             cudaStream_t s);
+cudaError_t hx_launch_axpby32(long long n, float ra, const float* a, float rk, const float* b, float* out,
+                              cudaStream_t s);
 cudaError_t hx_launch_dinv32(long long n, const float* diag, const unsigned char* dir, float* dinv, cudaStream_t s);
 cudaError_t hx_launch_masked_copy(long long n, const double* src, const unsigned char* dir, int constrained,
                                   double value, double* dst, cudaStream_t s);

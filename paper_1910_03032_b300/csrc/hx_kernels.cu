@@ -925,9 +925,9 @@ __global__ void __launch_bounds__(kThreads) scale_factors_kernel(long long rows,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) axpby_kernel(long long n, double ra, const double* __restrict__ a,
-                                                          double rk, const double* __restrict__ b,
-                                                          double* __restrict__ out) {
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) axpby_kernel(long long n, Real ra, const Real* __restrict__ a, Real rk,
+                                                          const Real* __restrict__ b, Real* __restrict__ out) {
   HX_GRID_STRIDE(g, n) { out[g] = ra * a[g] + rk * b[g]; }
 }
 
@@ -943,7 +943,14 @@ cudaError_t hx_launch_scale_factors(long long E, int Q3, double ra, double rk, d
 cudaError_t hx_launch_axpby(long long n, double ra, const double* a, double rk, const double* b, double* out,
                             cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  axpby_kernel<<<grid_for(n), kThreads, 0, s>>>(n, ra, a, rk, b, out);
+  axpby_kernel<double><<<grid_for(n), kThreads, 0, s>>>(n, ra, a, rk, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t hx_launch_axpby32(long long n, float ra, const float* a, float rk, const float* b, float* out,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  axpby_kernel<float><<<grid_for(n), kThreads, 0, s>>>(n, ra, a, rk, b, out);
   return cudaGetLastError();
 }
 
