@@ -159,12 +159,18 @@ HX_API hx_status hx_op_create(hx_mesh* mesh, double alpha, double nu, const doub
                               void* stream, hx_op** out);
 
 /*
- * Replace the coefficients of an existing operator: recomputes the stored
- * factors m = alpha w detJ, G = nu w detJ J^-1 J^-T (Sec. 3.1) and the
- * diagonal, e.g. when the time step 1/alpha or the viscosity changes between
- * the Helmholtz solves of successive time steps (Sec. 4.2, Sec. 5.3).  Same
- * meaning of alpha, nu, nu_q as hx_op_create; an HX_GEOM_ONTHEFLY operator takes
- * a nu_q field only if it was created with one.  Allocates nothing; stream-ordered.
+ * Replace the coefficients of an existing operator: updates the stored
+ * factors m = alpha w detJ, G = nu w detJ J^-1 J^-T (Sec. 3.1); the diagonal
+ * follows at the next call that needs it.  Use: the time step 1/alpha or the
+ * viscosity changes between the Helmholtz solves of successive time steps
+ * (Sec. 4.2, Sec. 5.3).  Same meaning of alpha, nu, nu_q as hx_op_create; an
+ * HX_GEOM_ONTHEFLY operator takes a nu_q field only if it was created with one.
+ * With stored factors and constant coefficients, both nonzero before and after,
+ * the factors are scaled in place by alpha'/alpha and nu'/nu (m is linear in
+ * alpha, G in nu; one rounding per update) and the diagonal is combined from
+ * its mass and stiffness parts; a zero coefficient, a nu field, or 64 such
+ * updates in a row recompute the factors from the geometry.  Allocates
+ * nothing; stream-ordered.
  */
 HX_API hx_status hx_op_set_coefficients(hx_op* op, double alpha, double nu, const double* nu_q, void* stream);
 
