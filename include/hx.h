@@ -151,8 +151,9 @@ HX_API hx_status hx_mesh_node_coords(const hx_mesh* mesh, double* xyz, void* str
  *   geom_mode  HX_GEOM_STORED: precompute m = alpha w detJ and G = nu w detJ J^-1 J^-T
  *              at every point ([E][7][q^3] doubles, Sec. 3.1 stored-J variant);
  *              HX_GEOM_ONTHEFLY: recompute them from the element vertices at each apply
- *   stream     stream for the setup kernels (geometric factors, diagonal)
- * Also assembles the diagonal of A (for Jacobi).  Returns HX_ERR_INVALID_MESH
+ *   stream     stream for the setup kernels (geometric factors)
+ * The diagonal of A (for Jacobi) is assembled by the first call that needs it
+ * (a solve, hx_op_diagonal).  Returns HX_ERR_INVALID_MESH
  * when detJ <= 0 at some quadrature point.  Synchronizes `stream` before returning.
  */
 HX_API hx_status hx_op_create(hx_mesh* mesh, double alpha, double nu, const double* nu_q, int geom_mode,
