@@ -305,6 +305,15 @@ HX_API hx_status hx_op_apply_f32(hx_op* op, const float* x, float* y, void* stre
 #define HX_F32_MMA_BF16 3
 #define HX_F32_MMA_BF16X3 4
 HX_API hx_status hx_op_set_f32_kernel(hx_op* op, int kind);
+/*
+ * Tile variant of a kind selected with hx_op_set_f32_kernel (test and tuning hook): -1, 0, +1
+ * for half, the default and twice the elements per block of HX_F32_DIRECT_STAGED and
+ * HX_F32_DIRECT with stored factors; other kinds and HX_F32_AUTO ignore it.  HX_ERR_ARG outside
+ * -1..1, HX_ERR_UNSUPPORTED for a nonzero tile with on-the-fly geometry; a variant the order
+ * does not have (more than 8 elements or 1024 threads per block) makes the next FP32 set-up
+ * return HX_ERR_UNSUPPORTED.  Takes effect at the next FP32 set-up.  Host-side only.
+ */
+HX_API hx_status hx_op_set_f32_tile(hx_op* op, int tile);
 HX_API hx_status hx_op_f32_kernel(const hx_op* op, int* kind, int* block_elems, float* ms /* 3 entries or NULL */);
 
 /*

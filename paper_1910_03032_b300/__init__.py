@@ -76,6 +76,7 @@ SIGNATURES = {
     "hx_op_apply_f32": (_I, [_P, _P, _P, _P]),
     "hx_op_set_wait_limit": (_I, [_P, _I]),
     "hx_op_set_f32_kernel": (_I, [_P, _I]),
+    "hx_op_set_f32_tile": (_I, [_P, _I]),
     "hx_op_f32_kernel": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "hx_op_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
     "hx_op_collocated_mass": (_I, [_P, _P, _P]),
@@ -333,6 +334,10 @@ HX_F32_MMA_BF16, HX_F32_MMA_BF16X3 = 3, 4
 
 def hx_op_set_f32_kernel(op, kind):
     _check(_lib.hx_op_set_f32_kernel(op, int(kind)))
+
+
+def hx_op_set_f32_tile(op, tile):
+    _check(_lib.hx_op_set_f32_tile(op, int(tile)))
 
 
 def hx_op_f32_kernel(op):
@@ -597,6 +602,9 @@ class Operator:
 
     def set_f32_kernel(self, kind):
         hx_op_set_f32_kernel(self.handle, kind)
+
+    def set_f32_tile(self, tile):
+        hx_op_set_f32_tile(self.handle, tile)
 
     def f32_kernel(self):
         return hx_op_f32_kernel(self.handle)

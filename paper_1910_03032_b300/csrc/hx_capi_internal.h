@@ -105,6 +105,7 @@ struct hx_op {
   int f32_request = HX_F32_AUTO;  // FP32 element kernel asked for (hx_op_set_f32_kernel)
   int f32_kind = -1;              // FP32 element kernel in use (-1: not chosen yet)
   int f32_tile = 0;               // its tile variant (-1, 0, +1: half, default, twice the elements per block)
+  int f32_tile_request = 0;       // tile asked for with a direct kind (hx_op_set_f32_tile)
   float f32_ms[3] = {-1.0f, -1.0f, -1.0f};  // autotuner: average time of each candidate (ms)
   float *yE32 = nullptr, *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *dinv32 = nullptr;
   double* rn2 = nullptr;        // device ||r||^2 of the outer FP64 residual

@@ -59,8 +59,18 @@ std::map<F32Key, std::pair<int, int>> g_f32_choice;  // (kind, tile)
 hx_status tune_f32(hx_op* op) {
   if (op->f32_kind >= 0) return HX_OK;
   if (op->f32_request >= 0) {
+    const bool direct = op->f32_request == HX_F32_DIRECT_STAGED || op->f32_request == HX_F32_DIRECT;
+    const int tile = direct ? op->f32_tile_request : 0;
+    if (direct && tile != 0) {
+      static const hx_block_elems_fn t[] = {nullptr, hx_apply32_block_elems_p1, hx_apply32_block_elems_p2,
+                                            hx_apply32_block_elems_p3, hx_apply32_block_elems_p4,
+                                            hx_apply32_block_elems_p5, hx_apply32_block_elems_p6,
+                                            hx_apply32_block_elems_p7, hx_apply32_block_elems_p8};
+      if (t[op->mesh->p](op->mesh->q, tile) == 0)
+        return fail(HX_ERR_UNSUPPORTED, "no FP32 tile variant %d for p = %d, q = %d", tile, op->mesh->p, op->mesh->q);
+    }
     op->f32_kind = op->f32_request;
-    op->f32_tile = 0;
+    op->f32_tile = tile;
     return HX_OK;
   }
   const hx_mesh* m = op->mesh;
@@ -423,6 +433,21 @@ hx_status hx_op_set_f32_kernel(hx_op* op, int kind) {
     return fail(HX_ERR_UNSUPPORTED, "FP32 kernel kind %d needs stored factors", kind);
   op->f32_request = kind;
   op->f32_kind = -1;  // resolved (or tuned) at the next FP32 set-up
+  if (op->graph32) {
+    cudaGraphExecDestroy(op->graph32);
+    op->graph32 = nullptr;
+  }
+  op->graph32_failed = false;
+  return HX_OK;
+}
+
+hx_status hx_op_set_f32_tile(hx_op* op, int tile) {
+  if (!op) return fail(HX_ERR_ARG, "op is NULL");
+  if (tile < -1 || tile > 1) return fail(HX_ERR_ARG, "FP32 tile variant %d is not -1, 0 or 1", tile);
+  if (tile != 0 && op->geom != HX_GEOM_STORED)
+    return fail(HX_ERR_UNSUPPORTED, "FP32 tile variants need stored factors");
+  op->f32_tile_request = tile;
+  op->f32_kind = -1;  // resolved at the next FP32 set-up
   if (op->graph32) {
     cudaGraphExecDestroy(op->graph32);
     op->graph32 = nullptr;

@@ -42,6 +42,44 @@ def test_fp32_apply_matches_oracle(hx, p, shape, geom, kind):
         assert ms[used] == min(m for m in ms if m >= 0)
 
 
+@pytest.mark.parametrize("p,q,shape", [(1, 3, (5, 5, 3)), (2, 4, (5, 5, 3)), (3, 5, (5, 5, 3)), (4, 6, (5, 3, 3)),
+                                       (4, 5, (3, 3, 3)), (5, 7, (4, 3, 2)), (6, 8, (3, 3, 1)), (8, 10, (3, 3, 1))])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_fp32_direct_tiles_match_oracle(hx, p, q, shape, kind):
+    """Every tile variant the autotuner may pick (half, default and twice the elements per block
+    of the B/D-direct kernels), forced one by one, on meshes with a ragged last block; a variant
+    the order does not have is refused."""
+    from oracle import fem
+    V, EV, om = case(shape, p, q=q)
+    op = hx.Operator(hx.Mesh.structured(*shape, p, q, V), 1.7, 0.45)
+    ref_op = fem.Operator(om, 1.7, 0.45)
+    x32 = S.random_vector(om.n_dof, 3033).astype(np.float32)
+    ref = ref_op.apply(x32.astype(np.float64), constrained=True)
+    seen = []
+    for tile in (-1, 0, 1):
+        op.set_f32_kernel(kind)
+        op.set_f32_tile(tile)
+        default = 8 if 8 * q * q <= 256 else 4 if 4 * q * q <= 256 else 2
+        ne = default // 2 if tile < 0 else default * 2 if tile > 0 else default
+        if ne < 1 or ne > 8 or ((ne * q * q + 31) // 32) * 32 > 1024:
+            with pytest.raises(hx.HxError) as ei:
+                op.apply_f32(torch.as_tensor(x32, device="cuda"))
+            assert ei.value.status == hx.HX_ERR_UNSUPPORTED
+            continue
+        try:
+            y = op.apply_f32(torch.as_tensor(x32, device="cuda")).double().cpu().numpy()
+        except hx.HxError as e:  # a variant whose shared memory exceeds a block's limit
+            assert kind == 1 and tile > 0, e
+            continue
+        assert rel_err(y, ref) <= 2e-5, (tile, rel_err(y, ref))
+        used, got_ne, _ = op.f32_kernel()
+        assert used == kind and got_ne == ne
+        seen.append(ne)
+    assert default in seen
+    with pytest.raises(hx.HxError):
+        op.set_f32_tile(2)
+
+
 @pytest.mark.parametrize("p,shape", [(1, (5, 5, 3)), (2, (5, 5, 3)), (3, (5, 5, 3)), (4, (5, 3, 3)), (5, (4, 3, 2)),
                                      (6, (3, 3, 1)), (7, (2, 2, 2)), (8, (3, 3, 1))])
 @pytest.mark.parametrize("kind,tol", [(3, 3e-2), (4, 1e-4)])
