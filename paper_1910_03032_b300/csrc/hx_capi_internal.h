@@ -82,7 +82,7 @@ struct hx_op {
   double* factors = nullptr;  // [E][7][Q3] (stored)
   double* nu_q = nullptr;     // [E][Q3] (on the fly with a field)
   bool use_field = false;     // on the fly: nu_q holds the current field
-  double* yE = nullptr;       // [E][n^3]
+  double* yE = nullptr;       // E-vector, E n^3 values in the mesh's layout (mesh->lay)
   double* diag = nullptr;     // [n_dof] unconstrained diagonal
   // solver workspace (allocated at the first solve)
   double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *dinv = nullptr, *partial = nullptr;
