@@ -330,7 +330,7 @@ def run_reference(args, world, rank):
 def workload_config(args):
     p, N = args.p, args.n
     return {"workload": f"FP64 Helmholtz alpha*M+nu*K (alpha=1/dt=1000, nu=1e-2) on a perturbed {N}^3 hex mesh, "
-                        f"Q_{p} GLL, q={p + 2} Gauss; coefficient setup + Jacobi-PCG to 1e-10 on the "
+                        f"Q_{p} GLL, q={p + 2} Gauss; coefficient update + Jacobi-PCG to 1e-10 on the "
                         f"manufactured RHS", "p": p, "q": p + 2, "mesh": f"{N}^3", "n_dof": (p * N + 1) ** 3,
             "geometry": args.geom, "l2": "inputs larger than L2 (geometric factors stream from HBM every apply)"}
 
