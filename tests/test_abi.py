@@ -82,6 +82,9 @@ def test_size_and_index_validation_without_device():
     assert lib.hx_op_create(None, ctypes.c_double(1.0), ctypes.c_double(1.0), None, 0, None,
                             ctypes.byref(out)) == hx.HX_ERR_ARG
     assert lib.hx_batch_create(0, None, None, None, ctypes.c_double(1e-10), 10, 0, ctypes.byref(out)) == hx.HX_ERR_ARG
+    for name, args in [("hx_op_set_f32_kernel", (0,)), ("hx_op_set_f32_tile", (0,)), ("hx_op_set_wait_limit", (1,)),
+                       ("hx_op_set_coefficients", (ctypes.c_double(1.0), ctypes.c_double(1.0), None, None))]:
+        assert getattr(lib, name)(None, *args) == hx.HX_ERR_ARG, name
 
 
 def test_build_flags_target_sm_103a():
